@@ -1,0 +1,18 @@
+"""FP64 CPU oracle for the indexed limit-set renderer (arXiv:1709.08018).
+
+TEST INFRASTRUCTURE: only the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
+with the CUDA library (``paper_1709_08018_gb300``) and never imports it.
+
+Parity status per function (what pins it is in ``tests/test_oracle_pins.py``):
+  grandma        pinned: trace, determinant and commutator-trace invariants,
+                 the closed-form gasket matrices at ta = tb = 2
+  seeds          pinned: fixed-point equation, attraction, gasket closed form
+  decode         pinned: brute-force scan of all 4^d base-4 strings filtered
+                 by the paper's indexed Cayley table (order and set), counts
+  eval           pinned: the paper's abA orbit order, independent matrix
+                 products, the Fuchsian circle, tree walk = per-word bitwise
+  render         pinned: brute-force render from the scan, hit conservation
+  mlp (numpy)    pinned: central finite differences, closed-form tiny nets
+"""
+from .oracle import *  # noqa: F401,F403

@@ -1,0 +1,153 @@
+"""ctypes front end of the C oracle (``kl_oracle.c``).
+
+TEST INFRASTRUCTURE: see the package docstring.
+"""
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import build_oracle
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build_oracle.build()
+        L = ctypes.CDLL(path)
+        D, U64, I, P = ctypes.c_double, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p
+        L.or_grandma.argtypes = [D, D, D, D, P]
+        L.or_grandma.restype = I
+        L.or_seeds.argtypes = [P, P]
+        L.or_seeds.restype = I
+        L.or_word_count.argtypes = [I]
+        L.or_word_count.restype = U64
+        L.or_decode.argtypes = [I, U64, P]
+        L.or_decode.restype = I
+        L.or_eval.argtypes = [P, P, I, P, U64, P]
+        L.or_eval.restype = I
+        L.or_render_indexed.argtypes = [P, P, I, P, I, I, U64, U64, P, P, D, P, P, U64, P]
+        L.or_render_indexed.restype = I
+        L.or_render_tree.argtypes = [P, P, I, P, I, I, I, P, P, D, P, P, U64, P]
+        L.or_render_tree.restype = I
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def grandma(ta: complex, tb: complex) -> np.ndarray:
+    """Generators a, b, A, B from traces: 32 doubles, per matrix p, q, r, s as
+    (re, im)."""
+    out = np.zeros(32, dtype=np.float64)
+    rc = lib().or_grandma(ta.real, ta.imag, tb.real, tb.imag, _ptr(out))
+    if rc != 0:
+        raise ValueError("degenerate traces for the recipe")
+    return out
+
+
+def seeds(gens: np.ndarray) -> np.ndarray:
+    """Attracting fixed points of a, b, A, B: 8 doubles (re, im)."""
+    g = np.ascontiguousarray(gens, dtype=np.float64)
+    out = np.zeros(8, dtype=np.float64)
+    if lib().or_seeds(_ptr(g), _ptr(out)) != 0:
+        raise ValueError("a generator has no attracting finite fixed point")
+    return out
+
+
+def group(ta: complex, tb: complex) -> Tuple[np.ndarray, np.ndarray]:
+    g = grandma(ta, tb)
+    return g, seeds(g)
+
+
+def as_matrices(gens: np.ndarray):
+    """32 doubles -> list of four 2x2 complex128 matrices [[p, q], [r, s]]."""
+    g = np.asarray(gens, dtype=np.float64).reshape(4, 4, 2)
+    c = g[..., 0] + 1j * g[..., 1]
+    return [c[k].reshape(2, 2) for k in range(4)]
+
+
+def as_points(seeds8: np.ndarray):
+    s = np.asarray(seeds8, dtype=np.float64).reshape(4, 2)
+    return [complex(s[k, 0], s[k, 1]) for k in range(4)]
+
+
+def word_count(d: int) -> int:
+    return int(lib().or_word_count(d))
+
+
+def decode(d: int, indices) -> np.ndarray:
+    """Letter codes (n, d) uint8 of the given word indices."""
+    idx = np.ascontiguousarray(indices, dtype=np.uint64).ravel()
+    out = np.zeros((idx.size, d), dtype=np.uint8)
+    buf = np.zeros(d, dtype=np.uint8)
+    L = lib()
+    for t, i in enumerate(idx):
+        if L.or_decode(d, int(i), _ptr(buf)) != 0:
+            raise IndexError(f"index {int(i)} outside [0, N_{d})")
+        out[t] = buf
+    return out
+
+
+def evaluate(gens, seeds8, d: int, indices) -> np.ndarray:
+    """Word values (complex128) of the given indices, one sequential orbit per word."""
+    idx = np.ascontiguousarray(indices, dtype=np.uint64).ravel()
+    g = np.ascontiguousarray(gens, dtype=np.float64)
+    s = np.ascontiguousarray(seeds8, dtype=np.float64)
+    out = np.zeros(2 * idx.size, dtype=np.float64)
+    if lib().or_eval(_ptr(g), _ptr(s), d, _ptr(idx), idx.size, _ptr(out)) != 0:
+        raise IndexError("bad depth or index")
+    return out[0::2] + 1j * out[1::2]
+
+
+@dataclass
+class Render:
+    image: np.ndarray        # uint32 (H, W)
+    in_window: int
+    dropped: int
+    edge_idx: np.ndarray     # uint64 (k,) indices of edge words
+    edge_uv: np.ndarray      # float64 (k, 2) their pixel coordinates (u, v)
+    edge_total: int          # edge words found (may exceed the stored k)
+
+
+def render(gens, seeds8, d: int, window: Sequence[float], width: int, height: int,
+           mode: str = "tree", threads: Optional[int] = None, eta: float = 0.0,
+           edge_cap: int = 1 << 16, i0: int = 0, i1: Optional[int] = None) -> Render:
+    """Hit image of all reduced words of length d (mode "tree": tree walk,
+    multi-threaded; mode "indexed": per word over [i0, i1), single thread).
+    Words whose pixel coordinates lie within ``eta`` pixels of a pixel edge are
+    logged as edge words."""
+    g = np.ascontiguousarray(gens, dtype=np.float64)
+    s = np.ascontiguousarray(seeds8, dtype=np.float64)
+    win = np.ascontiguousarray(window, dtype=np.float64)
+    img = np.zeros((height, width), dtype=np.uint32)
+    cnt = np.zeros(2, dtype=np.uint64)
+    cap = edge_cap if eta > 0 else 0
+    eidx = np.zeros(max(cap, 1), dtype=np.uint64)
+    euv = np.zeros(2 * max(cap, 1), dtype=np.float64)
+    ecount = np.zeros(1, dtype=np.uint64)
+    L = lib()
+    if mode == "tree":
+        if threads is None:
+            threads = os.cpu_count() or 1
+        rc = L.or_render_tree(_ptr(g), _ptr(s), d, _ptr(win), width, height, threads,
+                              _ptr(img), _ptr(cnt), eta, _ptr(eidx), _ptr(euv), cap, _ptr(ecount))
+    elif mode == "indexed":
+        n = word_count(d)
+        i1 = n if i1 is None else i1
+        rc = L.or_render_indexed(_ptr(g), _ptr(s), d, _ptr(win), width, height, i0, i1,
+                                 _ptr(img), _ptr(cnt), eta, _ptr(eidx), _ptr(euv), cap,
+                                 _ptr(ecount))
+    else:
+        raise ValueError(mode)
+    if rc != 0:
+        raise ValueError("bad render arguments")
+    k = int(min(int(ecount[0]), cap))
+    return Render(img, int(cnt[0]), int(cnt[1]), eidx[:k].copy(),
+                  euv[:2 * k].reshape(k, 2).copy(), int(ecount[0]))
