@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark: words/s evaluated and splatted at depth d, on GB300.
+
+Workload (default): the gasket group ta = tb = 2, all 516,560,652 reduced
+words of length 18, 4096 x 4096 uint32 hit image over [-1.5, 1.5]^2, mixed
+precision (FP32 per-word map with FP64 prefix matrices, FP64 near-parabolic
+prefixes), which is the configuration the words/s metric is quoted on; the
+plain FP64 render of the same job is timed beside it.  One step = one full
+kl_render call: image and counter zeroing, prefix table, suffix table, the
+per-word render kernel and the FP64 fallback kernel.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Rank 0 prints one JSON line.  With N > 1 (torchrun) every rank renders the
+whole job on its own GPU (independent replicas: weak scaling); value is the
+words of all ranks divided by the slowest rank's time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import klsynth  # noqa: E402
+
+METRIC = "words/sec evaluated+splatted at depth d"
+FP32_OPS_PER_WORD = 12    # FP32 FMA-pipe operations of the mixed per-word map
+FP64_OPS_PER_WORD = 13    # FP64 operations of the plain per-word map
+SMS = 152
+FP32_LANES_PER_SM = 128
+FP64_LANES_PER_SM = 2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    c = klsynth.C2
+    return c, {"workload": "gasket ta=tb=2, all reduced words of length 18, 4096x4096 uint32, "
+                           "window [-1.5,1.5]^2, mixed FP32/FP64",
+               "group": "grandma ta=tb=2+0i", "depth": c.depth, "words_per_step": c.n_words,
+               "image": [c.width, c.height], "window": list(c.window),
+               "l2": "flushed between timed steps (256 MiB write)"}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as f:
+                for ln in f:
+                    t = [x.strip() for x in ln.split(",")]
+                    if len(t) >= 9:
+                        rows.append(t)
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1709_08018_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    k = rec.get(kernel)
+    if not k or k.get("source_hash") != source_hash():
+        return None
+    return k.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(cfg, budget_s=15.0):
+    """The oracle's tree walk on all host cores over the first jobs of the same
+    render (equal-size jobs), sized to about budget_s seconds."""
+    import oracle
+    g, s = oracle.group(cfg.group.ta, cfg.group.tb)
+    jobs = oracle.tree_jobs(cfg.depth)
+    threads = os.cpu_count() or 1
+    per_job = cfg.n_words // jobs
+    t0 = time.perf_counter()
+    oracle.render(g, s, cfg.depth, cfg.window, cfg.width, cfg.height, threads=threads,
+                  jobs=(0, min(jobs, threads)))
+    dt = time.perf_counter() - t0
+    done, words, elapsed = min(jobs, threads), per_job * min(jobs, threads), dt
+    if elapsed < budget_s and done < jobs:
+        more = int(min(jobs - done, max(1, (budget_s - elapsed) / max(dt, 1e-9) * done)))
+        t0 = time.perf_counter()
+        oracle.render(g, s, cfg.depth, cfg.window, cfg.width, cfg.height, threads=threads,
+                      jobs=(done, done + more))
+        elapsed += time.perf_counter() - t0
+        done += more
+        words += per_job * more
+    return {"value": words / elapsed, "unit": "words/s", "cores": threads, "kind": "oracle",
+            "sample": f"tree-walk jobs 0..{done - 1} of {jobs} (words with fixed innermost 5 "
+                      f"letters; {words} of {cfg.n_words} words), FP64, {threads} threads",
+            "seconds": elapsed}
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm (rank 0 only)."""
+    world, rank, _ = dist_env()
+    cfg, config = workload()
+    if rank != 0:
+        return
+    import oracle
+    g, s = oracle.group(cfg.group.ta, cfg.group.tb)
+    jobs = oracle.tree_jobs(cfg.depth)
+    threads = os.cpu_count() or 1
+    per_job = cfg.n_words // jobs
+    # each step renders `chunk` equal-size jobs, sized so that warmup + steps
+    # end in about two minutes
+    t0 = time.perf_counter()
+    oracle.render(g, s, cfg.depth, cfg.window, cfg.width, cfg.height, threads=threads,
+                  jobs=(0, threads))
+    probe = (time.perf_counter() - t0) / threads
+    per_step = 120.0 / max(1, args.steps + args.warmup)
+    chunk = int(max(1, min(jobs, per_step / max(probe, 1e-9))))
+    times = []
+    for k in range(args.warmup + args.steps):
+        j0 = (k * chunk) % jobs
+        j1 = min(jobs, j0 + chunk)
+        t0 = time.perf_counter()
+        oracle.render(g, s, cfg.depth, cfg.window, cfg.width, cfg.height, threads=threads,
+                      jobs=(j0, j1))
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append((dt, (j1 - j0) * per_job))
+    secs = sum(t for t, _ in times)
+    words = sum(w for _, w in times)
+    value = words / secs
+    sample = (f"{chunk} of {jobs} equal tree-walk jobs per step ({chunk * per_job} of "
+              f"{cfg.n_words} words), FP64 oracle, {threads} threads")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "words/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * secs / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config,
+            "cpu_baseline": {"value": value, "unit": "words/s", "cores": threads,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "words/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import paper_1709_08018_gb300 as kl
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg, config = workload()
+    N = cfg.n_words
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    p = kl.params_init(cfg.group.ta, cfg.group.tb, cfg.depth, cfg.width, cfg.height,
+                       cfg.window, kl.MIXED)
+    r = kl.Renderer(p, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def events(n):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        for e in ev:
+            e.record(stream)   # create the underlying CUDA events
+        return ev
+
+    for _ in range(args.warmup):
+        r()
+    torch.cuda.synchronize(dev)
+
+    K = args.steps
+    st0, st1, kn0, kn1 = events(K), events(K), events(K), events(K)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    with sampler:
+        barrier()
+        torch.cuda.synchronize(dev)
+        for k in range(K):
+            flush.fill_(k & 0xFF)                   # L2 flush, outside the timed events
+            kl.set_profile_events(kn0[k], kn1[k])
+            st0[k].record(stream)
+            r()
+            st1[k].record(stream)
+        kl.set_profile_events()
+        torch.cuda.synchronize(dev)
+        barrier()
+    clocks = sampler.summary()
+    step_ms = [st0[k].elapsed_time(st1[k]) for k in range(K)]
+    kern_ms = [kn0[k].elapsed_time(kn1[k]) for k in range(K)]
+    total_ms = max_over_ranks(sum(step_ms))
+    value = world * N * K / (total_ms / 1000.0)
+    cnt = r.counters.cpu().tolist()
+    fp64_words = int(cnt[2])
+
+    # plain FP64 render of the same job, timed the same way
+    p64 = kl.params_init(cfg.group.ta, cfg.group.tb, cfg.depth, cfg.width, cfg.height,
+                         cfg.window, kl.FP64)
+    r64 = kl.Renderer(p64, device=dev)
+    r64()
+    K64 = max(3, min(10, K // 5))
+    a0, a1, b0, b1 = events(K64), events(K64), events(K64), events(K64)
+    torch.cuda.synchronize(dev)
+    for k in range(K64):
+        flush.fill_(k & 0xFF)
+        kl.set_profile_events(b0[k], b1[k])
+        a0[k].record(stream)
+        r64()
+        a1[k].record(stream)
+    kl.set_profile_events()
+    torch.cuda.synchronize(dev)
+    fp64_step_ms = statistics.median(a0[k].elapsed_time(a1[k]) for k in range(K64))
+    fp64_kern_ms = statistics.median(b0[k].elapsed_time(b1[k]) for k in range(K64))
+    del r64
+
+    # end to end through the public API: host parameters in, image and
+    # counters copied back to pinned host memory every step
+    host_img = torch.empty((cfg.height, cfg.width), dtype=torch.int32, pin_memory=True)
+    host_cnt = torch.empty(kl.KL_N_COUNTERS, dtype=torch.int64, pin_memory=True)
+    KE = max(3, min(K, 20))
+    e0, e1 = events(KE), events(KE)
+    torch.cuda.synchronize(dev)
+    barrier()
+    for k in range(KE):
+        flush.fill_(k & 0xFF)
+        e0[k].record(stream)
+        kl.render(r.p, r.image, r.counters, r.workspace)
+        host_img.copy_(r.image, non_blocking=True)
+        host_cnt.copy_(r.counters, non_blocking=True)
+        e1[k].record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = max_over_ranks(sum(e0[k].elapsed_time(e1[k]) for k in range(KE)))
+    e2e_value = world * N * KE / (e2e_ms / 1000.0)
+
+    pk = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    fp32_peak = SMS * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12     # T lane-ops/s
+    fp64_peak = SMS * FP64_LANES_PER_SM * sm_max * 1e6 / 1e12
+    kern_s = statistics.mean(kern_ms) / 1000.0
+    words_fp32 = N - fp64_words
+    achieved = words_fp32 * FP32_OPS_PER_WORD / kern_s / 1e12
+    roofline = {"bound": "alu", "kernel": "render32_kernel", "achieved": achieved,
+                "peak": fp32_peak, "unit": "T FP32-op/s", "frac": achieved / fp32_peak,
+                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x max SM clock",
+                "ops_per_word": FP32_OPS_PER_WORD,
+                "traffic": traffic_for("render32_kernel"),
+                "kernel_ms": statistics.mean(kern_ms),
+                "kernel_share_of_step": statistics.mean(kern_ms) / statistics.mean(step_ms)}
+    fp64_ach = N * FP64_OPS_PER_WORD / (fp64_kern_ms / 1000.0) / 1e12
+    plain = {"words_per_s": N / (fp64_step_ms / 1000.0), "ms_per_step": fp64_step_ms,
+             "kernel_ms": fp64_kern_ms,
+             "roofline": {"bound": "alu", "kernel": "render64_kernel", "achieved": fp64_ach,
+                          "peak": fp64_peak, "unit": "T FP64-op/s", "frac": fp64_ach / fp64_peak,
+                          "peak_kind": "derived: 152 SMs x 2 FP64 lanes x max SM clock",
+                          "ops_per_word": FP64_OPS_PER_WORD,
+                          "traffic": traffic_for("render64_kernel")}}
+    line = {"metric": METRIC, "value": value, "unit": "words/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": config, "clocks": clocks, "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": "words/s",
+                    "h2d_bytes_per_step": __import__("ctypes").sizeof(r.p),
+                    "d2h_bytes_per_step": cfg.width * cfg.height * 4 + kl.KL_N_COUNTERS * 8},
+            "gpu_launches": 4 * K,
+            "counters": {"in_window": int(cnt[0]), "dropped": int(cnt[1]),
+                         "fp64_words": fp64_words, "atomics": int(cnt[3])},
+            "plain_fp64": plain,
+            "speedup_mixed_over_fp64": fp64_step_ms / (total_ms / K)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,180 @@
+/*
+ * kl.h -- C ABI of the GB300 indexed limit-set renderer.
+ *
+ * The library renders the limit set (attractor) of a once-punctured-torus
+ * group generated by four linear-fractional maps a, b, A = a^-1, B = b^-1,
+ * following A. Rosa, "A new indexed approach to render the attractors of
+ * Kleinian groups" (arXiv:1709.08018): every reduced word of length d over
+ * {a, b, A, B} is pulled out of an integer index instead of being stored
+ * (Sec. "The revised deterministic approach"), its maps are applied to a seed
+ * point right to left (Sec. "Introduction"), and the resulting word value is
+ * drawn into a hit image (Sec. "Implementation", the index-search loop).
+ *
+ * Conventions shared by every entry point:
+ *  - Letters have codes a = 0, b = 1, A = 2, B = 3 (the row order of the
+ *    paper's Cayley table, Sec. "Once-punctured torus groups", minus one), so
+ *    the inverse of x is (x + 2) mod 4.
+ *  - A word w_1 .. w_d is applied right to left: w_d first, w_1 last.
+ *  - Word index i in [0, N_d), N_d = 4 * 3^(d-1): w_1 = floor(i / 3^(d-1)),
+ *    then each base-3 digit c_k of the rest (most significant first) selects
+ *    the c_k-th smallest letter other than inv(w_{k-1}).  This is the order
+ *    in which the paper's base-4 scan filtered by the indexed Cayley table
+ *    (Sec. "Cayley Multiplication Tables", "Implementation") meets reduced
+ *    words.
+ *  - Complex numbers are pairs of doubles (re, im).  A matrix [[p, q], [r, s]]
+ *    acting as z -> (p z + q)/(r z + s) is stored as 8 doubles
+ *    p.re p.im q.re q.im r.re r.im s.re s.im.
+ *  - Pointers named d_* are device pointers (cudaMalloc'd, or torch CUDA
+ *    tensors); all others are host pointers.  The caller owns every buffer;
+ *    the library never allocates, frees or retains caller memory.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Device
+ *    work is enqueued asynchronously; argument errors are returned before
+ *    anything is enqueued.  A CUDA launch error is returned as KL_ECUDA.
+ *  - Return values are kl_status codes; no C++ exception crosses the ABI.
+ */
+#ifndef KL_H
+#define KL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define KL_API __attribute__((visibility("default")))
+#else
+#define KL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+typedef enum {
+  KL_OK = 0,
+  KL_EINVAL = 1,      /* a null pointer, a bad size, window or depth */
+  KL_ERANGE = 2,      /* a value outside the representable range (e.g. N_d > 2^64) */
+  KL_ECUDA = 3,       /* the CUDA runtime reported an error */
+  KL_ENOSPACE = 4,    /* the workspace passed is smaller than required */
+  KL_EDEGENERATE = 5  /* degenerate traces or generators (recipe or fixed point undefined) */
+} kl_status;
+
+/* Arithmetic of the per-word work. */
+typedef enum {
+  KL_FP64 = 0,   /* every step in FP64 */
+  KL_MIXED = 1   /* prefix products, renormalisation and near-parabolic words in
+                    FP64; the per-word map in FP32 in a per-prefix local frame */
+} kl_precision;
+
+#define KL_MAX_DEPTH 40          /* N_40 = 4 * 3^39 < 2^64 */
+#define KL_MAX_IMAGE_SIDE 65536  /* width and height limit */
+
+/* Everything one render needs: the group (generators and seeds), the word
+ * length, the view window and the image size.  Fill with kl_params_init, or
+ * set the fields directly (gens and seeds from kl_grandma / kl_seeds or from
+ * the caller's own matrices of determinant one). */
+typedef struct {
+  double gens[32];         /* a, b, A, B (8 doubles each, layout above) */
+  double seeds[8];         /* seed point of each first-applied letter a, b, A, B */
+  uint32_t depth;          /* word length d, 1 .. KL_MAX_DEPTH */
+  uint32_t width, height;  /* image size in pixels, 1 .. KL_MAX_IMAGE_SIDE */
+  double x0, x1, y0, y1;   /* window: x0 < x1, y0 < y1; pixel (row, col) covers
+                              [x0 + col/sx, x0 + (col+1)/sx) x (y1 - (row+1)/sy, y1 - row/sy],
+                              sx = width/(x1-x0), sy = height/(y1-y0); row 0 is the top */
+  uint32_t precision;      /* kl_precision */
+  uint32_t renorm_every;   /* prefix products are divided by sqrt(det) every this many
+                              letters (0 = never); 8 by default */
+  double parabolic_tol;    /* KL_MIXED: a prefix matrix P with
+                              |tr(P)^2 - 4 det P| < tol * max(1, |tr P|^2) is near-parabolic
+                              and its words are evaluated in FP64; default 1e-6 */
+  uint32_t prefix_len;     /* letters per cached prefix matrix (0 = choose) */
+  uint32_t accumulate;     /* 0: kl_render zeroes the image and counters first;
+                              1: it adds to them */
+} kl_params;
+
+/* Counters written by kl_render (uint64 each). */
+enum {
+  KL_CNT_IN_WINDOW = 0,    /* words drawn into the image */
+  KL_CNT_DROPPED = 1,      /* words outside the window or non-finite */
+  KL_CNT_FP64_WORDS = 2,   /* KL_MIXED: words evaluated on the FP64 path */
+  KL_CNT_ATOMICS = 3,      /* image atomics issued (after run-length merging) */
+  KL_N_COUNTERS = 4
+};
+
+/* Human-readable name of a status code (static string). */
+KL_API const char* kl_status_string(int status);
+
+/* Number of reduced words of length `depth`: 4 * 3^(depth-1); 0 when depth is
+ * 0 or above KL_MAX_DEPTH.  Sec. "Once-punctured torus groups": the pruned tree
+ * drops the children aA, Aa, bB, Bb, leaving three children per node. */
+KL_API uint64_t kl_word_count(uint32_t depth);
+
+/* Grandma's two-generator recipe (Mumford, Series, Wright, "Indra's Pearls",
+ * ch. 8; the paper cites the book for its groups): from tr a = ta and
+ * tr b = tb it builds a, b of determinant one with tr(a b a^-1 b^-1) = -2, and
+ * A, B as their inverses.  gens_out: 32 doubles (host).  Returns KL_EINVAL on a
+ * null pointer or non-finite trace, KL_EDEGENERATE if a denominator of the
+ * recipe vanishes.  Host only; needs no GPU. */
+KL_API int kl_grandma(double ta_re, double ta_im, double tb_re, double tb_im, double* gens_out);
+
+/* Seeds: the attracting fixed point of each generator (the orbit of a word
+ * starts at the fixed point of its first-applied letter; Sec. "Implementation"
+ * feeds fixed points as orbit starts).  Ties between the two fixed points
+ * (parabolic maps) take ((p - s) + sqrt((p - s)^2 + 4 q r)) / (2 r).  gens: 32
+ * doubles, seeds_out: 8 doubles (host).  KL_EDEGENERATE if a generator has no
+ * attracting finite fixed point.  Host only. */
+KL_API int kl_seeds(const double* gens, double* seeds_out);
+
+/* Fill *p: generators and seeds from the traces, the given depth, image and
+ * window, and defaults for the rest (precision KL_FP64, renorm_every 8,
+ * parabolic_tol 1e-6, prefix_len 0, accumulate 0).  Host only. */
+KL_API int kl_params_init(kl_params* p, double ta_re, double ta_im, double tb_re, double tb_im,
+                   uint32_t depth, uint32_t width, uint32_t height,
+                   double x0, double x1, double y0, double y1);
+
+/* Index decode (Sec. "The revised deterministic approach": words are pulled
+ * out of integers instead of being stored).  For each of the n indices in
+ * d_index, writes its `depth` letter codes to d_letters[t*depth .. t*depth +
+ * depth - 1] (w_1 first).  An index >= N_depth gets letters 0xFF.  Device
+ * pointers; asynchronous on `stream`. */
+KL_API int kl_decode_words(uint32_t depth, const uint64_t* d_index, uint64_t n, uint8_t* d_letters,
+                    void* stream);
+
+/* Bytes of device workspace kl_render and kl_eval_words need for *p
+ * (prefix-matrix and suffix-point tables).  0 on invalid parameters. */
+KL_API size_t kl_workspace_bytes(const kl_params* p);
+
+/* Word values, computed with exactly the arithmetic kl_render uses for *p (its
+ * precision, prefix length and tables), returned as pixel coordinates:
+ * d_uv[2t] = (Re z - x0) * sx, d_uv[2t+1] = (y1 - Im z) * sy (so that the pixel is
+ * (floor(d_uv[2t+1]), floor(d_uv[2t])) when inside).  Non-finite values are
+ * returned as NaN; an index >= N_d gives NaN.  d_workspace: at least
+ * kl_workspace_bytes(p) bytes, 256-byte aligned; it is overwritten.  Sec.
+ * "Introduction" (word value = last orbit element). */
+KL_API int kl_eval_words(const kl_params* p, const uint64_t* d_index, uint64_t n, double* d_uv,
+                  void* d_workspace, size_t workspace_bytes, void* stream);
+
+/* Render: every reduced word of length p->depth is decoded from its index,
+ * evaluated and counted into the pixel it falls in (Sec. "Implementation",
+ * "limit set" mode: words of length exactly d).  d_image: width*height uint32,
+ * row-major, row 0 at y1; counts wrap modulo 2^32.  d_counters: KL_N_COUNTERS
+ * uint64 (may be NULL).  Unless p->accumulate, the image and counters are
+ * zeroed first (on `stream`).  d_workspace as for kl_eval_words.  Words whose
+ * value is outside the window or not finite are dropped and counted. */
+KL_API int kl_render(const kl_params* p, uint32_t* d_image, uint64_t* d_counters, void* d_workspace,
+              size_t workspace_bytes, void* stream);
+
+/* Instrumentation: when set, kl_render records the CUDA events ev_start and
+ * ev_stop (cudaEvent_t, created by the caller) on its stream immediately
+ * before and after its main per-word kernel (the FP64 or mixed render
+ * kernel), so that the caller can time that kernel alone with
+ * cudaEventElapsedTime.  NULL, NULL switches it off.  The setting is global to
+ * the process and applies to every following kl_render call.  This is an
+ * addition of this library (the paper reports no timings); it changes no
+ * result. */
+KL_API int kl_set_profile_events(void* ev_start, void* ev_stop);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KL_H */

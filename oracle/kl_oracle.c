@@ -372,15 +372,18 @@ typedef struct {
   walk_t wt;
   sink_t sink;
   int* next_job;       /* shared */
-  int n_jobs;
+  int n_jobs;          /* one past the last job to run */
 } worker_arg_t;
 
-/* jobs: the 4*3*3 = 36 subtrees of the three innermost letters
- * (or fewer when d < 3) */
+/* jobs: the 4 * 3^(J-1) subtrees of the J = min(d, 5) innermost letters,
+ * all of equal size N_d / (4 * 3^(J-1)); job = x + 4 * (base-3 digits of the
+ * next J-1 letters' ranks, innermost first). */
+static int job_levels(int d) { return d < 5 ? d : 5; }
+
 static void run_job(worker_arg_t* a, int job) {
   const walk_t* t = &a->wt;
   int d = t->d;
-  int roots = d >= 3 ? 3 : d;
+  int roots = job_levels(d);
   int x = job % 4, j = job / 4;  /* innermost letter x = w_d */
   cx z = mobius(&t->g[x], t->seeds[x]);
   int level = 1, inner = x;
@@ -414,8 +417,17 @@ static void* worker(void* p) {
   return NULL;
 }
 
+/* Number of equal-size jobs of the tree walk at depth d. */
+OR_EXPORT int or_tree_jobs(int d) {
+  int j = 4;
+  for (int k = 1; k < job_levels(d); ++k) j *= 3;
+  return j;
+}
+
+/* Tree-walk render of the jobs [job0, job1) (all jobs: 0, or_tree_jobs(d)). */
 OR_EXPORT int or_render_tree(const double* gens, const double* seeds8, int d,
                              const double* window, int width, int height, int n_threads,
+                             int job0, int job1,
                              uint32_t* image, uint64_t* counters, double eta,
                              uint64_t* edge_idx, double* edge_uv, uint64_t edge_cap,
                              uint64_t* edge_count) {
@@ -426,8 +438,10 @@ OR_EXPORT int or_render_tree(const double* gens, const double* seeds8, int d,
   if (n_threads > 256) n_threads = 256;
   view_t v = make_view(window, width, height, eta);
   uint64_t dummy = 0;
-  int next_job = 0;
-  int n_jobs = d >= 3 ? 36 : (d == 2 ? 12 : 4);
+  int n_jobs = or_tree_jobs(d);
+  if (job0 < 0 || job1 > n_jobs || job0 > job1) return -1;
+  int next_job = job0;
+  n_jobs = job1;
   worker_arg_t* args = (worker_arg_t*)calloc((size_t)n_threads, sizeof(worker_arg_t));
   pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
   if (!args || !th) { free(args); free(th); return -1; }
@@ -451,5 +465,16 @@ OR_EXPORT int or_render_tree(const double* gens, const double* seeds8, int d,
     counters[1] += args[k].sink.dropped;
   }
   free(args); free(th);
+  return 0;
+}
+
+/* or_decode for n indices: out[t*d .. t*d + d - 1]; an index >= N_d gives
+ * letters 0xFF (and the call still returns 0). */
+OR_EXPORT int or_decode_many(int d, const uint64_t* idx, uint64_t n, uint8_t* out) {
+  if (or_word_count(d) == 0) return -1;
+  for (uint64_t t = 0; t < n; ++t) {
+    if (or_decode(d, idx[t], out + t * (uint64_t)d) != 0)
+      memset(out + t * (uint64_t)d, 0xFF, (size_t)d);
+  }
   return 0;
 }

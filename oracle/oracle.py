@@ -28,11 +28,15 @@ def lib():
         L.or_word_count.restype = U64
         L.or_decode.argtypes = [I, U64, P]
         L.or_decode.restype = I
+        L.or_decode_many.argtypes = [I, P, U64, P]
+        L.or_decode_many.restype = I
         L.or_eval.argtypes = [P, P, I, P, U64, P]
         L.or_eval.restype = I
         L.or_render_indexed.argtypes = [P, P, I, P, I, I, U64, U64, P, P, D, P, P, U64, P]
         L.or_render_indexed.restype = I
-        L.or_render_tree.argtypes = [P, P, I, P, I, I, I, P, P, D, P, P, U64, P]
+        L.or_render_tree.argtypes = [P, P, I, P, I, I, I, I, I, P, P, D, P, P, U64, P]
+        L.or_tree_jobs.argtypes = [I]
+        L.or_tree_jobs.restype = I
         L.or_render_tree.restype = I
         _lib = L
     return _lib
@@ -82,16 +86,15 @@ def word_count(d: int) -> int:
     return int(lib().or_word_count(d))
 
 
-def decode(d: int, indices) -> np.ndarray:
-    """Letter codes (n, d) uint8 of the given word indices."""
+def decode(d: int, indices, strict: bool = True) -> np.ndarray:
+    """Letter codes (n, d) uint8 of the given word indices.  An index outside
+    [0, N_d) raises (strict) or decodes to letters 0xFF."""
     idx = np.ascontiguousarray(indices, dtype=np.uint64).ravel()
     out = np.zeros((idx.size, d), dtype=np.uint8)
-    buf = np.zeros(d, dtype=np.uint8)
-    L = lib()
-    for t, i in enumerate(idx):
-        if L.or_decode(d, int(i), _ptr(buf)) != 0:
-            raise IndexError(f"index {int(i)} outside [0, N_{d})")
-        out[t] = buf
+    if lib().or_decode_many(d, _ptr(idx), idx.size, _ptr(out)) != 0:
+        raise IndexError(f"bad depth {d}")
+    if strict and idx.size and (out[:, 0] == 0xFF).any():
+        raise IndexError(f"index outside [0, N_{d})")
     return out
 
 
@@ -106,6 +109,11 @@ def evaluate(gens, seeds8, d: int, indices) -> np.ndarray:
     return out[0::2] + 1j * out[1::2]
 
 
+def tree_jobs(d: int) -> int:
+    """Number of equal-size jobs the tree walk splits depth d into."""
+    return int(lib().or_tree_jobs(d))
+
+
 @dataclass
 class Render:
     image: np.ndarray        # uint32 (H, W)
@@ -118,9 +126,11 @@ class Render:
 
 def render(gens, seeds8, d: int, window: Sequence[float], width: int, height: int,
            mode: str = "tree", threads: Optional[int] = None, eta: float = 0.0,
-           edge_cap: int = 1 << 16, i0: int = 0, i1: Optional[int] = None) -> Render:
+           edge_cap: int = 1 << 16, i0: int = 0, i1: Optional[int] = None,
+           jobs: Optional[Tuple[int, int]] = None) -> Render:
     """Hit image of all reduced words of length d (mode "tree": tree walk,
-    multi-threaded; mode "indexed": per word over [i0, i1), single thread).
+    multi-threaded, optionally only the equal-size jobs [j0, j1) of
+    ``tree_jobs(d)``; mode "indexed": per word over [i0, i1), single thread).
     Words whose pixel coordinates lie within ``eta`` pixels of a pixel edge are
     logged as edge words."""
     g = np.ascontiguousarray(gens, dtype=np.float64)
@@ -136,7 +146,8 @@ def render(gens, seeds8, d: int, window: Sequence[float], width: int, height: in
     if mode == "tree":
         if threads is None:
             threads = os.cpu_count() or 1
-        rc = L.or_render_tree(_ptr(g), _ptr(s), d, _ptr(win), width, height, threads,
+        j0, j1 = jobs if jobs is not None else (0, tree_jobs(d))
+        rc = L.or_render_tree(_ptr(g), _ptr(s), d, _ptr(win), width, height, threads, j0, j1,
                               _ptr(img), _ptr(cnt), eta, _ptr(eidx), _ptr(euv), cap, _ptr(ecount))
     elif mode == "indexed":
         n = word_count(d)

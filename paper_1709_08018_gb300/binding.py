@@ -1,0 +1,225 @@
+"""ctypes binding of ``include/kl.h`` (argument marshalling only)."""
+import ctypes
+import os
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libkl.so")
+
+FP64, MIXED = 0, 1
+KL_CNT_IN_WINDOW, KL_CNT_DROPPED, KL_CNT_FP64_WORDS, KL_CNT_ATOMICS, KL_N_COUNTERS = 0, 1, 2, 3, 4
+
+# Every function include/kl.h declares, in declaration order.
+API = ("kl_status_string", "kl_word_count", "kl_grandma", "kl_seeds", "kl_params_init",
+       "kl_decode_words", "kl_workspace_bytes", "kl_eval_words", "kl_render",
+       "kl_set_profile_events")
+
+
+class Params(ctypes.Structure):
+    """Mirror of ``kl_params``."""
+    _fields_ = [
+        ("gens", ctypes.c_double * 32),
+        ("seeds", ctypes.c_double * 8),
+        ("depth", ctypes.c_uint32),
+        ("width", ctypes.c_uint32),
+        ("height", ctypes.c_uint32),
+        ("x0", ctypes.c_double),
+        ("x1", ctypes.c_double),
+        ("y0", ctypes.c_double),
+        ("y1", ctypes.c_double),
+        ("precision", ctypes.c_uint32),
+        ("renorm_every", ctypes.c_uint32),
+        ("parabolic_tol", ctypes.c_double),
+        ("prefix_len", ctypes.c_uint32),
+        ("accumulate", ctypes.c_uint32),
+    ]
+
+
+class KlError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"CUDA library {LIB_PATH} is missing: build it with __graft_entry__.build() "
+                "(there is no fallback implementation)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, U32, U64, I, D, SZ = (ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int,
+                                  ctypes.c_double, ctypes.c_size_t)
+        L.kl_status_string.argtypes = [I]
+        L.kl_status_string.restype = ctypes.c_char_p
+        L.kl_word_count.argtypes = [U32]
+        L.kl_word_count.restype = U64
+        L.kl_grandma.argtypes = [D, D, D, D, P]
+        L.kl_grandma.restype = I
+        L.kl_seeds.argtypes = [P, P]
+        L.kl_seeds.restype = I
+        L.kl_params_init.argtypes = [ctypes.POINTER(Params), D, D, D, D, U32, U32, U32, D, D, D, D]
+        L.kl_params_init.restype = I
+        L.kl_decode_words.argtypes = [U32, P, U64, P, P]
+        L.kl_decode_words.restype = I
+        L.kl_workspace_bytes.argtypes = [ctypes.POINTER(Params)]
+        L.kl_workspace_bytes.restype = SZ
+        L.kl_eval_words.argtypes = [ctypes.POINTER(Params), P, U64, P, P, SZ, P]
+        L.kl_eval_words.restype = I
+        L.kl_render.argtypes = [ctypes.POINTER(Params), P, P, P, SZ, P]
+        L.kl_render.restype = I
+        L.kl_set_profile_events.argtypes = [P, P]
+        L.kl_set_profile_events.restype = I
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> Tuple[str, ...]:
+    """Names of API that the loaded library exports."""
+    L = lib()
+    return tuple(n for n in API if hasattr(L, n))
+
+
+def status_string(status: int) -> str:
+    return lib().kl_status_string(status).decode()
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise KlError(status, what)
+
+
+def word_count(depth: int) -> int:
+    return int(lib().kl_word_count(depth))
+
+
+def grandma(ta: complex, tb: complex) -> np.ndarray:
+    out = np.zeros(32, dtype=np.float64)
+    _check(lib().kl_grandma(ta.real, ta.imag, tb.real, tb.imag, out.ctypes.data), "kl_grandma")
+    return out
+
+
+def seeds(gens) -> np.ndarray:
+    g = np.ascontiguousarray(gens, dtype=np.float64)
+    out = np.zeros(8, dtype=np.float64)
+    _check(lib().kl_seeds(g.ctypes.data, out.ctypes.data), "kl_seeds")
+    return out
+
+
+def params_init(ta: complex, tb: complex, depth: int, width: int, height: int,
+                window: Sequence[float], precision: int = FP64, **fields) -> Params:
+    p = Params()
+    x0, x1, y0, y1 = window
+    _check(lib().kl_params_init(ctypes.byref(p), ta.real, ta.imag, tb.real, tb.imag, depth,
+                                width, height, x0, x1, y0, y1), "kl_params_init")
+    p.precision = precision
+    for k, v in fields.items():
+        setattr(p, k, v)
+    return p
+
+
+def workspace_bytes(p: Params) -> int:
+    return int(lib().kl_workspace_bytes(ctypes.byref(p)))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _index_ptr(index):
+    torch = _torch()
+    if not index.is_cuda or not index.is_contiguous():
+        raise ValueError("indices must be a contiguous CUDA tensor")
+    if index.dtype not in (torch.int64, getattr(torch, "uint64", torch.int64)):
+        raise ValueError("indices must be int64 or uint64")
+    return index.data_ptr()
+
+
+def decode_words(depth: int, index, stream=None):
+    """Letters (n, depth) uint8 of a CUDA tensor of word indices."""
+    torch = _torch()
+    n = index.numel()
+    out = torch.empty((n, depth), dtype=torch.uint8, device=index.device)
+    _check(lib().kl_decode_words(depth, _index_ptr(index), n, out.data_ptr(),
+                                 _stream_handle(stream)), "kl_decode_words")
+    return out
+
+
+def _workspace(p: Params, device, workspace=None):
+    """The caller's workspace as given (the library checks its size and
+    alignment), or a new one of kl_workspace_bytes(p) bytes."""
+    if workspace is not None:
+        return workspace
+    need = workspace_bytes(p)
+    if need == 0:
+        raise KlError(1, "kl_workspace_bytes")
+    return _torch().empty(need, dtype=torch_uint8(), device=device)
+
+
+def torch_uint8():
+    return _torch().uint8
+
+
+def eval_words(p: Params, index, workspace=None, stream=None):
+    """Pixel coordinates (n, 2) float64 of the given words, computed exactly as
+    kl_render computes them."""
+    torch = _torch()
+    n = index.numel()
+    ws = _workspace(p, index.device, workspace)
+    out = torch.empty((n, 2), dtype=torch.float64, device=index.device)
+    _check(lib().kl_eval_words(ctypes.byref(p), _index_ptr(index), n, out.data_ptr(),
+                               ws.data_ptr(), ws.numel(), _stream_handle(stream)),
+           "kl_eval_words")
+    return out
+
+
+def render(p: Params, image=None, counters=None, workspace=None, stream=None, device="cuda"):
+    """Render into a (height, width) uint32 CUDA image; returns (image, counters)."""
+    torch = _torch()
+    if image is None:
+        image = torch.empty((p.height, p.width), dtype=torch.int32, device=device)
+    if counters is None:
+        counters = torch.zeros(KL_N_COUNTERS, dtype=torch.int64, device=image.device)
+    if image.numel() != p.width * p.height or image.element_size() != 4 or not image.is_cuda:
+        raise ValueError("image must be a CUDA tensor of width*height 32-bit elements")
+    ws = _workspace(p, image.device, workspace)
+    _check(lib().kl_render(ctypes.byref(p), image.data_ptr(), counters.data_ptr(), ws.data_ptr(),
+                           ws.numel(), _stream_handle(stream)), "kl_render")
+    return image, counters
+
+
+def set_profile_events(start=None, stop=None):
+    """Record two torch.cuda.Event objects (already recorded once, so that
+    they exist) around the main per-word kernel of every following render;
+    no arguments switches it off."""
+    a = start.cuda_event if start is not None else None
+    b = stop.cuda_event if stop is not None else None
+    _check(lib().kl_set_profile_events(a, b), "kl_set_profile_events")
+
+
+class Renderer:
+    """Holds parameters, workspace, image and counters for repeated renders."""
+
+    def __init__(self, p: Params, device="cuda"):
+        torch = _torch()
+        self.p = p
+        self.image = torch.empty((p.height, p.width), dtype=torch.int32, device=device)
+        self.counters = torch.zeros(KL_N_COUNTERS, dtype=torch.int64, device=device)
+        self.workspace = _workspace(p, device)
+
+    def __call__(self, stream=None):
+        return render(self.p, self.image, self.counters, self.workspace, stream)

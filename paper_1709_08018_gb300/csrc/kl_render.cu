@@ -1,0 +1,948 @@
+// Device side of the indexed limit-set renderer (sm_103a).
+//
+// A reduced word w_1 .. w_d is split into a prefix w_1 .. w_p (the letters
+// applied last) and a suffix w_{p+1} .. w_d (applied first, starting from the
+// seed of w_d).  Its value is P(v): P = M_{w_1} ... M_{w_p} is the prefix
+// matrix and v the suffix point.  The index of the word factors the same
+// way: i = (prefix index) * 3^s + (suffix digits), so instead of decoding i
+// digit by digit for every word, the kernels decode each prefix once (a
+// table of prefix constants) and each suffix once (a table of suffix points)
+// and enumerate the compatible pairs (suffix first letter != inverse of the
+// prefix last letter, Sec. "Once-punctured torus groups").
+//
+// Per word the only work left is one linear-fractional map and a splat.  With
+// det P = D the map is written in pole form
+//     P(v) = alpha + beta / (v + gamma),
+//     alpha = P00/P10, gamma = P11/P10, beta = -D/P10^2,
+// and folded into pixel units, u = (Re z - x0) sx = ax + (c1 wr + c2 wi)/|w|^2,
+// row coordinate v = (y1 - Im z) sy = ay + (c3 wr + c4 wi)/|w|^2, w = v + gamma:
+// 13 FP64 operations and one reciprocal seed per word.  Pixel binning uses
+// only integer operations on the high word of the coordinates.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "kl.h"
+
+namespace {
+
+constexpr int kMaxPrefix = 15;
+constexpr int kMaxSuffix = 9;
+constexpr int kMaxRenderDepth = kMaxPrefix + kMaxSuffix;
+constexpr int kThreads = 128;
+
+// Prefix flags.
+constexpr uint32_t kDirect = 1u;     // P10 ~ 0: pole form invalid, use the direct map
+constexpr uint32_t kNearPar = 2u;    // |tr^2 - 4 det| small: near-parabolic (cusp) prefix
+constexpr uint32_t kWide = 4u;       // local FP32 frame unsafe (far or huge offsets)
+constexpr uint32_t kFallback = 8u;   // KL_MIXED: words of this prefix run in FP64
+
+struct Plan {
+  int d, p, s;
+  int q;         // letters of the prefix tail table (the rest, p - q, in the head table)
+  int so, si;    // letters of the suffix head (matrix) and tail (point) tables
+  uint32_t np;   // prefix slots per last letter: 3^(p-1)
+  uint32_t ns;   // suffix points per first letter: 3^(s-1)
+  uint32_t p3_q1, p3_pq, p3_so1, p3_si, p3_si1;  // 3^(q-1), 3^(p-q), 3^(so-1), 3^si, 3^(si-1)
+  size_t off_pre64, off_pre32, off_flags, off_suf64, off_suf32, off_fb, off_fbcount;
+  size_t off_L, off_H, off_So, off_Si, total;
+};
+
+struct View {
+  double x0, y1, sx, sy;
+  uint32_t W, H;
+  uint32_t hiW, hiH;  // high words of (double)W and (double)H
+};
+
+struct Group {
+  double g[32];
+  double seed[8];
+};
+
+struct __align__(16) Pre64 {
+  double gr, gi, ax, ay, c1, c2, c3, c4;  // pole form; or P00..P11 (re, im) if kDirect
+};
+
+struct __align__(16) Pre32 {
+  float gr, gi, axf, ayf, c1, c2, c3, c4;
+  int axi, ayi, pad0, pad1;
+};
+
+struct dc {
+  double re, im;
+};
+
+__device__ __forceinline__ dc cadd(dc a, dc b) { return {a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ dc csub(dc a, dc b) { return {a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ dc cmul(dc a, dc b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+__device__ __forceinline__ dc cdiv(dc n, dc m) {
+  double den = m.re * m.re + m.im * m.im;
+  return {(n.re * m.re + n.im * m.im) / den, (n.im * m.re - n.re * m.im) / den};
+}
+__device__ __forceinline__ double cabs1(dc a) { return fabs(a.re) + fabs(a.im); }
+// principal square root
+__device__ __forceinline__ dc csqrt(dc a) {
+  double r = hypot(a.re, a.im);
+  if (r == 0.0) return {0.0, 0.0};
+  double t = sqrt(0.5 * (r + fabs(a.re)));
+  if (a.re >= 0.0) return {t, a.im / (2.0 * t)};
+  return {fabs(a.im) / (2.0 * t), copysign(t, a.im)};
+}
+
+struct M2 {
+  dc p, q, r, s;
+};
+
+__device__ __forceinline__ M2 load_gen(const Group& G, int x) {
+  const double* g = G.g + 8 * x;
+  return {{g[0], g[1]}, {g[2], g[3]}, {g[4], g[5]}, {g[6], g[7]}};
+}
+__device__ __forceinline__ M2 mmul(const M2& a, const M2& b) {
+  return {cadd(cmul(a.p, b.p), cmul(a.q, b.r)), cadd(cmul(a.p, b.q), cmul(a.q, b.s)),
+          cadd(cmul(a.r, b.p), cmul(a.s, b.r)), cadd(cmul(a.r, b.q), cmul(a.s, b.s))};
+}
+__device__ __forceinline__ dc mdet(const M2& a) { return csub(cmul(a.p, a.s), cmul(a.q, a.r)); }
+__device__ __forceinline__ void renormalise(M2& a) {
+  dc k = csqrt(mdet(a));
+  if (k.re == 0.0 && k.im == 0.0) return;
+  a.p = cdiv(a.p, k); a.q = cdiv(a.q, k); a.r = cdiv(a.r, k); a.s = cdiv(a.s, k);
+}
+__device__ __forceinline__ dc mobius(const M2& m, dc z) {
+  return cdiv(cadd(cmul(m.p, z), m.q), cadd(cmul(m.r, z), m.s));
+}
+
+// ---------------------------------------------------------------------------
+// per-word arithmetic, shared by the render kernels and the evaluation kernel
+
+// FP64 reciprocal: hardware seed (rcp.approx.ftz.f64) refined by one cubic
+// Newton-Raphson step y <- y (1 + e + e^2), e = 1 - m y (Householder order 3).
+__device__ __forceinline__ double rcp64(double m) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(m));
+  double e = __fma_rn(-m, y, 1.0);
+  double e2 = __fma_rn(e, e, e);
+  return __fma_rn(y, e2, y);
+}
+
+__device__ __forceinline__ float rcp32(float m) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(m));
+  return y;
+}
+
+__device__ __forceinline__ void uv_pole64(const Pre64& c, double vr, double vi, double& u,
+                                          double& v) {
+  double wr = __dadd_rn(vr, c.gr);
+  double wi = __dadd_rn(vi, c.gi);
+  double m = __fma_rn(wr, wr, __dmul_rn(wi, wi));
+  double r = rcp64(m);
+  double tx = __fma_rn(c.c1, wr, __dmul_rn(c.c2, wi));
+  double ty = __fma_rn(c.c3, wr, __dmul_rn(c.c4, wi));
+  u = __fma_rn(tx, r, c.ax);
+  v = __fma_rn(ty, r, c.ay);
+}
+
+// Direct form for prefixes whose P10 vanishes: z = (P00 v + P01)/(P10 v + P11).
+__device__ __forceinline__ void uv_direct64(const Pre64& c, double vr, double vi,
+                                            const View& V, double& u, double& v) {
+  dc P00 = {c.gr, c.gi}, P01 = {c.ax, c.ay}, P10 = {c.c1, c.c2}, P11 = {c.c3, c.c4};
+  dc z = {vr, vi};
+  dc w = cdiv(cadd(cmul(P00, z), P01), cadd(cmul(P10, z), P11));
+  u = (w.re - V.x0) * V.sx;
+  v = (V.y1 - w.im) * V.sy;
+}
+
+__device__ __forceinline__ void uv_pole32(const Pre32& c, float vr, float vi, float& uf,
+                                          float& vf) {
+  float wr = __fadd_rn(vr, c.gr);
+  float wi = __fadd_rn(vi, c.gi);
+  float m = __fmaf_rn(wr, wr, __fmul_rn(wi, wi));
+  float r = rcp32(m);
+  float tx = __fmaf_rn(c.c1, wr, __fmul_rn(c.c2, wi));
+  float ty = __fmaf_rn(c.c3, wr, __fmul_rn(c.c4, wi));
+  uf = __fmaf_rn(tx, r, c.axf);
+  vf = __fmaf_rn(ty, r, c.ayf);
+}
+
+// floor of a double in [0, 2^20) from its high word alone
+__device__ __forceinline__ uint32_t floor_hi(uint32_t h) {
+  int e = (int)(h >> 20) - 1023;
+  uint32_t mant = (h & 0xFFFFFu) | 0x100000u;
+  return e < 0 ? 0u : (mant >> (20 - e));
+}
+
+// Pixel id (row * W + col) of pixel coordinates (u, v), or -1 if outside
+// [0, W) x [0, H) or not finite.  For u >= 0, u < W iff hi(u) < hi(W) because
+// the low word of an integer below 2^20 is zero; negative values, infinities
+// and NaNs all have high words above hi(W).
+__device__ __forceinline__ int pixel64(double u, double v, const View& V) {
+  uint32_t hu = (uint32_t)__double2hiint(u);
+  uint32_t hv = (uint32_t)__double2hiint(v);
+  if (hu >= V.hiW || hv >= V.hiH) return -1;
+  return (int)(floor_hi(hv) * V.W + floor_hi(hu));
+}
+
+// Pixel id of a local-frame FP32 coordinate pair: col = axi + floor(uf).
+// floor(uf) for |uf| < 2^22 via the 1.5 * 2^23 rounding shift in
+// round-toward-minus-infinity; larger |uf| (and NaN, inf) are outside.
+__device__ __forceinline__ int floor_f32(float t) {
+  return __float_as_int(__fadd_rd(t, 12582912.0f)) - 0x4B400000;
+}
+__device__ __forceinline__ int pixel32(float uf, float vf, const Pre32& c, const View& V) {
+  uint32_t au = __float_as_uint(uf) & 0x7FFFFFFFu;
+  uint32_t av = __float_as_uint(vf) & 0x7FFFFFFFu;
+  int col = c.axi + floor_f32(uf);
+  int row = c.ayi + floor_f32(vf);
+  bool ok = (au < 0x4A800000u) & (av < 0x4A800000u) & ((uint32_t)col < V.W) &
+            ((uint32_t)row < V.H);
+  return ok ? row * (int)V.W + col : -1;
+}
+
+// ---------------------------------------------------------------------------
+// tables
+
+__device__ __forceinline__ int allowed_letter(int digit, int ban) {
+  return digit + (digit >= ban ? 1 : 0);
+}
+
+// Tables are built in two launches.  parts_kernel builds four small tables:
+//   L: prefix tails, the q innermost prefix letters w_{p-q+1} .. w_p, as a
+//      matrix, slot (x = w_p, base-3 ranks of w_{p-1} .. w_{p-q+1});
+//   H: prefix heads w_1 .. w_{p-q}, slot (y = the letter right of the head,
+//      base-3 ranks of w_{p-q} .. w_1);
+//   So: suffix heads w_{p+1} .. w_{p+so} as a matrix, slot (u = w_{p+1}, ranks);
+//   Si: suffix tails w_{p+so+1} .. w_d applied to the seed of w_d, one map at a
+//      time, slot (z = w_{p+so+1}, ranks).
+// combine_kernel then forms every prefix matrix P = H L (one 2x2 product) and
+// its pole-form constants, and every suffix point v = So(Si) (one map).  Each
+// L, H and So matrix is renormalised to det 1 every `renorm` letters and at
+// its end; P is not renormalised (its determinant enters beta explicitly).
+// The slot numbering is the same as for a single-level decode: a prefix slot
+// (x, r) has r = r_L 3^(p-q) + r_H, a suffix slot (u, j) has
+// j = j_So 3^si + rank(z) 3^(si-1) + j_Si.
+
+struct __align__(16) PartM {
+  M2 m;
+  int edge;  // L: its outermost letter w_{p-q+1}; So: its innermost letter w_{p+so}
+  int pad[3];
+};
+
+__device__ __forceinline__ M2 identity2() {
+  return {{1.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {1.0, 0.0}};
+}
+
+__global__ void parts_kernel(Group G, Plan L, int renorm, PartM* __restrict__ Lt,
+                             M2* __restrict__ Ht, PartM* __restrict__ Sot,
+                             double2* __restrict__ Sit) {
+  const uint32_t nL = 4u * L.p3_q1, nH = L.p > L.q ? 4u * L.p3_pq : 0u;
+  const uint32_t nSo = L.so > 0 ? 4u * L.p3_so1 : 0u, nSi = 4u * L.p3_si1;
+  const uint32_t total = nL + nH + nSo + nSi;
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += gridDim.x * blockDim.x) {
+    if (idx < nL + nH) {
+      // prefix part: letters taken right to left, matrix built by prepending
+      const bool tail = idx < nL;
+      const uint32_t slot = tail ? idx : idx - nL;
+      const uint32_t per = tail ? L.p3_q1 : L.p3_pq;
+      const int first = (int)(slot / per);
+      const uint32_t r = slot % per;
+      const int nlet = tail ? L.q - 1 : L.p - L.q;  // letters chosen by digits
+      M2 P = tail ? load_gen(G, first) : identity2();
+      int right = first;
+      uint32_t place = per / 3u;
+      int used = tail ? 1 : 0;
+      for (int k = 0; k < nlet; ++k) {
+        const int digit = (int)((r / place) % 3u);
+        place /= 3u;
+        const int w = allowed_letter(digit, (right + 2) & 3);
+        P = mmul(load_gen(G, w), P);
+        right = w;
+        if (renorm > 0 && (++used % renorm) == 0) renormalise(P);
+      }
+      if (renorm > 0 && (used % renorm) != 0) renormalise(P);
+      if (tail) {
+        PartM e;
+        e.m = P;
+        e.edge = right;
+        e.pad[0] = e.pad[1] = e.pad[2] = 0;
+        Lt[slot] = e;
+      } else {
+        Ht[slot] = P;
+      }
+    } else if (idx < nL + nH + nSo) {
+      // suffix head: letters left to right, matrix built by appending
+      const uint32_t slot = idx - nL - nH;
+      const int u = (int)(slot / L.p3_so1);
+      const uint32_t j = slot % L.p3_so1;
+      M2 S = load_gen(G, u);
+      int left = u, used = 1;
+      uint32_t place = L.p3_so1 / 3u;
+      for (int k = 1; k < L.so; ++k) {
+        const int digit = (int)((j / place) % 3u);
+        place /= 3u;
+        const int w = allowed_letter(digit, (left + 2) & 3);
+        S = mmul(S, load_gen(G, w));
+        left = w;
+        if (renorm > 0 && (++used % renorm) == 0) renormalise(S);
+      }
+      if (renorm > 0 && (used % renorm) != 0) renormalise(S);
+      PartM e;
+      e.m = S;
+      e.edge = left;
+      e.pad[0] = e.pad[1] = e.pad[2] = 0;
+      Sot[slot] = e;
+    } else {
+      // suffix tail: the orbit of the seed of w_d, innermost letter first
+      const uint32_t slot = idx - nL - nH - nSo;
+      int w[kMaxSuffix];
+      w[0] = (int)(slot / L.p3_si1);
+      const uint32_t j = slot % L.p3_si1;
+      uint32_t place = L.p3_si1 / 3u;
+      for (int k = 1; k < L.si; ++k) {
+        const int digit = (int)((j / place) % 3u);
+        place /= 3u;
+        w[k] = allowed_letter(digit, (w[k - 1] + 2) & 3);
+      }
+      const int last = w[L.si - 1];
+      dc z = {G.seed[2 * last], G.seed[2 * last + 1]};
+      for (int k = L.si - 1; k >= 0; --k) z = mobius(load_gen(G, w[k]), z);
+      Sit[slot] = make_double2(z.re, z.im);
+    }
+  }
+}
+
+__global__ void combine_kernel(View V, Plan L, double ptol, int mixed,
+                               const PartM* __restrict__ Lt, const M2* __restrict__ Ht,
+                               const PartM* __restrict__ Sot, const double2* __restrict__ Sit,
+                               Pre64* __restrict__ pre64, Pre32* __restrict__ pre32,
+                               uint32_t* __restrict__ flags, uint32_t* __restrict__ fb_list,
+                               uint32_t* __restrict__ fb_count, double2* __restrict__ suf64,
+                               float2* __restrict__ suf32) {
+  const uint32_t nP = 4u * L.np, nS = 4u * L.ns;
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nP + nS;
+       idx += gridDim.x * blockDim.x) {
+    if (idx >= nP) {
+      const uint32_t slot = idx - nP;
+      double2 v;
+      if (L.so == 0) {
+        v = Sit[slot];
+      } else {
+        const int u = (int)(slot / L.ns);
+        const uint32_t j = slot % L.ns;
+        const uint32_t j_so = j / L.p3_si, rem = j % L.p3_si;
+        const PartM& S = Sot[(uint32_t)u * L.p3_so1 + j_so];
+        const int z = allowed_letter((int)(rem / L.p3_si1), (S.edge + 2) & 3);
+        const double2 t = Sit[(uint32_t)z * L.p3_si1 + rem % L.p3_si1];
+        const dc r = mobius(S.m, {t.x, t.y});
+        v = make_double2(r.re, r.im);
+      }
+      suf64[slot] = v;
+      suf32[slot] = make_float2((float)v.x, (float)v.y);
+      continue;
+    }
+    const uint32_t slot = idx;
+    const int x = (int)(slot / L.np);
+    const uint32_t r = slot % L.np;
+    const PartM& T = Lt[(uint32_t)x * L.p3_q1 + r / L.p3_pq];
+    const M2 P = L.p > L.q ? mmul(Ht[(uint32_t)T.edge * L.p3_pq + r % L.p3_pq], T.m) : T.m;
+    const dc det = mdet(P);
+    const dc tr = cadd(P.p, P.s);
+    const double scale = fmax(fmax(cabs1(P.p), cabs1(P.q)), fmax(cabs1(P.r), cabs1(P.s)));
+    uint32_t fl = 0;
+    const dc tr2m4 = csub(cmul(tr, tr), {4.0 * det.re, 4.0 * det.im});
+    const double t2 = tr.re * tr.re + tr.im * tr.im;
+    if (hypot(tr2m4.re, tr2m4.im) < ptol * fmax(1.0, t2)) fl |= kNearPar;
+    Pre64 c64;
+    Pre32 c32;
+    if (!(cabs1(P.r) > 1e-12 * scale)) {
+      fl |= kDirect;
+      c64 = {P.p.re, P.p.im, P.q.re, P.q.im, P.r.re, P.r.im, P.s.re, P.s.im};
+      c32 = {};
+    } else {
+      const dc inv10 = cdiv({1.0, 0.0}, P.r);
+      const dc alpha = cmul(P.p, inv10);
+      const dc gamma = cmul(P.s, inv10);
+      const dc mbeta = cmul(det, cmul(inv10, inv10));  // -beta
+      const double ax = (alpha.re - V.x0) * V.sx;
+      const double ay = (V.y1 - alpha.im) * V.sy;
+      const double c1 = -V.sx * mbeta.re, c2 = -V.sx * mbeta.im;
+      const double c3 = V.sy * mbeta.im, c4 = -V.sy * mbeta.re;
+      c64 = {gamma.re, gamma.im, ax, ay, c1, c2, c3, c4};
+      const double lim = 1048576.0;  // 2^20
+      if (!(fabs(ax) < lim && fabs(ay) < lim && fabs(gamma.re) < 1e15 && fabs(gamma.im) < 1e15))
+        fl |= kWide;
+      const double axi = floor(fmax(fmin(ax, lim), -lim));
+      const double ayi = floor(fmax(fmin(ay, lim), -lim));
+      c32.gr = (float)gamma.re;
+      c32.gi = (float)gamma.im;
+      c32.axf = (float)(ax - axi);
+      c32.ayf = (float)(ay - ayi);
+      c32.c1 = (float)c1;
+      c32.c2 = (float)c2;
+      c32.c3 = (float)c3;
+      c32.c4 = (float)c4;
+      c32.axi = (int)axi;
+      c32.ayi = (int)ayi;
+      c32.pad0 = c32.pad1 = 0;
+    }
+    if (mixed && (fl & (kDirect | kNearPar | kWide))) {
+      fl |= kFallback;
+      const uint32_t k = atomicAdd(fb_count, 1u);
+      fb_list[k] = slot;
+    }
+    pre64[slot] = c64;
+    pre32[slot] = c32;
+    flags[slot] = fl;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// splat helpers
+
+struct Tally {
+  uint32_t in_window = 0, words = 0, atomics = 0;
+  int cur = -1;
+  uint32_t run = 0;
+
+  __device__ __forceinline__ void add(int pix, uint32_t* __restrict__ img) {
+    ++words;
+    if (pix != cur) {
+      if (cur >= 0) {
+        atomicAdd(img + cur, run);
+        ++atomics;
+      }
+      cur = pix;
+      run = 0;
+    }
+    ++run;
+    in_window += (pix >= 0);
+  }
+  __device__ __forceinline__ void flush(uint32_t* __restrict__ img) {
+    if (cur >= 0 && run) {
+      atomicAdd(img + cur, run);
+      ++atomics;
+    }
+    cur = -1;
+    run = 0;
+  }
+};
+
+__device__ __forceinline__ void publish(const Tally& t, uint32_t fp64_words,
+                                        unsigned long long* counters) {
+  unsigned long long a = t.in_window, b = t.words - t.in_window, c = fp64_words, e = t.atomics;
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xFFFFFFFFu, a, o);
+    b += __shfl_down_sync(0xFFFFFFFFu, b, o);
+    c += __shfl_down_sync(0xFFFFFFFFu, c, o);
+    e += __shfl_down_sync(0xFFFFFFFFu, e, o);
+  }
+  if ((threadIdx.x & 31) == 0 && counters) {
+    if (a) atomicAdd(counters + KL_CNT_IN_WINDOW, a);
+    if (b) atomicAdd(counters + KL_CNT_DROPPED, b);
+    if (c) atomicAdd(counters + KL_CNT_FP64_WORDS, c);
+    if (e) atomicAdd(counters + KL_CNT_ATOMICS, e);
+  }
+}
+
+// blockIdx.y = 3 * x + k enumerates the 12 compatible (prefix last letter x,
+// suffix first letter u) pairs: u is the k-th letter other than inv(x).
+__device__ __forceinline__ void pair_of(int q, int& x, int& u) {
+  x = q / 3;
+  u = allowed_letter(q % 3, (x + 2) & 3);
+}
+
+// ---------------------------------------------------------------------------
+// render kernels
+
+// FP64: thread = one prefix slot of last letter x, looping over the suffix
+// points of first letter u held in shared memory (all lanes read the same
+// point: a broadcast).  Consecutive suffix points differ in their innermost
+// letters, so consecutive words usually land in the same pixel; the tally
+// merges such runs into one atomic.
+__global__ void __launch_bounds__(kThreads) render64_kernel(
+    const Pre64* __restrict__ pre, const uint32_t* __restrict__ flags,
+    const double2* __restrict__ suf, Plan L, View V, uint32_t* __restrict__ img,
+    unsigned long long* counters) {
+  extern __shared__ double2 s_suf64[];
+  int x, u;
+  pair_of(blockIdx.y, x, u);
+  const double2* src = suf + (size_t)u * L.ns;
+  for (uint32_t t = threadIdx.x; t < L.ns; t += blockDim.x) s_suf64[t] = src[t];
+  __syncthreads();
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  Tally t;
+  if (r < L.np) {
+    const uint32_t slot = (uint32_t)x * L.np + r;
+    const Pre64 c = pre[slot];
+    if (flags[slot] & kDirect) {
+      for (uint32_t j = 0; j < L.ns; ++j) {
+        double uu, vv;
+        const double2 s = s_suf64[j];
+        uv_direct64(c, s.x, s.y, V, uu, vv);
+        t.add(pixel64(uu, vv, V), img);
+      }
+    } else {
+#pragma unroll 4
+      for (uint32_t j = 0; j < L.ns; ++j) {
+        double uu, vv;
+        const double2 s = s_suf64[j];
+        uv_pole64(c, s.x, s.y, uu, vv);
+        t.add(pixel64(uu, vv, V), img);
+      }
+    }
+    t.flush(img);
+  }
+  publish(t, 0, counters);
+}
+
+// Mixed: as render64_kernel with the per-word map in FP32 in the prefix's
+// local frame; prefixes flagged kFallback are skipped here and rendered by
+// fallback64_kernel.
+__global__ void __launch_bounds__(kThreads) render32_kernel(
+    const Pre32* __restrict__ pre, const uint32_t* __restrict__ flags,
+    const float2* __restrict__ suf, Plan L, View V, uint32_t* __restrict__ img,
+    unsigned long long* counters) {
+  extern __shared__ float2 s_suf32[];
+  int x, u;
+  pair_of(blockIdx.y, x, u);
+  const float2* src = suf + (size_t)u * L.ns;
+  for (uint32_t t = threadIdx.x; t < L.ns; t += blockDim.x) s_suf32[t] = src[t];
+  __syncthreads();
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  Tally t;
+  if (r < L.np) {
+    const uint32_t slot = (uint32_t)x * L.np + r;
+    if (!(flags[slot] & kFallback)) {
+      const Pre32 c = pre[slot];
+#pragma unroll 4
+      for (uint32_t j = 0; j < L.ns; ++j) {
+        float uf, vf;
+        const float2 s = s_suf32[j];
+        uv_pole32(c, s.x, s.y, uf, vf);
+        t.add(pixel32(uf, vf, c, V), img);
+      }
+      t.flush(img);
+    }
+  }
+  publish(t, 0, counters);
+}
+
+// Mixed-mode FP64 fallback: work item = (fallback prefix, one of its three
+// compatible suffix letters, a chunk of kFbChunk suffix points); grid-stride
+// over items, the prefix count read on the device.
+constexpr uint32_t kFbChunk = 64;
+
+__global__ void __launch_bounds__(kThreads) fallback64_kernel(
+    const Pre64* __restrict__ pre, const uint32_t* __restrict__ flags,
+    const uint32_t* __restrict__ fb_list, const uint32_t* __restrict__ fb_count,
+    const double2* __restrict__ suf, Plan L, View V, uint32_t* __restrict__ img,
+    unsigned long long* counters) {
+  const uint32_t chunks = (L.ns + kFbChunk - 1) / kFbChunk;
+  const uint32_t per_prefix = 3u * chunks;
+  const uint64_t items = (uint64_t)per_prefix * (*fb_count);
+  Tally t;
+  uint32_t fp64_words = 0;
+  for (uint64_t it = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; it < items;
+       it += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t slot = fb_list[it / per_prefix];
+    const uint32_t rem = (uint32_t)(it % per_prefix);
+    const int x = (int)(slot / L.np);
+    const int u = allowed_letter((int)(rem / chunks), (x + 2) & 3);
+    const uint32_t j0 = (rem % chunks) * kFbChunk;
+    const uint32_t j1 = min(L.ns, j0 + kFbChunk);
+    const Pre64 c = pre[slot];
+    const bool direct = flags[slot] & kDirect;
+    const double2* src = suf + (size_t)u * L.ns;
+    for (uint32_t j = j0; j < j1; ++j) {
+      double uu, vv;
+      const double2 s = src[j];
+      if (direct)
+        uv_direct64(c, s.x, s.y, V, uu, vv);
+      else
+        uv_pole64(c, s.x, s.y, uu, vv);
+      t.add(pixel64(uu, vv, V), img);
+    }
+    t.flush(img);
+    fp64_words += j1 - j0;
+  }
+  publish(t, fp64_words, counters);
+}
+
+// ---------------------------------------------------------------------------
+// decode, sequential words (d = 1) and evaluation
+
+__device__ __forceinline__ void decode_word(uint64_t i, int d, int* w) {
+  for (int k = d - 1; k >= 1; --k) {
+    w[k] = (int)(i % 3u);
+    i /= 3u;
+  }
+  w[0] = (int)i;
+  for (int k = 1; k < d; ++k) w[k] = allowed_letter(w[k], (w[k - 1] + 2) & 3);
+}
+
+__global__ void decode_kernel(const uint64_t* __restrict__ idx, uint64_t n, int d, uint64_t N,
+                              uint8_t* __restrict__ out) {
+  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n;
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i = idx[t];
+    uint8_t* o = out + t * (uint64_t)d;
+    if (i >= N) {
+      for (int k = 0; k < d; ++k) o[k] = 0xFF;
+      continue;
+    }
+    int w[KL_MAX_DEPTH];
+    decode_word(i, d, w);
+    for (int k = 0; k < d; ++k) o[k] = (uint8_t)w[k];
+  }
+}
+
+// Words of length 1: the map of the letter applied to its own seed.
+__global__ void render_single_letter_kernel(Group G, View V, uint32_t* img,
+                                            unsigned long long* counters) {
+  const int x = threadIdx.x;
+  if (x >= 4) return;
+  dc z = mobius(load_gen(G, x), {G.seed[2 * x], G.seed[2 * x + 1]});
+  const int pix = pixel64((z.re - V.x0) * V.sx, (V.y1 - z.im) * V.sy, V);
+  if (pix >= 0) atomicAdd(img + pix, 1u);
+  if (counters) {
+    atomicAdd(counters + (pix >= 0 ? KL_CNT_IN_WINDOW : KL_CNT_DROPPED), 1ull);
+    if (pix >= 0) atomicAdd(counters + KL_CNT_ATOMICS, 1ull);
+  }
+}
+
+__global__ void eval_kernel(const uint64_t* __restrict__ idx, uint64_t n, uint64_t N, Group G,
+                            Plan L, View V, int mixed, const Pre64* __restrict__ pre64,
+                            const Pre32* __restrict__ pre32, const uint32_t* __restrict__ flags,
+                            const double2* __restrict__ suf64, const float2* __restrict__ suf32,
+                            double* __restrict__ out) {
+  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n;
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i = idx[t];
+    double uu = __longlong_as_double(0x7FF8000000000000ll), vv = uu;
+    if (i < N) {
+      int w[kMaxRenderDepth];
+      decode_word(i, L.d, w);
+      if (L.d == 1) {
+        const int x = w[0];
+        dc z = mobius(load_gen(G, x), {G.seed[2 * x], G.seed[2 * x + 1]});
+        uu = (z.re - V.x0) * V.sx;
+        vv = (V.y1 - z.im) * V.sy;
+      } else {
+        uint32_t r = 0;
+        for (int k = L.p - 2; k >= 0; --k) {
+          const int ban = (w[k + 1] + 2) & 3;
+          r = 3u * r + (uint32_t)(w[k] - (w[k] > ban ? 1 : 0));
+        }
+        const uint32_t slot = (uint32_t)w[L.p - 1] * L.np + r;
+        const uint32_t sslot = (uint32_t)w[L.p] * L.ns + (uint32_t)(i % (uint64_t)L.ns);
+        const uint32_t fl = flags[slot];
+        if (mixed && !(fl & kFallback)) {
+          const Pre32 c = pre32[slot];
+          const float2 s = suf32[sslot];
+          float uf, vf;
+          uv_pole32(c, s.x, s.y, uf, vf);
+          uu = (double)c.axi + (double)uf;
+          vv = (double)c.ayi + (double)vf;
+        } else if (fl & kDirect) {
+          const double2 s = suf64[sslot];
+          uv_direct64(pre64[slot], s.x, s.y, V, uu, vv);
+        } else {
+          const double2 s = suf64[sslot];
+          uv_pole64(pre64[slot], s.x, s.y, uu, vv);
+        }
+      }
+      if (!isfinite(uu) || !isfinite(vv)) {
+        uu = __longlong_as_double(0x7FF8000000000000ll);
+        vv = uu;
+      }
+    }
+    out[2 * t] = uu;
+    out[2 * t + 1] = vv;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host helpers
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+uint32_t pow3u(int e) {
+  uint32_t v = 1;
+  while (e-- > 0) v *= 3u;
+  return v;
+}
+
+bool valid_view(const kl_params* p) {
+  if (p->width < 1 || p->height < 1 || p->width > KL_MAX_IMAGE_SIDE ||
+      p->height > KL_MAX_IMAGE_SIDE)
+    return false;
+  if ((uint64_t)p->width * p->height > (1ull << 31) - 1) return false;
+  if (!(p->x0 < p->x1) || !(p->y0 < p->y1)) return false;
+  const double v[4] = {p->x0, p->x1, p->y0, p->y1};
+  for (double t : v)
+    if (!isfinite(t)) return false;
+  for (int k = 0; k < 32; ++k)
+    if (!isfinite(p->gens[k])) return false;
+  for (int k = 0; k < 8; ++k)
+    if (!isfinite(p->seeds[k])) return false;
+  return true;
+}
+
+// Prefix/suffix split: up to 9 prefix letters while the words are few
+// (enough threads), then suffixes of up to 8 letters (9 beyond depth 20),
+// the rest prefix.
+int make_plan(const kl_params* p, Plan* L) {
+  const int d = (int)p->depth;
+  if (d < 1 || d > kMaxRenderDepth) return KL_ERANGE;
+  int pl, sl;
+  if (d == 1) {
+    pl = 1;
+    sl = 0;
+  } else if (p->prefix_len) {
+    pl = (int)p->prefix_len;
+    sl = d - pl;
+    if (pl < 1 || sl < 1 || pl > kMaxPrefix || sl > kMaxSuffix) return KL_EINVAL;
+  } else if (d <= 10) {
+    pl = d - 1;
+    sl = 1;
+  } else {
+    sl = d - 9;
+    const int smax = d > 20 ? 9 : 8;
+    if (sl > smax) sl = smax;
+    pl = d - sl;
+    if (pl > kMaxPrefix) return KL_ERANGE;
+  }
+  L->d = d;
+  L->p = pl;
+  L->s = sl;
+  L->np = pow3u(pl - 1);
+  L->ns = sl > 0 ? pow3u(sl - 1) : 0;
+  L->q = (pl + 1) / 2;
+  L->so = sl / 2;
+  L->si = sl - L->so;
+  L->p3_q1 = pow3u(L->q - 1);
+  L->p3_pq = pow3u(pl - L->q);
+  L->p3_so1 = L->so > 0 ? pow3u(L->so - 1) : 1;
+  L->p3_si = pow3u(L->si);
+  L->p3_si1 = L->si > 0 ? pow3u(L->si - 1) : 1;
+  const size_t nP = 4ull * L->np, nS = 4ull * L->ns;
+  size_t off = 0;
+  L->off_pre64 = off; off = align256(off + nP * sizeof(Pre64));
+  L->off_pre32 = off; off = align256(off + nP * sizeof(Pre32));
+  L->off_flags = off; off = align256(off + nP * sizeof(uint32_t));
+  L->off_suf64 = off; off = align256(off + nS * sizeof(double2));
+  L->off_suf32 = off; off = align256(off + nS * sizeof(float2));
+  L->off_fb = off; off = align256(off + nP * sizeof(uint32_t));
+  L->off_fbcount = off; off = align256(off + sizeof(uint32_t));
+  L->off_L = off; off = align256(off + 4ull * L->p3_q1 * sizeof(PartM));
+  L->off_H = off; off = align256(off + 4ull * L->p3_pq * sizeof(M2));
+  L->off_So = off; off = align256(off + 4ull * L->p3_so1 * sizeof(PartM));
+  L->off_Si = off; off = align256(off + 4ull * L->p3_si1 * sizeof(double2));
+  L->total = off;
+  return KL_OK;
+}
+
+View make_view(const kl_params* p) {
+  View V;
+  V.x0 = p->x0;
+  V.y1 = p->y1;
+  V.sx = (double)p->width / (p->x1 - p->x0);
+  V.sy = (double)p->height / (p->y1 - p->y0);
+  V.W = p->width;
+  V.H = p->height;
+  const double w = (double)p->width, h = (double)p->height;
+  uint64_t bw, bh;
+  memcpy(&bw, &w, sizeof bw);
+  memcpy(&bh, &h, sizeof bh);
+  V.hiW = (uint32_t)(bw >> 32);
+  V.hiH = (uint32_t)(bh >> 32);
+  return V;
+}
+
+Group make_group(const kl_params* p) {
+  Group G;
+  for (int k = 0; k < 32; ++k) G.g[k] = p->gens[k];
+  for (int k = 0; k < 8; ++k) G.seed[k] = p->seeds[k];
+  return G;
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return n;
+}
+
+int check_launch() {
+  return cudaGetLastError() == cudaSuccess ? KL_OK : KL_ECUDA;
+}
+
+// caller events recorded around the main per-word kernel (kl_set_profile_events)
+cudaEvent_t g_prof_start = nullptr, g_prof_stop = nullptr;
+
+int prof_mark(cudaEvent_t e, cudaStream_t s) {
+  if (!e) return KL_OK;
+  return cudaEventRecord(e, s) == cudaSuccess ? KL_OK : KL_ECUDA;
+}
+
+struct Tables {
+  Pre64* pre64;
+  Pre32* pre32;
+  uint32_t* flags;
+  double2* suf64;
+  float2* suf32;
+  uint32_t* fb;
+  uint32_t* fbcount;
+  PartM* Lt;
+  M2* Ht;
+  PartM* Sot;
+  double2* Sit;
+};
+
+Tables carve(const Plan& L, void* ws) {
+  char* b = (char*)ws;
+  return {(Pre64*)(b + L.off_pre64), (Pre32*)(b + L.off_pre32), (uint32_t*)(b + L.off_flags),
+          (double2*)(b + L.off_suf64), (float2*)(b + L.off_suf32), (uint32_t*)(b + L.off_fb),
+          (uint32_t*)(b + L.off_fbcount), (PartM*)(b + L.off_L), (M2*)(b + L.off_H),
+          (PartM*)(b + L.off_So), (double2*)(b + L.off_Si)};
+}
+
+int build_tables(const kl_params* p, const Plan& L, const View& V, const Group& G,
+                 const Tables& T, cudaStream_t st) {
+  const int mixed = p->precision == KL_MIXED;
+  if (cudaMemsetAsync(T.fbcount, 0, sizeof(uint32_t), st) != cudaSuccess) return KL_ECUDA;
+  const uint32_t nParts = 4u * L.p3_q1 + (L.p > L.q ? 4u * L.p3_pq : 0u) +
+                          (L.so > 0 ? 4u * L.p3_so1 : 0u) + 4u * L.p3_si1;
+  parts_kernel<<<(nParts + 63) / 64, 64, 0, st>>>(G, L, (int)p->renorm_every, T.Lt, T.Ht, T.Sot,
+                                                  T.Sit);
+  if (check_launch() != KL_OK) return KL_ECUDA;
+  const uint32_t n = 4u * L.np + 4u * L.ns;
+  combine_kernel<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(
+      V, L, p->parabolic_tol, mixed, T.Lt, T.Ht, T.Sot, T.Sit, T.pre64, T.pre32, T.flags, T.fb,
+      T.fbcount, T.suf64, T.suf32);
+  return check_launch();
+}
+
+int validate(const kl_params* p, size_t ws_bytes, void* ws, Plan* L) {
+  if (!p || !valid_view(p)) return KL_EINVAL;
+  if (p->precision != KL_FP64 && p->precision != KL_MIXED) return KL_EINVAL;
+  if (!(p->parabolic_tol >= 0.0)) return KL_EINVAL;
+  const int st = make_plan(p, L);
+  if (st != KL_OK) return st;
+  if (L->d > 1) {
+    if (!ws) return KL_EINVAL;
+    if (((uintptr_t)ws & 255u) != 0) return KL_EINVAL;
+    if (ws_bytes < L->total) return KL_ENOSPACE;
+  }
+  return KL_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+
+extern "C" size_t kl_workspace_bytes(const kl_params* p) {
+  if (!p || !valid_view(p)) return 0;
+  Plan L;
+  if (make_plan(p, &L) != KL_OK) return 0;
+  return L.total;
+}
+
+extern "C" int kl_decode_words(uint32_t depth, const uint64_t* d_index, uint64_t n,
+                               uint8_t* d_letters, void* stream) {
+  if (depth < 1 || depth > KL_MAX_DEPTH) return KL_EINVAL;
+  if (n == 0) return KL_OK;
+  if (!d_index || !d_letters) return KL_EINVAL;
+  const int sms = sm_count();
+  if (sms <= 0) return KL_ECUDA;
+  const uint64_t blocks = (n + kThreads - 1) / kThreads;
+  const unsigned g = (unsigned)(blocks < (uint64_t)sms * 16 ? blocks : (uint64_t)sms * 16);
+  decode_kernel<<<g, kThreads, 0, (cudaStream_t)stream>>>(d_index, n, (int)depth,
+                                                          kl_word_count(depth), d_letters);
+  return check_launch();
+}
+
+extern "C" int kl_eval_words(const kl_params* p, const uint64_t* d_index, uint64_t n,
+                             double* d_uv, void* d_workspace, size_t workspace_bytes,
+                             void* stream) {
+  Plan L;
+  int st = validate(p, workspace_bytes, d_workspace, &L);
+  if (st != KL_OK) return st;
+  if (n == 0) return KL_OK;
+  if (!d_index || !d_uv) return KL_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const View V = make_view(p);
+  const Group G = make_group(p);
+  Tables T{};
+  if (L.d > 1) {
+    T = carve(L, d_workspace);
+    st = build_tables(p, L, V, G, T, s);
+    if (st != KL_OK) return st;
+  }
+  const int sms = sm_count();
+  const uint64_t blocks = (n + kThreads - 1) / kThreads;
+  const unsigned g = (unsigned)(blocks < (uint64_t)sms * 16 ? blocks : (uint64_t)sms * 16);
+  eval_kernel<<<g, kThreads, 0, s>>>(d_index, n, kl_word_count(p->depth), G, L, V,
+                                     p->precision == KL_MIXED, T.pre64, T.pre32, T.flags,
+                                     T.suf64, T.suf32, d_uv);
+  return check_launch();
+}
+
+extern "C" int kl_render(const kl_params* p, uint32_t* d_image, uint64_t* d_counters,
+                         void* d_workspace, size_t workspace_bytes, void* stream) {
+  Plan L;
+  int st = validate(p, workspace_bytes, d_workspace, &L);
+  if (st != KL_OK) return st;
+  if (!d_image) return KL_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long* cnt = (unsigned long long*)d_counters;
+  if (!p->accumulate) {
+    if (cudaMemsetAsync(d_image, 0, (size_t)p->width * p->height * sizeof(uint32_t), s) !=
+        cudaSuccess)
+      return KL_ECUDA;
+    if (cnt && cudaMemsetAsync(cnt, 0, KL_N_COUNTERS * sizeof(uint64_t), s) != cudaSuccess)
+      return KL_ECUDA;
+  }
+  const View V = make_view(p);
+  const Group G = make_group(p);
+  if (L.d == 1) {
+    render_single_letter_kernel<<<1, 32, 0, s>>>(G, V, d_image, cnt);
+    return check_launch();
+  }
+  const Tables T = carve(L, d_workspace);
+  st = build_tables(p, L, V, G, T, s);
+  if (st != KL_OK) return st;
+  const dim3 grid((L.np + kThreads - 1) / kThreads, 12);
+  if (p->precision == KL_FP64) {
+    const size_t smem = (size_t)L.ns * sizeof(double2);
+    if (cudaFuncSetAttribute(render64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return KL_ECUDA;
+    if (prof_mark(g_prof_start, s) != KL_OK) return KL_ECUDA;
+    render64_kernel<<<grid, kThreads, smem, s>>>(T.pre64, T.flags, T.suf64, L, V, d_image, cnt);
+    if (check_launch() != KL_OK) return KL_ECUDA;
+    return prof_mark(g_prof_stop, s);
+  }
+  const size_t smem = (size_t)L.ns * sizeof(float2);
+  if (cudaFuncSetAttribute(render32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return KL_ECUDA;
+  if (prof_mark(g_prof_start, s) != KL_OK) return KL_ECUDA;
+  render32_kernel<<<grid, kThreads, smem, s>>>(T.pre32, T.flags, T.suf32, L, V, d_image, cnt);
+  if (check_launch() != KL_OK) return KL_ECUDA;
+  if (prof_mark(g_prof_stop, s) != KL_OK) return KL_ECUDA;
+  const int sms = sm_count();
+  fallback64_kernel<<<sms * 4, kThreads, 0, s>>>(T.pre64, T.flags, T.fb, T.fbcount, T.suf64, L, V,
+                                                  d_image, cnt);
+  return check_launch();
+}
+
+extern "C" int kl_set_profile_events(void* ev_start, void* ev_stop) {
+  if ((ev_start == nullptr) != (ev_stop == nullptr)) return KL_EINVAL;
+  g_prof_start = (cudaEvent_t)ev_start;
+  g_prof_stop = (cudaEvent_t)ev_stop;
+  return KL_OK;
+}

@@ -1,0 +1,90 @@
+"""The C-ABI library without a GPU: it loads, exports every declared entry
+point, and its host-side arithmetic (recipe, seeds, counts, validation) agrees
+with the oracle.  No device call is made here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import klsynth
+import oracle
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def kl():
+    from paper_1709_08018_gb300 import build
+    build.build()
+    import paper_1709_08018_gb300 as kl
+    return kl
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            names += re.findall(r"^KL_API\b[^;(]*?\b(kl_\w+)\s*\(", text, flags=re.M)
+    return names
+
+
+def test_every_declared_symbol_is_exported(kl):
+    names = declared_functions()
+    assert len(names) >= 9
+    assert set(names) == set(kl.binding.API)
+    assert set(kl.exported_symbols()) == set(names)
+
+
+def test_word_count(kl):
+    for d in range(0, 43):
+        assert kl.word_count(d) == oracle.word_count(d)
+
+
+def test_status_strings(kl):
+    assert kl.status_string(0) == "ok"
+    assert kl.status_string(4) == "workspace too small"
+    assert kl.status_string(99) == "unknown status"
+
+
+TRACES = [(2 + 0j, 2 + 0j), (1.91 + 0.05j, 1.91 + 0.05j), (3 + 0j, 3 + 0j)] + [
+    (g.ta, g.tb) for g, _ in klsynth.draw_groups(klsynth.BATCH_SEED, 8)]
+
+
+@pytest.mark.parametrize("ta,tb", TRACES)
+def test_grandma_and_seeds_agree_with_oracle(kl, ta, tb):
+    g_lib, g_or = kl.grandma(ta, tb), oracle.grandma(ta, tb)
+    assert np.allclose(g_lib, g_or, rtol=1e-14, atol=1e-15)
+    s_lib, s_or = kl.seeds(g_lib), oracle.seeds(g_or)
+    assert np.allclose(s_lib, s_or, rtol=1e-12, atol=1e-13)
+
+
+def test_grandma_rejects_bad_traces(kl):
+    with pytest.raises(kl.KlError) as e:
+        kl.grandma(float("nan") + 0j, 2 + 0j)
+    assert e.value.status == 1
+    # ta = tb = 0 makes the recipe's z0 denominator vanish
+    with pytest.raises(kl.KlError):
+        kl.grandma(0j, 0j)
+
+
+def test_params_init_defaults(kl):
+    p = kl.params_init(2 + 0j, 2 + 0j, 10, 1024, 768, (-1.5, 1.5, -1.0, 1.0))
+    assert (p.depth, p.width, p.height) == (10, 1024, 768)
+    assert (p.x0, p.x1, p.y0, p.y1) == (-1.5, 1.5, -1.0, 1.0)
+    assert p.precision == kl.FP64 and p.renorm_every == 8 and p.parabolic_tol == 1e-6
+    assert p.prefix_len == 0 and p.accumulate == 0
+    assert np.allclose(list(p.gens), oracle.grandma(2, 2), atol=1e-15)
+
+
+def test_workspace_validation(kl):
+    good = kl.params_init(2 + 0j, 2 + 0j, 18, 4096, 4096, (-1.5, 1.5, -1.5, 1.5))
+    n = kl.workspace_bytes(good)
+    assert n > 0 and n % 256 == 0
+    # suffix of 8 letters: 4 * 3^7 points; prefix of 10 letters: 4 * 3^9 slots
+    assert n >= 4 * 3 ** 9 * (64 + 48 + 4) + 4 * 3 ** 7 * 24
+    for field, bad in [("depth", 0), ("depth", 25), ("width", 0), ("height", 70000),
+                       ("x1", -2.0), ("y0", float("nan")), ("prefix_len", 18)]:
+        p = kl.params_init(2 + 0j, 2 + 0j, 18, 4096, 4096, (-1.5, 1.5, -1.5, 1.5))
+        setattr(p, field, bad)
+        assert kl.workspace_bytes(p) == 0, field
