@@ -338,11 +338,11 @@ def run_ours(args):
     kern_s = statistics.mean(kern_ms) / 1000.0
     words_fp32 = N - fp64_words
     achieved = words_fp32 * FP32_OPS_PER_WORD / kern_s / 1e12
-    roofline = {"bound": "alu", "kernel": "render32_kernel", "achieved": achieved,
+    roofline = {"bound": "alu", "kernel": "render_mixed_kernel", "achieved": achieved,
                 "peak": fp32_peak, "unit": "T FP32-op/s", "frac": achieved / fp32_peak,
                 "peak_kind": "derived: 152 SMs x 128 FP32 lanes x max SM clock",
                 "ops_per_word": FP32_OPS_PER_WORD,
-                "traffic": traffic_for("render32_kernel"),
+                "traffic": traffic_for("render_mixed_kernel"),
                 "kernel_ms": statistics.mean(kern_ms),
                 "kernel_share_of_step": statistics.mean(kern_ms) / statistics.mean(step_ms)}
     fp64_ach = N * FP64_OPS_PER_WORD / (fp64_kern_ms / 1000.0) / 1e12

@@ -43,6 +43,7 @@ struct Plan {
   int so, si;    // letters of the suffix head (matrix) and tail (point) tables
   uint32_t np;   // prefix slots per last letter: 3^(p-1)
   uint32_t ns;   // suffix points per first letter: 3^(s-1)
+  uint32_t npairs;  // FP32 point pairs per first letter: ceil(ns / 2)
   uint32_t p3_q1, p3_pq, p3_so1, p3_si, p3_si1;  // 3^(q-1), 3^(p-q), 3^(so-1), 3^si, 3^(si-1)
   size_t off_pre64, off_pre32, off_flags, off_suf64, off_suf32, off_fb, off_fbcount;
   size_t off_L, off_H, off_So, off_Si, total;
@@ -65,7 +66,8 @@ struct __align__(16) Pre64 {
 
 struct __align__(16) Pre32 {
   float gr, gi, axf, ayf, c1, c2, c3, c4;
-  int axi, ayi, pad0, pad1;
+  int axi, ayi;  // integer part of the pixel coordinates of alpha
+  int kx, ky;    // 0x4B400000 - axi, 0x4B400000 - ayi (see render_mixed_kernel)
 };
 
 struct dc {
@@ -104,13 +106,20 @@ __device__ __forceinline__ M2 mmul(const M2& a, const M2& b) {
           cadd(cmul(a.r, b.p), cmul(a.s, b.r)), cadd(cmul(a.r, b.q), cmul(a.s, b.s))};
 }
 __device__ __forceinline__ dc mdet(const M2& a) { return csub(cmul(a.p, a.s), cmul(a.q, a.r)); }
+// 1/z for z != 0: conj(z) / |z|^2 with one real division
+__device__ __forceinline__ dc crcp(dc z) {
+  const double t = 1.0 / (z.re * z.re + z.im * z.im);
+  return {z.re * t, -z.im * t};
+}
+// divide by the principal square root of the determinant
 __device__ __forceinline__ void renormalise(M2& a) {
   dc k = csqrt(mdet(a));
   if (k.re == 0.0 && k.im == 0.0) return;
-  a.p = cdiv(a.p, k); a.q = cdiv(a.q, k); a.r = cdiv(a.r, k); a.s = cdiv(a.s, k);
+  k = crcp(k);
+  a.p = cmul(a.p, k); a.q = cmul(a.q, k); a.r = cmul(a.r, k); a.s = cmul(a.s, k);
 }
 __device__ __forceinline__ dc mobius(const M2& m, dc z) {
-  return cdiv(cadd(cmul(m.p, z), m.q), cadd(cmul(m.r, z), m.s));
+  return cmul(cadd(cmul(m.p, z), m.q), crcp(cadd(cmul(m.r, z), m.s)));
 }
 
 // ---------------------------------------------------------------------------
@@ -184,20 +193,37 @@ __device__ __forceinline__ int pixel64(double u, double v, const View& V) {
   return (int)(floor_hi(hv) * V.W + floor_hi(hu));
 }
 
-// Pixel id of a local-frame FP32 coordinate pair: col = axi + floor(uf).
-// floor(uf) for |uf| < 2^22 via the 1.5 * 2^23 rounding shift in
-// round-toward-minus-infinity; larger |uf| (and NaN, inf) are outside.
-__device__ __forceinline__ int floor_f32(float t) {
-  return __float_as_int(__fadd_rd(t, 12582912.0f)) - 0x4B400000;
+// Packed FP32 pairs (Blackwell f32x2 add/mul/fma): two words per instruction,
+// each half rounded exactly as the scalar operation.
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 pk(float lo, float hi) {
+  f2 d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
 }
-__device__ __forceinline__ int pixel32(float uf, float vf, const Pre32& c, const View& V) {
-  uint32_t au = __float_as_uint(uf) & 0x7FFFFFFFu;
-  uint32_t av = __float_as_uint(vf) & 0x7FFFFFFFu;
-  int col = c.axi + floor_f32(uf);
-  int row = c.ayi + floor_f32(vf);
-  bool ok = (au < 0x4A800000u) & (av < 0x4A800000u) & ((uint32_t)col < V.W) &
-            ((uint32_t)row < V.H);
-  return ok ? row * (int)V.W + col : -1;
+__device__ __forceinline__ void upk(f2 a, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 add2_rm(f2 a, f2 b) {
+  f2 d;
+  asm("add.rm.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
 }
 
 // ---------------------------------------------------------------------------
@@ -319,7 +345,7 @@ __global__ void combine_kernel(View V, Plan L, double ptol, int mixed,
                                Pre64* __restrict__ pre64, Pre32* __restrict__ pre32,
                                uint32_t* __restrict__ flags, uint32_t* __restrict__ fb_list,
                                uint32_t* __restrict__ fb_count, double2* __restrict__ suf64,
-                               float2* __restrict__ suf32) {
+                               float* __restrict__ suf32p) {
   const uint32_t nP = 4u * L.np, nS = 4u * L.ns;
   for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nP + nS;
        idx += gridDim.x * blockDim.x) {
@@ -339,7 +365,18 @@ __global__ void combine_kernel(View V, Plan L, double ptol, int mixed,
         v = make_double2(r.re, r.im);
       }
       suf64[slot] = v;
-      suf32[slot] = make_float2((float)v.x, (float)v.y);
+      // pair-interleaved FP32 table: per first letter u, entry k holds
+      // (re v_2k, re v_2k+1, im v_2k, im v_2k+1); an odd count is padded with NaN
+      {
+        const uint32_t u = slot / L.ns, j = slot % L.ns;
+        float* e = suf32p + 4ull * ((uint64_t)u * L.npairs + j / 2u);
+        e[j & 1u] = (float)v.x;
+        e[2 + (j & 1u)] = (float)v.y;
+        if (j + 1u == L.ns && (L.ns & 1u)) {
+          e[1] = __int_as_float(0x7FC00000);
+          e[3] = __int_as_float(0x7FC00000);
+        }
+      }
       continue;
     }
     const uint32_t slot = idx;
@@ -353,7 +390,8 @@ __global__ void combine_kernel(View V, Plan L, double ptol, int mixed,
     uint32_t fl = 0;
     const dc tr2m4 = csub(cmul(tr, tr), {4.0 * det.re, 4.0 * det.im});
     const double t2 = tr.re * tr.re + tr.im * tr.im;
-    if (hypot(tr2m4.re, tr2m4.im) < ptol * fmax(1.0, t2)) fl |= kNearPar;
+    const double lim2 = ptol * fmax(1.0, t2);
+    if (tr2m4.re * tr2m4.re + tr2m4.im * tr2m4.im < lim2 * lim2) fl |= kNearPar;
     Pre64 c64;
     Pre32 c32;
     if (!(cabs1(P.r) > 1e-12 * scale)) {
@@ -361,7 +399,7 @@ __global__ void combine_kernel(View V, Plan L, double ptol, int mixed,
       c64 = {P.p.re, P.p.im, P.q.re, P.q.im, P.r.re, P.r.im, P.s.re, P.s.im};
       c32 = {};
     } else {
-      const dc inv10 = cdiv({1.0, 0.0}, P.r);
+      const dc inv10 = crcp(P.r);
       const dc alpha = cmul(P.p, inv10);
       const dc gamma = cmul(P.s, inv10);
       const dc mbeta = cmul(det, cmul(inv10, inv10));  // -beta
@@ -385,7 +423,8 @@ __global__ void combine_kernel(View V, Plan L, double ptol, int mixed,
       c32.c4 = (float)c4;
       c32.axi = (int)axi;
       c32.ayi = (int)ayi;
-      c32.pad0 = c32.pad1 = 0;
+      c32.kx = 0x4B400000 - (int)axi;
+      c32.ky = 0x4B400000 - (int)ayi;
     }
     if (mixed && (fl & (kDirect | kNearPar | kWide))) {
       fl |= kFallback;
@@ -401,37 +440,35 @@ __global__ void combine_kernel(View V, Plan L, double ptol, int mixed,
 // ---------------------------------------------------------------------------
 // splat helpers
 
+// Run-length tally of one thread's words.  Consecutive words of a thread
+// differ only in their innermost letters, so they usually land in the same
+// pixel; a run of equal pixels becomes one atomic add.  pix < 0 marks a
+// dropped word (such runs are discarded).
 struct Tally {
-  uint32_t in_window = 0, words = 0, atomics = 0;
+  uint32_t in_window = 0, atomics = 0;
   int cur = -1;
   uint32_t run = 0;
 
-  __device__ __forceinline__ void add(int pix, uint32_t* __restrict__ img) {
-    ++words;
-    if (pix != cur) {
-      if (cur >= 0) {
-        atomicAdd(img + cur, run);
-        ++atomics;
-      }
-      cur = pix;
-      run = 0;
-    }
-    ++run;
-    in_window += (pix >= 0);
-  }
   __device__ __forceinline__ void flush(uint32_t* __restrict__ img) {
     if (cur >= 0 && run) {
       atomicAdd(img + cur, run);
       ++atomics;
+      in_window += run;
     }
-    cur = -1;
     run = 0;
+  }
+  __device__ __forceinline__ void add(int pix, uint32_t* __restrict__ img) {
+    if (pix != cur) {
+      flush(img);
+      cur = pix;
+    }
+    ++run;
   }
 };
 
-__device__ __forceinline__ void publish(const Tally& t, uint32_t fp64_words,
+__device__ __forceinline__ void publish(const Tally& t, uint32_t words, uint32_t fp64_words,
                                         unsigned long long* counters) {
-  unsigned long long a = t.in_window, b = t.words - t.in_window, c = fp64_words, e = t.atomics;
+  unsigned long long a = t.in_window, b = words - t.in_window, c = fp64_words, e = t.atomics;
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_down_sync(0xFFFFFFFFu, a, o);
     b += __shfl_down_sync(0xFFFFFFFFu, b, o);
@@ -446,128 +483,201 @@ __device__ __forceinline__ void publish(const Tally& t, uint32_t fp64_words,
   }
 }
 
-// blockIdx.y = 3 * x + k enumerates the 12 compatible (prefix last letter x,
-// suffix first letter u) pairs: u is the k-th letter other than inv(x).
-__device__ __forceinline__ void pair_of(int q, int& x, int& u) {
+// Work items of the persistent render kernels: item = (q, prefix block pb,
+// suffix chunk c), chunk index fastest.  q = 3 x + k enumerates the 12
+// compatible (prefix last letter x, suffix first letter u) pairs, u being the
+// k-th letter other than inv(x); thread t of the block takes prefix slot
+// (x, pb * kThreads + t) and the chunk's suffix points.  Items all cost the
+// same, so a static block-stride assignment balances to within one item.
+struct Work {
+  uint32_t n_pb;      // prefix blocks per letter: ceil(np / kThreads)
+  uint32_t n_chunks;  // suffix chunks per first letter
+  uint32_t chunk;     // suffix points (FP64) or point pairs (FP32) per chunk
+  uint32_t n_items;   // 12 * n_pb * n_chunks
+};
+
+__device__ __forceinline__ void item_of(uint32_t item, const Work& W, int& x, int& u,
+                                        uint32_t& pb, uint32_t& c) {
+  c = item % W.n_chunks;
+  const uint32_t t = item / W.n_chunks;
+  pb = t % W.n_pb;
+  const int q = (int)(t / W.n_pb);
   x = q / 3;
   u = allowed_letter(q % 3, (x + 2) & 3);
 }
 
 // ---------------------------------------------------------------------------
 // render kernels
+//
+// Both render kernels are persistent: each block takes items from a device
+// work queue (one atomic per item) until the queue is empty.
 
-// FP64: thread = one prefix slot of last letter x, looping over the suffix
-// points of first letter u held in shared memory (all lanes read the same
-// point: a broadcast).  Consecutive suffix points differ in their innermost
-// letters, so consecutive words usually land in the same pixel; the tally
-// merges such runs into one atomic.
-__global__ void __launch_bounds__(kThreads) render64_kernel(
-    const Pre64* __restrict__ pre, const uint32_t* __restrict__ flags,
-    const double2* __restrict__ suf, Plan L, View V, uint32_t* __restrict__ img,
-    unsigned long long* counters) {
-  extern __shared__ double2 s_suf64[];
-  int x, u;
-  pair_of(blockIdx.y, x, u);
-  const double2* src = suf + (size_t)u * L.ns;
-  for (uint32_t t = threadIdx.x; t < L.ns; t += blockDim.x) s_suf64[t] = src[t];
+__device__ __forceinline__ uint32_t next_item(uint32_t* queue) {
+  __shared__ uint32_t s_item;
   __syncthreads();
-  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-  Tally t;
-  if (r < L.np) {
-    const uint32_t slot = (uint32_t)x * L.np + r;
-    const Pre64 c = pre[slot];
-    if (flags[slot] & kDirect) {
-      for (uint32_t j = 0; j < L.ns; ++j) {
-        double uu, vv;
-        const double2 s = s_suf64[j];
-        uv_direct64(c, s.x, s.y, V, uu, vv);
-        t.add(pixel64(uu, vv, V), img);
-      }
-    } else {
-#pragma unroll 4
-      for (uint32_t j = 0; j < L.ns; ++j) {
-        double uu, vv;
-        const double2 s = s_suf64[j];
-        uv_pole64(c, s.x, s.y, uu, vv);
-        t.add(pixel64(uu, vv, V), img);
-      }
-    }
-    t.flush(img);
-  }
-  publish(t, 0, counters);
+  if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
+  __syncthreads();
+  return s_item;
 }
 
-// Mixed: as render64_kernel with the per-word map in FP32 in the prefix's
-// local frame; prefixes flagged kFallback are skipped here and rendered by
-// fallback64_kernel.
-__global__ void __launch_bounds__(kThreads) render32_kernel(
-    const Pre32* __restrict__ pre, const uint32_t* __restrict__ flags,
-    const float2* __restrict__ suf, Plan L, View V, uint32_t* __restrict__ img,
-    unsigned long long* counters) {
-  extern __shared__ float2 s_suf32[];
-  int x, u;
-  pair_of(blockIdx.y, x, u);
-  const float2* src = suf + (size_t)u * L.ns;
-  for (uint32_t t = threadIdx.x; t < L.ns; t += blockDim.x) s_suf32[t] = src[t];
-  __syncthreads();
-  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-  Tally t;
-  if (r < L.np) {
-    const uint32_t slot = (uint32_t)x * L.np + r;
-    if (!(flags[slot] & kFallback)) {
-      const Pre32 c = pre[slot];
-#pragma unroll 4
-      for (uint32_t j = 0; j < L.ns; ++j) {
-        float uf, vf;
-        const float2 s = s_suf32[j];
-        uv_pole32(c, s.x, s.y, uf, vf);
-        t.add(pixel32(uf, vf, c, V), img);
-      }
-      t.flush(img);
-    }
-  }
-  publish(t, 0, counters);
-}
-
-// Mixed-mode FP64 fallback: work item = (fallback prefix, one of its three
-// compatible suffix letters, a chunk of kFbChunk suffix points); grid-stride
-// over items, the prefix count read on the device.
-constexpr uint32_t kFbChunk = 64;
-
-__global__ void __launch_bounds__(kThreads) fallback64_kernel(
-    const Pre64* __restrict__ pre, const uint32_t* __restrict__ flags,
-    const uint32_t* __restrict__ fb_list, const uint32_t* __restrict__ fb_count,
-    const double2* __restrict__ suf, Plan L, View V, uint32_t* __restrict__ img,
-    unsigned long long* counters) {
-  const uint32_t chunks = (L.ns + kFbChunk - 1) / kFbChunk;
-  const uint32_t per_prefix = 3u * chunks;
-  const uint64_t items = (uint64_t)per_prefix * (*fb_count);
-  Tally t;
-  uint32_t fp64_words = 0;
-  for (uint64_t it = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; it < items;
-       it += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t slot = fb_list[it / per_prefix];
-    const uint32_t rem = (uint32_t)(it % per_prefix);
-    const int x = (int)(slot / L.np);
-    const int u = allowed_letter((int)(rem / chunks), (x + 2) & 3);
-    const uint32_t j0 = (rem % chunks) * kFbChunk;
-    const uint32_t j1 = min(L.ns, j0 + kFbChunk);
-    const Pre64 c = pre[slot];
-    const bool direct = flags[slot] & kDirect;
-    const double2* src = suf + (size_t)u * L.ns;
+// FP64 words of one prefix slot on suffix points [j0, j1) of first letter u.
+__device__ __forceinline__ void words64(const Pre64& k, bool direct, const double2* src,
+                                        uint32_t j0, uint32_t j1, const View& V, Tally& t,
+                                        uint32_t* __restrict__ img) {
+  if (direct) {
     for (uint32_t j = j0; j < j1; ++j) {
       double uu, vv;
-      const double2 s = src[j];
-      if (direct)
-        uv_direct64(c, s.x, s.y, V, uu, vv);
-      else
-        uv_pole64(c, s.x, s.y, uu, vv);
+      const double2 s = __ldg(src + j);
+      uv_direct64(k, s.x, s.y, V, uu, vv);
       t.add(pixel64(uu, vv, V), img);
     }
-    t.flush(img);
-    fp64_words += j1 - j0;
+  } else {
+#pragma unroll 2
+    for (uint32_t j = j0; j < j1; ++j) {
+      double uu, vv;
+      const double2 s = __ldg(src + j);
+      uv_pole64(k, s.x, s.y, uu, vv);
+      t.add(pixel64(uu, vv, V), img);
+    }
   }
-  publish(t, fp64_words, counters);
+  t.flush(img);
+}
+
+// FP64: per item each thread evaluates its prefix on `chunk` consecutive
+// suffix points, read with a warp-uniform address (a broadcast from L1).
+__global__ void __launch_bounds__(kThreads) render64_kernel(
+    const Pre64* __restrict__ pre, const uint32_t* __restrict__ flags,
+    const double2* __restrict__ suf, Plan L, View V, Work Wk, uint32_t* queue,
+    uint32_t* __restrict__ img, unsigned long long* counters) {
+  Tally t;
+  uint32_t words = 0;
+  for (;;) {
+    const uint32_t item = next_item(queue);
+    if (item >= Wk.n_items) break;
+    int x, u;
+    uint32_t pb, c;
+    item_of(item, Wk, x, u, pb, c);
+    const uint32_t r = pb * kThreads + threadIdx.x;
+    if (r >= L.np) continue;
+    const uint32_t slot = (uint32_t)x * L.np + r;
+    const uint32_t j0 = c * Wk.chunk, j1 = min(L.ns, j0 + Wk.chunk);
+    words64(pre[slot], flags[slot] & kDirect, suf + (size_t)u * L.ns, j0, j1, V, t, img);
+    words += j1 - j0;
+  }
+  publish(t, words, 0, counters);
+}
+
+// Mixed-mode FP64 fallback unit: (fallback prefix, one of its three suffix
+// letters, a chunk of kFbChunk suffix points).  Kept out of line so that its
+// registers do not bind the FP32 loop.
+constexpr uint32_t kFbChunk = 64;
+
+struct UnitTally {
+  uint32_t words, in_window, atomics;
+};
+
+__device__ __noinline__ UnitTally fallback_unit(uint32_t unit, const Pre64* __restrict__ pre,
+                                                const uint32_t* __restrict__ flags,
+                                                const uint32_t* __restrict__ fb_list,
+                                                const double2* __restrict__ suf, uint32_t np,
+                                                uint32_t ns, View V, uint32_t* __restrict__ img) {
+  const uint32_t chunks = (ns + kFbChunk - 1) / kFbChunk;
+  const uint32_t per_prefix = 3u * chunks;
+  const uint32_t slot = fb_list[unit / per_prefix];
+  const uint32_t rem = unit % per_prefix;
+  const int x = (int)(slot / np);
+  const int u = allowed_letter((int)(rem / chunks), (x + 2) & 3);
+  const uint32_t j0 = (rem % chunks) * kFbChunk;
+  const uint32_t j1 = min(ns, j0 + kFbChunk);
+  Tally t;
+  words64(pre[slot], flags[slot] & kDirect, suf + (size_t)u * ns, j0, j1, V, t, img);
+  return {j1 - j0, t.in_window, t.atomics};
+}
+
+// Pixel ids in the mixed kernel: for |uf| < 2^22, adding 1.5 * 2^23 rounded
+// toward minus infinity leaves floor(uf) in the low mantissa bits:
+// bits(t) - 0x4B400000 = floor(uf), so col = bits(t) - kx with
+// kx = 0x4B400000 - axi.  Any |uf| >= 2^22, infinity or NaN gives a t whose
+// bits put col outside [0, W) (|axi| < 2^20 and W <= 2^16), so one unsigned
+// compare per coordinate rejects out-of-window and non-finite words alike.
+//
+// Mixed: the queue holds first the FP64 fallback items (kThreads units each:
+// near-parabolic, direct-form and far prefixes), then the FP32 items.  Blocks
+// that draw fallback items keep the FP64 pipe busy while the others run FP32
+// work, so the fallback words overlap the FP32 words.  FP32 items evaluate the
+// per-word map in the prefix's local frame, two words per packed f32x2
+// instruction; a pair whose two words are both inside the window and in the
+// pixel of the current run costs one predicated compare chain and one add.
+__global__ void __launch_bounds__(kThreads, 12) render_mixed_kernel(
+    const Pre32* __restrict__ pre32, const Pre64* __restrict__ pre64,
+    const uint32_t* __restrict__ flags, const float4* __restrict__ sufp,
+    const double2* __restrict__ suf64, const uint32_t* __restrict__ fb_list,
+    const uint32_t* __restrict__ fb_count, Plan L, View V, Work Wk, uint32_t* queue,
+    uint32_t* __restrict__ img, unsigned long long* counters) {
+  const uint32_t fb_units = 3u * ((L.ns + kFbChunk - 1) / kFbChunk) * (*fb_count);
+  const uint32_t n64 = (fb_units + kThreads - 1) / kThreads;
+  const uint32_t total = n64 + Wk.n_items;
+  Tally t;
+  uint32_t words = 0, fp64_words = 0;
+  for (;;) {
+    const uint32_t item = next_item(queue);
+    if (item >= total) break;
+    if (item < n64) {
+      const uint32_t unit = item * kThreads + threadIdx.x;
+      if (unit < fb_units) {
+        const UnitTally r = fallback_unit(unit, pre64, flags, fb_list, suf64, L.np, L.ns, V, img);
+        words += r.words;
+        fp64_words += r.words;
+        t.in_window += r.in_window;
+        t.atomics += r.atomics;
+      }
+      continue;
+    }
+    int x, u;
+    uint32_t pb, c;
+    item_of(item - n64, Wk, x, u, pb, c);
+    const uint32_t r = pb * kThreads + threadIdx.x;
+    if (r >= L.np) continue;
+    const uint32_t slot = (uint32_t)x * L.np + r;
+    if (flags[slot] & kFallback) continue;
+    const Pre32 k = pre32[slot];
+    const f2 GR = pk(k.gr, k.gr), GI = pk(k.gi, k.gi);
+    const f2 C1 = pk(k.c1, k.c1), C2 = pk(k.c2, k.c2), C3 = pk(k.c3, k.c3), C4 = pk(k.c4, k.c4);
+    const f2 AX = pk(k.axf, k.axf), AY = pk(k.ayf, k.ayf);
+    const f2 magic = 0x4B4000004B400000ull;  // (1.5 * 2^23, 1.5 * 2^23)
+    const int W = (int)V.W;
+    const float4* src = sufp + (size_t)u * L.npairs;
+    const uint32_t k0 = c * Wk.chunk, k1 = min(L.npairs, k0 + Wk.chunk);
+#pragma unroll 2
+    for (uint32_t e = k0; e < k1; ++e) {
+      const float4 s = __ldg(src + e);
+      const f2 wr = add2(pk(s.x, s.y), GR);
+      const f2 wi = add2(pk(s.z, s.w), GI);
+      const f2 m = fma2(wr, wr, mul2(wi, wi));
+      float ma, mb;
+      upk(m, ma, mb);
+      const f2 rr = pk(rcp32(ma), rcp32(mb));
+      const f2 tx = fma2(C1, wr, mul2(C2, wi));
+      const f2 ty = fma2(C3, wr, mul2(C4, wi));
+      float tua, tub, tva, tvb;
+      upk(add2_rm(fma2(tx, rr, AX), magic), tua, tub);
+      upk(add2_rm(fma2(ty, rr, AY), magic), tva, tvb);
+      const int ca = __float_as_int(tua) - k.kx, cb = __float_as_int(tub) - k.kx;
+      const int ra = __float_as_int(tva) - k.ky, rb = __float_as_int(tvb) - k.ky;
+      const int pa = ra * W + ca, pb2 = rb * W + cb;
+      const bool oka = ((uint32_t)ca < V.W) & ((uint32_t)ra < V.H);
+      const bool okb = ((uint32_t)cb < V.W) & ((uint32_t)rb < V.H);
+      if (oka & okb & (pa == t.cur) & (pb2 == t.cur)) {
+        t.run += 2;
+      } else {
+        t.add(oka ? pa : -1, img);
+        t.add(okb ? pb2 : -1, img);
+      }
+    }
+    words += min(2u * k1, L.ns) - 2u * k0;
+    t.flush(img);
+  }
+  publish(t, words, fp64_words, counters);
 }
 
 // ---------------------------------------------------------------------------
@@ -615,7 +725,7 @@ __global__ void render_single_letter_kernel(Group G, View V, uint32_t* img,
 __global__ void eval_kernel(const uint64_t* __restrict__ idx, uint64_t n, uint64_t N, Group G,
                             Plan L, View V, int mixed, const Pre64* __restrict__ pre64,
                             const Pre32* __restrict__ pre32, const uint32_t* __restrict__ flags,
-                            const double2* __restrict__ suf64, const float2* __restrict__ suf32,
+                            const double2* __restrict__ suf64, const float4* __restrict__ suf32p,
                             double* __restrict__ out) {
   for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n;
        t += (uint64_t)gridDim.x * blockDim.x) {
@@ -640,9 +750,10 @@ __global__ void eval_kernel(const uint64_t* __restrict__ idx, uint64_t n, uint64
         const uint32_t fl = flags[slot];
         if (mixed && !(fl & kFallback)) {
           const Pre32 c = pre32[slot];
-          const float2 s = suf32[sslot];
+          const uint32_t jj = sslot % L.ns;
+          const float4 e = suf32p[(uint64_t)w[L.p] * L.npairs + jj / 2u];
           float uf, vf;
-          uv_pole32(c, s.x, s.y, uf, vf);
+          uv_pole32(c, (jj & 1u) ? e.y : e.x, (jj & 1u) ? e.w : e.z, uf, vf);
           uu = (double)c.axi + (double)uf;
           vv = (double)c.ayi + (double)vf;
         } else if (fl & kDirect) {
@@ -719,6 +830,7 @@ int make_plan(const kl_params* p, Plan* L) {
   L->s = sl;
   L->np = pow3u(pl - 1);
   L->ns = sl > 0 ? pow3u(sl - 1) : 0;
+  L->npairs = (L->ns + 1) / 2;
   L->q = (pl + 1) / 2;
   L->so = sl / 2;
   L->si = sl - L->so;
@@ -733,9 +845,9 @@ int make_plan(const kl_params* p, Plan* L) {
   L->off_pre32 = off; off = align256(off + nP * sizeof(Pre32));
   L->off_flags = off; off = align256(off + nP * sizeof(uint32_t));
   L->off_suf64 = off; off = align256(off + nS * sizeof(double2));
-  L->off_suf32 = off; off = align256(off + nS * sizeof(float2));
+  L->off_suf32 = off; off = align256(off + 4ull * L->npairs * sizeof(float4));
   L->off_fb = off; off = align256(off + nP * sizeof(uint32_t));
-  L->off_fbcount = off; off = align256(off + sizeof(uint32_t));
+  L->off_fbcount = off; off = align256(off + 2 * sizeof(uint32_t));  // fallback count, queue
   L->off_L = off; off = align256(off + 4ull * L->p3_q1 * sizeof(PartM));
   L->off_H = off; off = align256(off + 4ull * L->p3_pq * sizeof(M2));
   L->off_So = off; off = align256(off + 4ull * L->p3_so1 * sizeof(PartM));
@@ -792,7 +904,7 @@ struct Tables {
   Pre32* pre32;
   uint32_t* flags;
   double2* suf64;
-  float2* suf32;
+  float4* suf32p;
   uint32_t* fb;
   uint32_t* fbcount;
   PartM* Lt;
@@ -804,7 +916,7 @@ struct Tables {
 Tables carve(const Plan& L, void* ws) {
   char* b = (char*)ws;
   return {(Pre64*)(b + L.off_pre64), (Pre32*)(b + L.off_pre32), (uint32_t*)(b + L.off_flags),
-          (double2*)(b + L.off_suf64), (float2*)(b + L.off_suf32), (uint32_t*)(b + L.off_fb),
+          (double2*)(b + L.off_suf64), (float4*)(b + L.off_suf32), (uint32_t*)(b + L.off_fb),
           (uint32_t*)(b + L.off_fbcount), (PartM*)(b + L.off_L), (M2*)(b + L.off_H),
           (PartM*)(b + L.off_So), (double2*)(b + L.off_Si)};
 }
@@ -812,7 +924,7 @@ Tables carve(const Plan& L, void* ws) {
 int build_tables(const kl_params* p, const Plan& L, const View& V, const Group& G,
                  const Tables& T, cudaStream_t st) {
   const int mixed = p->precision == KL_MIXED;
-  if (cudaMemsetAsync(T.fbcount, 0, sizeof(uint32_t), st) != cudaSuccess) return KL_ECUDA;
+  if (cudaMemsetAsync(T.fbcount, 0, 2 * sizeof(uint32_t), st) != cudaSuccess) return KL_ECUDA;
   const uint32_t nParts = 4u * L.p3_q1 + (L.p > L.q ? 4u * L.p3_pq : 0u) +
                           (L.so > 0 ? 4u * L.p3_so1 : 0u) + 4u * L.p3_si1;
   parts_kernel<<<(nParts + 63) / 64, 64, 0, st>>>(G, L, (int)p->renorm_every, T.Lt, T.Ht, T.Sot,
@@ -821,8 +933,34 @@ int build_tables(const kl_params* p, const Plan& L, const View& V, const Group& 
   const uint32_t n = 4u * L.np + 4u * L.ns;
   combine_kernel<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(
       V, L, p->parabolic_tol, mixed, T.Lt, T.Ht, T.Sot, T.Sit, T.pre64, T.pre32, T.flags, T.fb,
-      T.fbcount, T.suf64, T.suf32);
+      T.fbcount, T.suf64, (float*)T.suf32p);
   return check_launch();
+}
+
+// SM count and resident blocks per SM of a render kernel on the current device.
+int device_slots(const void* kernel, int* sms, int* occ) {
+  *sms = sm_count();
+  if (*sms <= 0) return KL_ECUDA;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kernel, kThreads, 0) != cudaSuccess ||
+      *occ < 1)
+    return KL_ECUDA;
+  return KL_OK;
+}
+
+// Items of about equal cost, at least ~12 per resident block, so that the
+// block-stride assignment ends within a small fraction of one item.
+Work make_work(const Plan& L, uint32_t units, int slots) {
+  Work W;
+  W.n_pb = (L.np + kThreads - 1) / kThreads;
+  const uint64_t base = 12ull * W.n_pb;
+  const uint64_t target = 12ull * (uint64_t)slots;
+  uint64_t n_chunks = (target + base - 1) / base;
+  if (n_chunks < 1) n_chunks = 1;
+  if (n_chunks > units) n_chunks = units;
+  W.chunk = (uint32_t)((units + n_chunks - 1) / n_chunks);
+  W.n_chunks = (units + W.chunk - 1) / W.chunk;
+  W.n_items = (uint32_t)(base * W.n_chunks);
+  return W;
 }
 
 int validate(const kl_params* p, size_t ws_bytes, void* ws, Plan* L) {
@@ -887,7 +1025,7 @@ extern "C" int kl_eval_words(const kl_params* p, const uint64_t* d_index, uint64
   const unsigned g = (unsigned)(blocks < (uint64_t)sms * 16 ? blocks : (uint64_t)sms * 16);
   eval_kernel<<<g, kThreads, 0, s>>>(d_index, n, kl_word_count(p->depth), G, L, V,
                                      p->precision == KL_MIXED, T.pre64, T.pre32, T.flags,
-                                     T.suf64, T.suf32, d_uv);
+                                     T.suf64, T.suf32p, d_uv);
   return check_launch();
 }
 
@@ -915,29 +1053,25 @@ extern "C" int kl_render(const kl_params* p, uint32_t* d_image, uint64_t* d_coun
   const Tables T = carve(L, d_workspace);
   st = build_tables(p, L, V, G, T, s);
   if (st != KL_OK) return st;
-  const dim3 grid((L.np + kThreads - 1) / kThreads, 12);
+  uint32_t* queue = T.fbcount + 1;
+  int sms = 0, occ = 0;
   if (p->precision == KL_FP64) {
-    const size_t smem = (size_t)L.ns * sizeof(double2);
-    if (cudaFuncSetAttribute(render64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-      return KL_ECUDA;
+    if (device_slots((const void*)render64_kernel, &sms, &occ) != KL_OK) return KL_ECUDA;
+    const Work Wk = make_work(L, L.ns, sms * occ);
     if (prof_mark(g_prof_start, s) != KL_OK) return KL_ECUDA;
-    render64_kernel<<<grid, kThreads, smem, s>>>(T.pre64, T.flags, T.suf64, L, V, d_image, cnt);
+    render64_kernel<<<sms * occ, kThreads, 0, s>>>(T.pre64, T.flags, T.suf64, L, V, Wk, queue,
+                                                    d_image, cnt);
     if (check_launch() != KL_OK) return KL_ECUDA;
     return prof_mark(g_prof_stop, s);
   }
-  const size_t smem = (size_t)L.ns * sizeof(float2);
-  if (cudaFuncSetAttribute(render32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess)
-    return KL_ECUDA;
+  if (device_slots((const void*)render_mixed_kernel, &sms, &occ) != KL_OK) return KL_ECUDA;
+  const Work Wk = make_work(L, L.npairs, sms * occ);
   if (prof_mark(g_prof_start, s) != KL_OK) return KL_ECUDA;
-  render32_kernel<<<grid, kThreads, smem, s>>>(T.pre32, T.flags, T.suf32, L, V, d_image, cnt);
+  render_mixed_kernel<<<sms * occ, kThreads, 0, s>>>(T.pre32, T.pre64, T.flags, T.suf32p, T.suf64,
+                                                     T.fb, T.fbcount, L, V, Wk, queue, d_image,
+                                                     cnt);
   if (check_launch() != KL_OK) return KL_ECUDA;
-  if (prof_mark(g_prof_stop, s) != KL_OK) return KL_ECUDA;
-  const int sms = sm_count();
-  fallback64_kernel<<<sms * 4, kThreads, 0, s>>>(T.pre64, T.flags, T.fb, T.fbcount, T.suf64, L, V,
-                                                  d_image, cnt);
-  return check_launch();
+  return prof_mark(g_prof_stop, s);
 }
 
 extern "C" int kl_set_profile_events(void* ev_start, void* ev_stop) {
