@@ -163,6 +163,32 @@ KL_API int kl_eval_words(const kl_params* p, const uint64_t* d_index, uint64_t n
 KL_API int kl_render(const kl_params* p, uint32_t* d_image, uint64_t* d_counters, void* d_workspace,
               size_t workspace_bytes, void* stream);
 
+/* Size of the library's own device scratch array used by kl_render_noalloc. */
+#define KL_STATIC_SCRATCH_BYTES (32u << 20)
+
+/* kl_render for callers that cannot allocate device memory: the same render,
+ * with the prefix and suffix tables placed in a scratch array compiled into
+ * the library instead of a caller-provided workspace.  Some callers cannot call
+ * cudaMalloc at render time: code embedded in a host application that owns
+ * the whole device heap through its own pool, or a render loop that must run
+ * within a fixed device-memory budget and cannot risk an allocation failure
+ * mid-frame.  They pass only the image and the counters.
+ * There is no counterpart of this call in the paper.
+ *  - The scratch array holds KL_STATIC_SCRATCH_BYTES (32 MiB) on every GPU that
+ *    loads the library, until the process exits, whether or not this call is
+ *    used.  A request whose kl_workspace_bytes(p) exceeds it returns
+ *    KL_ENOSPACE before anything is enqueued.
+ *  - The first call on each device looks up the array's device address with
+ *    that device current (cudaGetSymbolAddress) and caches it; make that first
+ *    call before any stream capture.
+ *  - All calls share the one array, which keeps the last call's tables; the
+ *    render rebuilds and re-zeroes what it needs on every call.  Calls that
+ *    overlap on the GPU (concurrent streams, or several host threads) race on
+ *    the array and give wrong images: serialise them.
+ *  - Neither this call nor anything it calls allocates or frees memory. */
+KL_API int kl_render_noalloc(const kl_params* p, uint32_t* d_image, uint64_t* d_counters,
+                             void* stream);
+
 /* Instrumentation: when set, kl_render records the CUDA events ev_start and
  * ev_stop (cudaEvent_t, created by the caller) on its stream immediately
  * before and after its main per-word kernel (the FP64 or mixed render

@@ -14,7 +14,8 @@ KL_CNT_IN_WINDOW, KL_CNT_DROPPED, KL_CNT_FP64_WORDS, KL_CNT_ATOMICS, KL_N_COUNTE
 # Every function include/kl.h declares, in declaration order.
 API = ("kl_status_string", "kl_word_count", "kl_grandma", "kl_seeds", "kl_params_init",
        "kl_decode_words", "kl_workspace_bytes", "kl_eval_words", "kl_render",
-       "kl_set_profile_events")
+       "kl_render_noalloc", "kl_set_profile_events")
+KL_STATIC_SCRATCH_BYTES = 32 << 20
 
 
 class Params(ctypes.Structure):
@@ -75,6 +76,8 @@ def lib():
         L.kl_eval_words.restype = I
         L.kl_render.argtypes = [ctypes.POINTER(Params), P, P, P, SZ, P]
         L.kl_render.restype = I
+        L.kl_render_noalloc.argtypes = [ctypes.POINTER(Params), P, P, P]
+        L.kl_render_noalloc.restype = I
         L.kl_set_profile_events.argtypes = [P, P]
         L.kl_set_profile_events.restype = I
         _lib = L
@@ -199,6 +202,16 @@ def render(p: Params, image=None, counters=None, workspace=None, stream=None, de
     ws = _workspace(p, image.device, workspace)
     _check(lib().kl_render(ctypes.byref(p), image.data_ptr(), counters.data_ptr(), ws.data_ptr(),
                            ws.numel(), _stream_handle(stream)), "kl_render")
+    return image, counters
+
+
+def render_noalloc(p: Params, image, counters, stream=None):
+    """kl_render_noalloc: render into caller-provided image and counters using
+    the library's own static scratch array (no allocation anywhere)."""
+    if image.numel() != p.width * p.height or image.element_size() != 4 or not image.is_cuda:
+        raise ValueError("image must be a CUDA tensor of width*height 32-bit elements")
+    _check(lib().kl_render_noalloc(ctypes.byref(p), image.data_ptr(), counters.data_ptr(),
+                                   _stream_handle(stream)), "kl_render_noalloc")
     return image, counters
 
 

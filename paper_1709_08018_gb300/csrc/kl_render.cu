@@ -22,6 +22,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "kl.h"
 
 namespace {
@@ -1079,4 +1081,44 @@ extern "C" int kl_set_profile_events(void* ev_start, void* ev_stop) {
   g_prof_start = (cudaEvent_t)ev_start;
   g_prof_stop = (cudaEvent_t)ev_stop;
   return KL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// kl_render without allocation: the workspace is a static device array of this
+// file.  In host code the symbol g_noalloc_scratch is only a host-side stand-in,
+// so its device address is looked up once per device (with that device
+// current) and cached.
+
+namespace {
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[KL_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return KL_ECUDA;
+  if (dev < 0 || dev >= kMaxDevices) return KL_ERANGE;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return KL_ECUDA;
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return KL_OK;
+}
+
+}  // namespace
+
+extern "C" int kl_render_noalloc(const kl_params* p, uint32_t* d_image, uint64_t* d_counters,
+                                 void* stream) {
+  if (!p) return KL_EINVAL;
+  if (kl_workspace_bytes(p) > KL_STATIC_SCRATCH_BYTES) return KL_ENOSPACE;
+  void* scratch = nullptr;
+  const int st = noalloc_scratch(&scratch);
+  if (st != KL_OK) return st;
+  return kl_render(p, d_image, d_counters, scratch, KL_STATIC_SCRATCH_BYTES, stream);
 }
