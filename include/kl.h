@@ -89,6 +89,10 @@ typedef struct {
   uint32_t prefix_len;     /* letters per cached prefix matrix (0 = choose) */
   uint32_t accumulate;     /* 0: kl_render zeroes the image and counters first;
                               1: it adds to them */
+  uint32_t block_threads;  /* threads per block of the render kernels: 64, 128 or 256
+                              (0 = 128); a tuning knob, results do not depend on it */
+  uint32_t chunk_pairs;    /* suffix-point pairs per work item (FP64: twice as many points);
+                              0 = choose; a tuning knob, results do not depend on it */
 } kl_params;
 
 /* Counters written by kl_render (uint64 each). */
@@ -162,6 +166,52 @@ KL_API int kl_eval_words(const kl_params* p, const uint64_t* d_index, uint64_t n
  * value is outside the window or not finite are dropped and counted. */
 KL_API int kl_render(const kl_params* p, uint32_t* d_image, uint64_t* d_counters, void* d_workspace,
               size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched render: a sweep over many groups in one persistent launch.
+ *
+ * n_groups parameter sets with their own traces/generators, seeds, depth and
+ * prefix_len, sharing precision, image size, window, renorm_every,
+ * parabolic_tol and the tuning knobs of params[0].  Every group's words are
+ * rendered exactly as kl_render would render them, into its own image:
+ * d_images holds n_groups images of width*height uint32, group k at offset
+ * k*width*height; d_counters holds n_groups * KL_N_COUNTERS uint64.  All
+ * groups' work items share one device queue (FP64 fallback items first), so
+ * groups of uneven depth balance across the GPU in a single launch of the
+ * render kernel.  Images and counters are zeroed by each render (accumulate
+ * is ignored).
+ *
+ * A kl_batch is a host-side handle (it owns host memory and, after
+ * kl_batch_capture, a CUDA graph); all device memory is the caller's.
+ */
+typedef struct kl_batch kl_batch;
+
+/* Validate the parameter sets and plan the batch on the current device.
+ * *out receives a handle to free with kl_batch_destroy.  KL_EINVAL if the sets
+ * do not share precision, image size and window; other codes as kl_render. */
+KL_API int kl_batch_create(const kl_params* params, uint32_t n_groups, kl_batch** out);
+
+/* Device workspace bytes the batch needs (256-byte aligned), 0 on a null handle. */
+KL_API size_t kl_batch_workspace_bytes(const kl_batch* b);
+
+/* Enqueue the whole batch on `stream`: upload of the group descriptors (from
+ * host memory owned by the handle), zeroing, the table passes and the one
+ * persistent render launch. */
+KL_API int kl_batch_render(kl_batch* b, uint32_t* d_images, uint64_t* d_counters,
+                           void* d_workspace, size_t workspace_bytes, void* stream);
+
+/* Capture the batch into a CUDA graph held by the handle (the descriptors are
+ * uploaded first, outside the graph; the graph holds the zeroing, the table
+ * passes and the render launch).  The buffers must stay valid while the graph
+ * is replayed.  `stream` must not be capturing already. */
+KL_API int kl_batch_capture(kl_batch* b, uint32_t* d_images, uint64_t* d_counters,
+                            void* d_workspace, size_t workspace_bytes, void* stream);
+
+/* Launch the captured graph on `stream`.  KL_EINVAL if nothing was captured. */
+KL_API int kl_batch_replay(kl_batch* b, void* stream);
+
+/* Free the handle and its graph (after the work using it has finished). */
+KL_API void kl_batch_destroy(kl_batch* b);
 
 /* Size of the library's own device scratch array used by kl_render_noalloc. */
 #define KL_STATIC_SCRATCH_BYTES (32u << 20)

@@ -9,7 +9,7 @@ and fails loudly if it has not been built (``__graft_entry__.build()`` or
 """
 from .binding import (  # noqa: F401
     KL_CNT_ATOMICS, KL_CNT_DROPPED, KL_CNT_FP64_WORDS, KL_CNT_IN_WINDOW, KL_N_COUNTERS,
-    FP64, MIXED, KlError, Params, Renderer, decode_words, eval_words, exported_symbols,
+    Batch, FP64, MIXED, KlError, Params, Renderer, decode_words, eval_words, exported_symbols,
     grandma, lib, params_init, render, render_noalloc, seeds, set_profile_events, status_string, word_count,
     workspace_bytes,
 )

@@ -14,7 +14,8 @@ KL_CNT_IN_WINDOW, KL_CNT_DROPPED, KL_CNT_FP64_WORDS, KL_CNT_ATOMICS, KL_N_COUNTE
 # Every function include/kl.h declares, in declaration order.
 API = ("kl_status_string", "kl_word_count", "kl_grandma", "kl_seeds", "kl_params_init",
        "kl_decode_words", "kl_workspace_bytes", "kl_eval_words", "kl_render",
-       "kl_render_noalloc", "kl_set_profile_events")
+       "kl_batch_create", "kl_batch_workspace_bytes", "kl_batch_render", "kl_batch_capture",
+       "kl_batch_replay", "kl_batch_destroy", "kl_render_noalloc", "kl_set_profile_events")
 KL_STATIC_SCRATCH_BYTES = 32 << 20
 
 
@@ -35,6 +36,8 @@ class Params(ctypes.Structure):
         ("parabolic_tol", ctypes.c_double),
         ("prefix_len", ctypes.c_uint32),
         ("accumulate", ctypes.c_uint32),
+        ("block_threads", ctypes.c_uint32),
+        ("chunk_pairs", ctypes.c_uint32),
     ]
 
 
@@ -76,6 +79,17 @@ def lib():
         L.kl_eval_words.restype = I
         L.kl_render.argtypes = [ctypes.POINTER(Params), P, P, P, SZ, P]
         L.kl_render.restype = I
+        L.kl_batch_create.argtypes = [ctypes.POINTER(Params), U32, ctypes.POINTER(P)]
+        L.kl_batch_create.restype = I
+        L.kl_batch_workspace_bytes.argtypes = [P]
+        L.kl_batch_workspace_bytes.restype = SZ
+        for fn in (L.kl_batch_render, L.kl_batch_capture):
+            fn.argtypes = [P, P, P, P, SZ, P]
+            fn.restype = I
+        L.kl_batch_replay.argtypes = [P, P]
+        L.kl_batch_replay.restype = I
+        L.kl_batch_destroy.argtypes = [P]
+        L.kl_batch_destroy.restype = None
         L.kl_render_noalloc.argtypes = [ctypes.POINTER(Params), P, P, P]
         L.kl_render_noalloc.restype = I
         L.kl_set_profile_events.argtypes = [P, P]
@@ -213,6 +227,58 @@ def render_noalloc(p: Params, image, counters, stream=None):
     _check(lib().kl_render_noalloc(ctypes.byref(p), image.data_ptr(), counters.data_ptr(),
                                    _stream_handle(stream)), "kl_render_noalloc")
     return image, counters
+
+
+class Batch:
+    """A batched render of many groups (kl_batch_*): one persistent launch,
+    optionally captured once in a CUDA graph and replayed."""
+
+    def __init__(self, params, device="cuda"):
+        torch = _torch()
+        n = len(params)
+        arr = (Params * n)(*params)
+        h = ctypes.c_void_p()
+        _check(lib().kl_batch_create(arr, n, ctypes.byref(h)), "kl_batch_create")
+        self.handle = h
+        self.n = n
+        self.width, self.height = params[0].width, params[0].height
+        need = int(lib().kl_batch_workspace_bytes(h))
+        self.workspace = torch.empty(need, dtype=torch.uint8, device=device)
+        self.images = torch.empty((n, self.height, self.width), dtype=torch.int32, device=device)
+        self.counters = torch.zeros((n, KL_N_COUNTERS), dtype=torch.int64, device=device)
+        self.captured = False
+
+    def _args(self):
+        return (self.handle, self.images.data_ptr(), self.counters.data_ptr(),
+                self.workspace.data_ptr(), self.workspace.numel())
+
+    def render(self, stream=None):
+        _check(lib().kl_batch_render(*self._args(), _stream_handle(stream)), "kl_batch_render")
+        return self.images, self.counters
+
+    def capture(self):
+        """Capture the batch into a CUDA graph (on a side stream: the legacy
+        default stream cannot be captured)."""
+        torch = _torch()
+        side = torch.cuda.Stream(device=self.images.device)
+        side.wait_stream(torch.cuda.current_stream(self.images.device))
+        _check(lib().kl_batch_capture(*self._args(), side.cuda_stream), "kl_batch_capture")
+        torch.cuda.current_stream(self.images.device).wait_stream(side)
+        self.captured = True
+
+    def replay(self, stream=None):
+        _check(lib().kl_batch_replay(self.handle, _stream_handle(stream)), "kl_batch_replay")
+        return self.images, self.counters
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib is not None:
+            try:
+                _torch().cuda.synchronize()
+            except Exception:
+                pass
+            _lib.kl_batch_destroy(h)
+            self.handle = None
 
 
 def set_profile_events(start=None, stop=None):

@@ -1,0 +1,843 @@
+// Shared device code of the indexed limit-set renderer (sm_103a): data
+// layouts, the per-word arithmetic, the table builders and the per-item render
+// bodies used by both the single render (kl_render.cu) and the batched render
+// (kl_batch.cu).
+//
+// A reduced word w_1 .. w_d is split into a prefix w_1 .. w_p (the letters
+// applied last) and a suffix w_{p+1} .. w_d (applied first, starting from the
+// seed of w_d).  Its value is P(v): P = M_{w_1} ... M_{w_p} is the prefix
+// matrix and v the suffix point.  The index of the word factors the same
+// way: i = (prefix index) * 3^s + (suffix digits), so instead of decoding i
+// digit by digit for every word, the kernels decode each prefix once (a table
+// of prefix constants) and each suffix once (a table of suffix points) and
+// enumerate the compatible pairs (suffix first letter != inverse of the prefix
+// last letter, Sec. "Once-punctured torus groups").
+//
+// Per word the only work left is one linear-fractional map and a splat.  With
+// det P = D the map is written in pole form
+//     P(v) = alpha + beta / (v + gamma),
+//     alpha = P00/P10, gamma = P11/P10, beta = -D/P10^2,
+// and folded into pixel units, u = (Re z - x0) sx = ax + (c1 wr + c2 wi)/|w|^2,
+// row coordinate v = (y1 - Im z) sy = ay + (c3 wr + c4 wi)/|w|^2, w = v + gamma:
+// 13 FP64 operations and one reciprocal seed per word.  Pixel binning uses
+// only integer operations.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "kl.h"
+
+namespace {
+
+constexpr int kMaxPrefix = 15;
+constexpr int kMaxSuffix = 9;
+constexpr int kMaxRenderDepth = kMaxPrefix + kMaxSuffix;
+constexpr int kDefaultThreads = 128;
+
+// Prefix flags.
+constexpr uint32_t kDirect = 1u;     // P10 ~ 0: pole form invalid, use the direct map
+constexpr uint32_t kNearPar = 2u;    // |tr^2 - 4 det| small: near-parabolic (cusp) prefix
+constexpr uint32_t kWide = 4u;       // local FP32 frame unsafe (far or huge offsets)
+constexpr uint32_t kFallback = 8u;   // KL_MIXED: words of this prefix run in FP64
+
+// FP64 fallback work unit: a chunk of this many suffix points.
+constexpr uint32_t kFbChunk = 64;
+
+struct Plan {
+  int d, p, s;
+  int q;         // letters of the prefix tail table (the rest, p - q, in the head table)
+  int so, si;    // letters of the suffix head (matrix) and tail (point) tables
+  uint32_t np;   // prefix slots per last letter: 3^(p-1)
+  uint32_t ns;   // suffix points per first letter: 3^(s-1)
+  uint32_t npairs;  // FP32 point pairs per first letter: ceil(ns / 2)
+  uint32_t p3_q1, p3_pq, p3_so1, p3_si, p3_si1;  // 3^(q-1), 3^(p-q), 3^(so-1), 3^si, 3^(si-1)
+  size_t off_pre64, off_pre32, off_flags, off_suf64, off_suf32, off_fb, off_fbcount;
+  size_t off_L, off_H, off_So, off_Si, total;
+};
+
+struct View {
+  double x0, y1, sx, sy;
+  uint32_t W, H;
+  uint32_t hiW, hiH;  // high words of (double)W and (double)H
+};
+
+struct Group {
+  double g[32];
+  double seed[8];
+};
+
+struct __align__(16) Pre64 {
+  double gr, gi, ax, ay, c1, c2, c3, c4;  // pole form; or P00..P11 (re, im) if kDirect
+};
+
+struct __align__(16) Pre32 {
+  float gr, gi, axf, ayf, c1, c2, c3, c4;
+  int axi, ayi;  // integer part of the pixel coordinates of alpha
+  int kx, ky;    // 0x4B400000 - axi, 0x4B400000 - ayi (see mixed_item)
+};
+
+struct dc {
+  double re, im;
+};
+
+struct M2 {
+  dc p, q, r, s;
+};
+
+struct __align__(16) PartM {
+  M2 m;
+  int edge;  // L: its outermost letter w_{p-q+1}; So: its innermost letter w_{p+so}
+  int pad[3];
+};
+
+// Device tables of one render, carved from the caller's workspace.
+struct Tables {
+  Pre64* pre64;
+  Pre32* pre32;
+  uint32_t* flags;
+  double2* suf64;
+  float4* suf32p;
+  unsigned long long* fb;  // fallback entries: (group << 32) | prefix slot
+  uint32_t* fbcount;       // [0] fallback entries, [1] work-queue head
+  PartM* Lt;
+  M2* Ht;
+  PartM* Sot;
+  double2* Sit;
+};
+
+// Work items of the persistent render kernels: item = (q, prefix block pb,
+// suffix chunk c), chunk index fastest.  q = 3 x + k enumerates the 12
+// compatible (prefix last letter x, suffix first letter u) pairs, u being the
+// k-th letter other than inv(x); thread t of the block takes prefix slot
+// (x, pb * BT + t) and the chunk's suffix points.
+struct Work {
+  uint32_t n_pb;      // prefix blocks per letter: ceil(np / BT)
+  uint32_t n_chunks;  // suffix chunks per first letter
+  uint32_t chunk;     // suffix points (FP64) or point pairs (FP32) per chunk
+  uint32_t n_items;   // 12 * n_pb * n_chunks
+};
+
+// ---------------------------------------------------------------------------
+// complex FP64 helpers (tables only; the per-word code spells out its ops)
+
+__device__ __forceinline__ dc cadd(dc a, dc b) { return {a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ dc csub(dc a, dc b) { return {a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ dc cmul(dc a, dc b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+__device__ __forceinline__ dc cdiv(dc n, dc m) {
+  double den = m.re * m.re + m.im * m.im;
+  return {(n.re * m.re + n.im * m.im) / den, (n.im * m.re - n.re * m.im) / den};
+}
+__device__ __forceinline__ double cabs1(dc a) { return fabs(a.re) + fabs(a.im); }
+// principal square root
+__device__ __forceinline__ dc csqrt(dc a) {
+  double r = hypot(a.re, a.im);
+  if (r == 0.0) return {0.0, 0.0};
+  double t = sqrt(0.5 * (r + fabs(a.re)));
+  if (a.re >= 0.0) return {t, a.im / (2.0 * t)};
+  return {fabs(a.im) / (2.0 * t), copysign(t, a.im)};
+}
+// 1/z for z != 0: conj(z) / |z|^2 with one real division
+__device__ __forceinline__ dc crcp(dc z) {
+  const double t = 1.0 / (z.re * z.re + z.im * z.im);
+  return {z.re * t, -z.im * t};
+}
+
+__device__ __forceinline__ M2 load_gen(const Group& G, int x) {
+  const double* g = G.g + 8 * x;
+  return {{g[0], g[1]}, {g[2], g[3]}, {g[4], g[5]}, {g[6], g[7]}};
+}
+__device__ __forceinline__ M2 mmul(const M2& a, const M2& b) {
+  return {cadd(cmul(a.p, b.p), cmul(a.q, b.r)), cadd(cmul(a.p, b.q), cmul(a.q, b.s)),
+          cadd(cmul(a.r, b.p), cmul(a.s, b.r)), cadd(cmul(a.r, b.q), cmul(a.s, b.s))};
+}
+__device__ __forceinline__ dc mdet(const M2& a) { return csub(cmul(a.p, a.s), cmul(a.q, a.r)); }
+// divide by the principal square root of the determinant
+__device__ __forceinline__ void renormalise(M2& a) {
+  dc k = csqrt(mdet(a));
+  if (k.re == 0.0 && k.im == 0.0) return;
+  k = crcp(k);
+  a.p = cmul(a.p, k); a.q = cmul(a.q, k); a.r = cmul(a.r, k); a.s = cmul(a.s, k);
+}
+__device__ __forceinline__ M2 identity2() {
+  return {{1.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {1.0, 0.0}};
+}
+__device__ __forceinline__ dc mobius(const M2& m, dc z) {
+  return cmul(cadd(cmul(m.p, z), m.q), crcp(cadd(cmul(m.r, z), m.s)));
+}
+
+// ---------------------------------------------------------------------------
+// per-word arithmetic, shared by the render kernels and the evaluation kernel
+
+// FP64 reciprocal: hardware seed (rcp.approx.ftz.f64) refined by one cubic
+// Newton-Raphson step y <- y (1 + e + e^2), e = 1 - m y (Householder order 3).
+__device__ __forceinline__ double rcp64(double m) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(m));
+  double e = __fma_rn(-m, y, 1.0);
+  double e2 = __fma_rn(e, e, e);
+  return __fma_rn(y, e2, y);
+}
+
+__device__ __forceinline__ float rcp32(float m) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(m));
+  return y;
+}
+
+__device__ __forceinline__ void uv_pole64(const Pre64& c, double vr, double vi, double& u,
+                                          double& v) {
+  double wr = __dadd_rn(vr, c.gr);
+  double wi = __dadd_rn(vi, c.gi);
+  double m = __fma_rn(wr, wr, __dmul_rn(wi, wi));
+  double r = rcp64(m);
+  double tx = __fma_rn(c.c1, wr, __dmul_rn(c.c2, wi));
+  double ty = __fma_rn(c.c3, wr, __dmul_rn(c.c4, wi));
+  u = __fma_rn(tx, r, c.ax);
+  v = __fma_rn(ty, r, c.ay);
+}
+
+// Direct form for prefixes whose P10 vanishes: z = (P00 v + P01)/(P10 v + P11).
+__device__ __forceinline__ void uv_direct64(const Pre64& c, double vr, double vi,
+                                            const View& V, double& u, double& v) {
+  dc P00 = {c.gr, c.gi}, P01 = {c.ax, c.ay}, P10 = {c.c1, c.c2}, P11 = {c.c3, c.c4};
+  dc z = {vr, vi};
+  dc w = cdiv(cadd(cmul(P00, z), P01), cadd(cmul(P10, z), P11));
+  u = (w.re - V.x0) * V.sx;
+  v = (V.y1 - w.im) * V.sy;
+}
+
+// Scalar form of the mixed per-word map (the evaluation kernel); the render
+// evaluates the same operations two words at a time.
+__device__ __forceinline__ void uv_pole32(const Pre32& c, float vr, float vi, float& uf,
+                                          float& vf) {
+  float wr = __fadd_rn(vr, c.gr);
+  float wi = __fadd_rn(vi, c.gi);
+  float m = __fmaf_rn(wr, wr, __fmul_rn(wi, wi));
+  float r = rcp32(m);
+  float tx = __fmaf_rn(c.c1, wr, __fmul_rn(c.c2, wi));
+  float ty = __fmaf_rn(c.c3, wr, __fmul_rn(c.c4, wi));
+  uf = __fmaf_rn(tx, r, c.axf);
+  vf = __fmaf_rn(ty, r, c.ayf);
+}
+
+// floor of a double in [0, 2^20) from its high word alone
+__device__ __forceinline__ uint32_t floor_hi(uint32_t h) {
+  int e = (int)(h >> 20) - 1023;
+  uint32_t mant = (h & 0xFFFFFu) | 0x100000u;
+  return e < 0 ? 0u : (mant >> (20 - e));
+}
+
+// Pixel id (row * W + col) of pixel coordinates (u, v), or -1 if outside
+// [0, W) x [0, H) or not finite.  For u >= 0, u < W iff hi(u) < hi(W) because
+// the low word of an integer below 2^20 is zero; negative values, infinities
+// and NaNs all have high words above hi(W).
+__device__ __forceinline__ int pixel64(double u, double v, const View& V) {
+  uint32_t hu = (uint32_t)__double2hiint(u);
+  uint32_t hv = (uint32_t)__double2hiint(v);
+  if (hu >= V.hiW || hv >= V.hiH) return -1;
+  return (int)(floor_hi(hv) * V.W + floor_hi(hu));
+}
+
+// Packed FP32 pairs (Blackwell f32x2 add/mul/fma): two words per instruction,
+// each half rounded exactly as the scalar operation.
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 pk(float lo, float hi) {
+  f2 d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ void upk(f2 a, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 add2_rm(f2 a, f2 b) {
+  f2 d;
+  asm("add.rm.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// ---------------------------------------------------------------------------
+// words and tables
+
+__device__ __forceinline__ int allowed_letter(int digit, int ban) {
+  return digit + (digit >= ban ? 1 : 0);
+}
+
+// Index -> letters w_1 .. w_d: w_1 = i / 3^(d-1), then each base-3 digit picks
+// the digit-th letter other than the inverse of the letter before it.
+__device__ __forceinline__ void decode_word(uint64_t i, int d, int* w) {
+  for (int k = d - 1; k >= 1; --k) {
+    w[k] = (int)(i % 3u);
+    i /= 3u;
+  }
+  w[0] = (int)i;
+  for (int k = 1; k < d; ++k) w[k] = allowed_letter(w[k], (w[k - 1] + 2) & 3);
+}
+
+// Tables are built in two passes.  The parts pass builds four small tables:
+//   L: prefix tails, the q innermost prefix letters w_{p-q+1} .. w_p, as a
+//      matrix, slot (x = w_p, base-3 ranks of w_{p-1} .. w_{p-q+1});
+//   H: prefix heads w_1 .. w_{p-q}, slot (y = the letter right of the head,
+//      base-3 ranks of w_{p-q} .. w_1);
+//   So: suffix heads w_{p+1} .. w_{p+so} as a matrix, slot (u = w_{p+1}, ranks);
+//   Si: suffix tails w_{p+so+1} .. w_d applied to the seed of w_d, one map at a
+//      time, slot (z = w_{p+so+1}, ranks).
+// The combine pass then forms every prefix matrix P = H L (one 2x2 product)
+// and its pole-form constants, and every suffix point v = So(Si) (one map).
+// Each L, H and So matrix is renormalised to det 1 every `renorm` letters and
+// at its end; P is not renormalised (its determinant enters beta explicitly).
+// The slot numbering is the same as for a single-level decode: a prefix slot
+// (x, r) has r = r_L 3^(p-q) + r_H, a suffix slot (u, j) has
+// j = j_So 3^si + rank(z) 3^(si-1) + j_Si.
+
+__host__ __device__ __forceinline__ uint32_t parts_count(const Plan& L) {
+  return 4u * L.p3_q1 + (L.p > L.q ? 4u * L.p3_pq : 0u) + (L.so > 0 ? 4u * L.p3_so1 : 0u) +
+         4u * L.p3_si1;
+}
+__host__ __device__ __forceinline__ uint32_t combine_count(const Plan& L) {
+  return 4u * L.np + 4u * L.ns;
+}
+
+__device__ void part_entry(const Group& G, const Plan& L, int renorm, uint32_t idx,
+                           const Tables& T) {
+  const uint32_t nL = 4u * L.p3_q1, nH = L.p > L.q ? 4u * L.p3_pq : 0u;
+  const uint32_t nSo = L.so > 0 ? 4u * L.p3_so1 : 0u;
+  if (idx < nL + nH) {
+    // prefix part: letters taken right to left, matrix built by prepending
+    const bool tail = idx < nL;
+    const uint32_t slot = tail ? idx : idx - nL;
+    const uint32_t per = tail ? L.p3_q1 : L.p3_pq;
+    const int first = (int)(slot / per);
+    const uint32_t r = slot % per;
+    const int nlet = tail ? L.q - 1 : L.p - L.q;  // letters chosen by digits
+    M2 P = tail ? load_gen(G, first) : identity2();
+    int right = first;
+    uint32_t place = per / 3u;
+    int used = tail ? 1 : 0;
+    for (int k = 0; k < nlet; ++k) {
+      const int digit = (int)((r / place) % 3u);
+      place /= 3u;
+      const int w = allowed_letter(digit, (right + 2) & 3);
+      P = mmul(load_gen(G, w), P);
+      right = w;
+      if (renorm > 0 && (++used % renorm) == 0) renormalise(P);
+    }
+    if (renorm > 0 && (used % renorm) != 0) renormalise(P);
+    if (tail) {
+      PartM e;
+      e.m = P;
+      e.edge = right;
+      e.pad[0] = e.pad[1] = e.pad[2] = 0;
+      T.Lt[slot] = e;
+    } else {
+      T.Ht[slot] = P;
+    }
+  } else if (idx < nL + nH + nSo) {
+    // suffix head: letters left to right, matrix built by appending
+    const uint32_t slot = idx - nL - nH;
+    const int u = (int)(slot / L.p3_so1);
+    const uint32_t j = slot % L.p3_so1;
+    M2 S = load_gen(G, u);
+    int left = u, used = 1;
+    uint32_t place = L.p3_so1 / 3u;
+    for (int k = 1; k < L.so; ++k) {
+      const int digit = (int)((j / place) % 3u);
+      place /= 3u;
+      const int w = allowed_letter(digit, (left + 2) & 3);
+      S = mmul(S, load_gen(G, w));
+      left = w;
+      if (renorm > 0 && (++used % renorm) == 0) renormalise(S);
+    }
+    if (renorm > 0 && (used % renorm) != 0) renormalise(S);
+    PartM e;
+    e.m = S;
+    e.edge = left;
+    e.pad[0] = e.pad[1] = e.pad[2] = 0;
+    T.Sot[slot] = e;
+  } else {
+    // suffix tail: the orbit of the seed of w_d, innermost letter first
+    const uint32_t slot = idx - nL - nH - nSo;
+    int w[kMaxSuffix];
+    w[0] = (int)(slot / L.p3_si1);
+    const uint32_t j = slot % L.p3_si1;
+    uint32_t place = L.p3_si1 / 3u;
+    for (int k = 1; k < L.si; ++k) {
+      const int digit = (int)((j / place) % 3u);
+      place /= 3u;
+      w[k] = allowed_letter(digit, (w[k - 1] + 2) & 3);
+    }
+    const int last = w[L.si - 1];
+    dc z = {G.seed[2 * last], G.seed[2 * last + 1]};
+    for (int k = L.si - 1; k >= 0; --k) z = mobius(load_gen(G, w[k]), z);
+    T.Sit[slot] = make_double2(z.re, z.im);
+  }
+}
+
+// Combine pass entry idx (prefix slots first, then suffix slots).  Fallback
+// prefixes (mixed mode) are appended to fb_list as (group << 32) | slot.
+__device__ void combine_entry(const View& V, const Plan& L, double ptol, int mixed,
+                              uint32_t idx, const Tables& T, uint32_t group,
+                              unsigned long long* __restrict__ fb_list,
+                              uint32_t* __restrict__ fb_count) {
+  const uint32_t nP = 4u * L.np;
+  if (idx >= nP) {
+    const uint32_t slot = idx - nP;
+    double2 v;
+    if (L.so == 0) {
+      v = T.Sit[slot];
+    } else {
+      const int u = (int)(slot / L.ns);
+      const uint32_t j = slot % L.ns;
+      const uint32_t j_so = j / L.p3_si, rem = j % L.p3_si;
+      const PartM& S = T.Sot[(uint32_t)u * L.p3_so1 + j_so];
+      const int z = allowed_letter((int)(rem / L.p3_si1), (S.edge + 2) & 3);
+      const double2 t = T.Sit[(uint32_t)z * L.p3_si1 + rem % L.p3_si1];
+      const dc r = mobius(S.m, {t.x, t.y});
+      v = make_double2(r.re, r.im);
+    }
+    T.suf64[slot] = v;
+    // pair-interleaved FP32 table: per first letter u, entry k holds
+    // (re v_2k, re v_2k+1, im v_2k, im v_2k+1); an odd count is padded with NaN
+    const uint32_t u = slot / L.ns, j = slot % L.ns;
+    float* e = (float*)T.suf32p + 4ull * ((uint64_t)u * L.npairs + j / 2u);
+    e[j & 1u] = (float)v.x;
+    e[2 + (j & 1u)] = (float)v.y;
+    if (j + 1u == L.ns && (L.ns & 1u)) {
+      e[1] = __int_as_float(0x7FC00000);
+      e[3] = __int_as_float(0x7FC00000);
+    }
+    return;
+  }
+  const uint32_t slot = idx;
+  const int x = (int)(slot / L.np);
+  const uint32_t r = slot % L.np;
+  const PartM& TL = T.Lt[(uint32_t)x * L.p3_q1 + r / L.p3_pq];
+  const M2 P = L.p > L.q ? mmul(T.Ht[(uint32_t)TL.edge * L.p3_pq + r % L.p3_pq], TL.m) : TL.m;
+  const dc det = mdet(P);
+  const dc tr = cadd(P.p, P.s);
+  const double scale = fmax(fmax(cabs1(P.p), cabs1(P.q)), fmax(cabs1(P.r), cabs1(P.s)));
+  uint32_t fl = 0;
+  const dc tr2m4 = csub(cmul(tr, tr), {4.0 * det.re, 4.0 * det.im});
+  const double t2 = tr.re * tr.re + tr.im * tr.im;
+  const double lim2 = ptol * fmax(1.0, t2);
+  if (tr2m4.re * tr2m4.re + tr2m4.im * tr2m4.im < lim2 * lim2) fl |= kNearPar;
+  Pre64 c64;
+  Pre32 c32;
+  if (!(cabs1(P.r) > 1e-12 * scale)) {
+    fl |= kDirect;
+    c64 = {P.p.re, P.p.im, P.q.re, P.q.im, P.r.re, P.r.im, P.s.re, P.s.im};
+    c32 = {};
+  } else {
+    const dc inv10 = crcp(P.r);
+    const dc alpha = cmul(P.p, inv10);
+    const dc gamma = cmul(P.s, inv10);
+    const dc mbeta = cmul(det, cmul(inv10, inv10));  // -beta
+    const double ax = (alpha.re - V.x0) * V.sx;
+    const double ay = (V.y1 - alpha.im) * V.sy;
+    const double c1 = -V.sx * mbeta.re, c2 = -V.sx * mbeta.im;
+    const double c3 = V.sy * mbeta.im, c4 = -V.sy * mbeta.re;
+    c64 = {gamma.re, gamma.im, ax, ay, c1, c2, c3, c4};
+    const double lim = 1048576.0;  // 2^20
+    if (!(fabs(ax) < lim && fabs(ay) < lim && fabs(gamma.re) < 1e15 && fabs(gamma.im) < 1e15))
+      fl |= kWide;
+    const double axi = floor(fmax(fmin(ax, lim), -lim));
+    const double ayi = floor(fmax(fmin(ay, lim), -lim));
+    c32.gr = (float)gamma.re;
+    c32.gi = (float)gamma.im;
+    c32.axf = (float)(ax - axi);
+    c32.ayf = (float)(ay - ayi);
+    c32.c1 = (float)c1;
+    c32.c2 = (float)c2;
+    c32.c3 = (float)c3;
+    c32.c4 = (float)c4;
+    c32.axi = (int)axi;
+    c32.ayi = (int)ayi;
+    c32.kx = 0x4B400000 - (int)axi;
+    c32.ky = 0x4B400000 - (int)ayi;
+  }
+  if (mixed && (fl & (kDirect | kNearPar | kWide))) {
+    fl |= kFallback;
+    const uint32_t k = atomicAdd(fb_count, 1u);
+    fb_list[k] = ((unsigned long long)group << 32) | slot;
+  }
+  T.pre64[slot] = c64;
+  T.pre32[slot] = c32;
+  T.flags[slot] = fl;
+}
+
+// ---------------------------------------------------------------------------
+// splat
+
+// Run-length tally of one thread's words.  Consecutive words of a thread
+// differ only in their innermost letters, so they usually land in the same
+// pixel; a run of equal pixels becomes one atomic add.  pix < 0 marks a
+// dropped word (such runs are discarded).
+struct Tally {
+  uint32_t in_window = 0, atomics = 0;
+  int cur = -1;
+  uint32_t run = 0;
+
+  __device__ __forceinline__ void flush(uint32_t* __restrict__ img) {
+    if (cur >= 0 && run) {
+      atomicAdd(img + cur, run);
+      ++atomics;
+      in_window += run;
+    }
+    run = 0;
+  }
+  __device__ __forceinline__ void add(int pix, uint32_t* __restrict__ img) {
+    if (pix != cur) {
+      flush(img);
+      cur = pix;
+    }
+    ++run;
+  }
+};
+
+struct UnitTally {
+  uint32_t words, in_window, atomics;
+};
+
+// Warp-sum the four counters and add them once per warp (all lanes must call).
+__device__ __forceinline__ void publish_counts(uint32_t in_window, uint32_t words,
+                                               uint32_t fp64_words, uint32_t atomics,
+                                               unsigned long long* counters) {
+  unsigned long long a = in_window, b = words - in_window, c = fp64_words, e = atomics;
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xFFFFFFFFu, a, o);
+    b += __shfl_down_sync(0xFFFFFFFFu, b, o);
+    c += __shfl_down_sync(0xFFFFFFFFu, c, o);
+    e += __shfl_down_sync(0xFFFFFFFFu, e, o);
+  }
+  if ((threadIdx.x & 31) == 0 && counters) {
+    if (a) atomicAdd(counters + KL_CNT_IN_WINDOW, a);
+    if (b) atomicAdd(counters + KL_CNT_DROPPED, b);
+    if (c) atomicAdd(counters + KL_CNT_FP64_WORDS, c);
+    if (e) atomicAdd(counters + KL_CNT_ATOMICS, e);
+  }
+}
+
+__device__ __forceinline__ uint32_t next_item(uint32_t* queue) {
+  __shared__ uint32_t s_item;
+  __syncthreads();
+  if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
+  __syncthreads();
+  return s_item;
+}
+
+__device__ __forceinline__ void item_of(uint32_t item, const Work& W, int& x, int& u,
+                                        uint32_t& pb, uint32_t& c) {
+  c = item % W.n_chunks;
+  const uint32_t t = item / W.n_chunks;
+  pb = t % W.n_pb;
+  const int q = (int)(t / W.n_pb);
+  x = q / 3;
+  u = allowed_letter(q % 3, (x + 2) & 3);
+}
+
+// FP64 words of one prefix slot on suffix points [j0, j1) of one first letter.
+__device__ __forceinline__ void words64(const Pre64& k, bool direct, const double2* src,
+                                        uint32_t j0, uint32_t j1, const View& V, Tally& t,
+                                        uint32_t* __restrict__ img) {
+  if (direct) {
+    for (uint32_t j = j0; j < j1; ++j) {
+      double uu, vv;
+      const double2 s = __ldg(src + j);
+      uv_direct64(k, s.x, s.y, V, uu, vv);
+      t.add(pixel64(uu, vv, V), img);
+    }
+  } else {
+#pragma unroll 2
+    for (uint32_t j = j0; j < j1; ++j) {
+      double uu, vv;
+      const double2 s = __ldg(src + j);
+      uv_pole64(k, s.x, s.y, uu, vv);
+      t.add(pixel64(uu, vv, V), img);
+    }
+  }
+  t.flush(img);
+}
+
+// One FP64 item of a plain render: words of this thread's prefix on one chunk.
+template <int BT>
+__device__ __forceinline__ void fp64_item(uint32_t item, const Work& Wk, const Plan& L,
+                                          const View& V, const Tables& T, Tally& t,
+                                          uint32_t& words, uint32_t* __restrict__ img) {
+  int x, u;
+  uint32_t pb, c;
+  item_of(item, Wk, x, u, pb, c);
+  const uint32_t r = pb * BT + threadIdx.x;
+  if (r >= L.np) return;
+  const uint32_t slot = (uint32_t)x * L.np + r;
+  const uint32_t j0 = c * Wk.chunk, j1 = min(L.ns, j0 + Wk.chunk);
+  words64(T.pre64[slot], T.flags[slot] & kDirect, T.suf64 + (size_t)u * L.ns, j0, j1, V, t,
+          img);
+  words += j1 - j0;
+}
+
+// Mixed-mode FP64 fallback unit (kept out of line so that its registers do
+// not bind the FP32 loop): (fallback prefix, one of its three suffix letters,
+// a chunk of kFbChunk suffix points).  Chunks past the end are empty.
+__device__ __noinline__ UnitTally fallback_unit(const Pre64* __restrict__ pre,
+                                                const uint32_t* __restrict__ flags,
+                                                const double2* __restrict__ suf, uint32_t slot,
+                                                uint32_t k, uint32_t c, uint32_t np, uint32_t ns,
+                                                View V, uint32_t* __restrict__ img) {
+  const int x = (int)(slot / np);
+  const int u = allowed_letter((int)k, (x + 2) & 3);
+  const uint32_t j0 = c * kFbChunk;
+  if (j0 >= ns) return {0u, 0u, 0u};
+  const uint32_t j1 = min(ns, j0 + kFbChunk);
+  Tally t;
+  words64(pre[slot], flags[slot] & kDirect, suf + (size_t)u * ns, j0, j1, V, t, img);
+  return {j1 - j0, t.in_window, t.atomics};
+}
+
+// One FP32 item of a mixed render.  The per-word map runs in the prefix's
+// local frame, two words per packed f32x2 instruction.
+//
+// Pixel ids: for |uf| < 2^22, adding 1.5 * 2^23 rounded toward minus infinity
+// leaves floor(uf) in the low mantissa bits: bits(t) - 0x4B400000 = floor(uf),
+// so col = bits(t) - kx with kx = 0x4B400000 - axi.  Any |uf| >= 2^22,
+// infinity or NaN gives a t whose bits put col outside [0, W) (|axi| < 2^20
+// and W <= 2^16), so one unsigned compare per coordinate rejects
+// out-of-window and non-finite words alike.  A pair whose two words are both
+// inside the window and in the pixel of the current run costs one predicated
+// compare chain and one add.
+template <int BT>
+__device__ __forceinline__ void mixed_item(uint32_t item, const Work& Wk, const Plan& L,
+                                           const View& V, const Tables& T, Tally& t,
+                                           uint32_t& words, uint32_t* __restrict__ img) {
+  int x, u;
+  uint32_t pb, c;
+  item_of(item, Wk, x, u, pb, c);
+  const uint32_t r = pb * BT + threadIdx.x;
+  if (r >= L.np) return;
+  const uint32_t slot = (uint32_t)x * L.np + r;
+  if (T.flags[slot] & kFallback) return;
+  const Pre32 k = T.pre32[slot];
+  const f2 GR = pk(k.gr, k.gr), GI = pk(k.gi, k.gi);
+  const f2 C1 = pk(k.c1, k.c1), C2 = pk(k.c2, k.c2), C3 = pk(k.c3, k.c3), C4 = pk(k.c4, k.c4);
+  const f2 AX = pk(k.axf, k.axf), AY = pk(k.ayf, k.ayf);
+  const f2 magic = 0x4B4000004B400000ull;  // (1.5 * 2^23, 1.5 * 2^23)
+  const int W = (int)V.W;
+  const float4* src = T.suf32p + (size_t)u * L.npairs;
+  const uint32_t k0 = c * Wk.chunk, k1 = min(L.npairs, k0 + Wk.chunk);
+#pragma unroll 2
+  for (uint32_t e = k0; e < k1; ++e) {
+    const float4 s = __ldg(src + e);
+    const f2 wr = add2(pk(s.x, s.y), GR);
+    const f2 wi = add2(pk(s.z, s.w), GI);
+    const f2 m = fma2(wr, wr, mul2(wi, wi));
+    float ma, mb;
+    upk(m, ma, mb);
+    const f2 rr = pk(rcp32(ma), rcp32(mb));
+    const f2 tx = fma2(C1, wr, mul2(C2, wi));
+    const f2 ty = fma2(C3, wr, mul2(C4, wi));
+    float tua, tub, tva, tvb;
+    upk(add2_rm(fma2(tx, rr, AX), magic), tua, tub);
+    upk(add2_rm(fma2(ty, rr, AY), magic), tva, tvb);
+    const int ca = __float_as_int(tua) - k.kx, cb = __float_as_int(tub) - k.kx;
+    const int ra = __float_as_int(tva) - k.ky, rb = __float_as_int(tvb) - k.ky;
+    const int pa = ra * W + ca, pb2 = rb * W + cb;
+    const bool oka = ((uint32_t)ca < V.W) & ((uint32_t)ra < V.H);
+    const bool okb = ((uint32_t)cb < V.W) & ((uint32_t)rb < V.H);
+    if (oka & okb & (pa == t.cur) & (pb2 == t.cur)) {
+      t.run += 2;
+    } else {
+      t.add(oka ? pa : -1, img);
+      t.add(okb ? pb2 : -1, img);
+    }
+  }
+  words += min(2u * k1, L.ns) - 2u * k0;
+  t.flush(img);
+}
+
+// ---------------------------------------------------------------------------
+// host helpers
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+inline uint32_t pow3u(int e) {
+  uint32_t v = 1;
+  while (e-- > 0) v *= 3u;
+  return v;
+}
+
+inline bool valid_view(const kl_params* p) {
+  if (p->width < 1 || p->height < 1 || p->width > KL_MAX_IMAGE_SIDE ||
+      p->height > KL_MAX_IMAGE_SIDE)
+    return false;
+  if ((uint64_t)p->width * p->height > (1ull << 31) - 1) return false;
+  if (!(p->x0 < p->x1) || !(p->y0 < p->y1)) return false;
+  const double v[4] = {p->x0, p->x1, p->y0, p->y1};
+  for (double t : v)
+    if (!isfinite(t)) return false;
+  for (int k = 0; k < 32; ++k)
+    if (!isfinite(p->gens[k])) return false;
+  for (int k = 0; k < 8; ++k)
+    if (!isfinite(p->seeds[k])) return false;
+  if (p->block_threads != 0 && p->block_threads != 64 && p->block_threads != 128 &&
+      p->block_threads != 256)
+    return false;
+  return true;
+}
+
+// Prefix/suffix split.  Single renders: up to 9 prefix letters while the
+// words are few (enough threads), then suffixes of up to 8 letters (9 beyond
+// depth 20), the rest prefix.  Batched renders draw their parallelism from
+// many groups and use suffixes of up to 8 letters with at least 7 prefix
+// letters (729 prefix slots per letter fill whole thread blocks).
+inline int make_plan(const kl_params* p, Plan* L, bool batched) {
+  const int d = (int)p->depth;
+  if (d < 1 || d > kMaxRenderDepth) return KL_ERANGE;
+  int pl, sl;
+  if (d == 1) {
+    pl = 1;
+    sl = 0;
+  } else if (p->prefix_len) {
+    pl = (int)p->prefix_len;
+    sl = d - pl;
+    if (pl < 1 || sl < 1 || pl > kMaxPrefix || sl > kMaxSuffix) return KL_EINVAL;
+  } else if (batched) {
+    sl = d - 7;
+    if (sl > 8) sl = 8;
+    if (sl < 1) sl = 1;
+    pl = d - sl;
+    if (pl > kMaxPrefix) return KL_ERANGE;
+  } else if (d <= 10) {
+    pl = d - 1;
+    sl = 1;
+  } else {
+    sl = d - 9;
+    const int smax = d > 20 ? 9 : 8;
+    if (sl > smax) sl = smax;
+    pl = d - sl;
+    if (pl > kMaxPrefix) return KL_ERANGE;
+  }
+  L->d = d;
+  L->p = pl;
+  L->s = sl;
+  L->np = pow3u(pl - 1);
+  L->ns = sl > 0 ? pow3u(sl - 1) : 0;
+  L->npairs = (L->ns + 1) / 2;
+  L->q = (pl + 1) / 2;
+  L->so = sl / 2;
+  L->si = sl - L->so;
+  L->p3_q1 = pow3u(L->q - 1);
+  L->p3_pq = pow3u(pl - L->q);
+  L->p3_so1 = L->so > 0 ? pow3u(L->so - 1) : 1;
+  L->p3_si = pow3u(L->si);
+  L->p3_si1 = L->si > 0 ? pow3u(L->si - 1) : 1;
+  const size_t nP = 4ull * L->np, nS = 4ull * L->ns;
+  size_t off = 0;
+  L->off_pre64 = off; off = align256(off + nP * sizeof(Pre64));
+  L->off_pre32 = off; off = align256(off + nP * sizeof(Pre32));
+  L->off_flags = off; off = align256(off + nP * sizeof(uint32_t));
+  L->off_suf64 = off; off = align256(off + nS * sizeof(double2));
+  L->off_suf32 = off; off = align256(off + 4ull * L->npairs * sizeof(float4));
+  L->off_fb = off; off = align256(off + nP * sizeof(unsigned long long));
+  L->off_fbcount = off; off = align256(off + 2 * sizeof(uint32_t));  // fallback count, queue
+  L->off_L = off; off = align256(off + 4ull * L->p3_q1 * sizeof(PartM));
+  L->off_H = off; off = align256(off + 4ull * L->p3_pq * sizeof(M2));
+  L->off_So = off; off = align256(off + 4ull * L->p3_so1 * sizeof(PartM));
+  L->off_Si = off; off = align256(off + 4ull * L->p3_si1 * sizeof(double2));
+  L->total = off;
+  return KL_OK;
+}
+
+inline View make_view(const kl_params* p) {
+  View V;
+  V.x0 = p->x0;
+  V.y1 = p->y1;
+  V.sx = (double)p->width / (p->x1 - p->x0);
+  V.sy = (double)p->height / (p->y1 - p->y0);
+  V.W = p->width;
+  V.H = p->height;
+  const double w = (double)p->width, h = (double)p->height;
+  uint64_t bw, bh;
+  memcpy(&bw, &w, sizeof bw);
+  memcpy(&bh, &h, sizeof bh);
+  V.hiW = (uint32_t)(bw >> 32);
+  V.hiH = (uint32_t)(bh >> 32);
+  return V;
+}
+
+inline Group make_group(const kl_params* p) {
+  Group G;
+  for (int k = 0; k < 32; ++k) G.g[k] = p->gens[k];
+  for (int k = 0; k < 8; ++k) G.seed[k] = p->seeds[k];
+  return G;
+}
+
+inline Tables carve(const Plan& L, void* ws) {
+  char* b = (char*)ws;
+  return {(Pre64*)(b + L.off_pre64),          (Pre32*)(b + L.off_pre32),
+          (uint32_t*)(b + L.off_flags),        (double2*)(b + L.off_suf64),
+          (float4*)(b + L.off_suf32),          (unsigned long long*)(b + L.off_fb),
+          (uint32_t*)(b + L.off_fbcount),      (PartM*)(b + L.off_L),
+          (M2*)(b + L.off_H),                  (PartM*)(b + L.off_So),
+          (double2*)(b + L.off_Si)};
+}
+
+inline int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return n;
+}
+
+inline int check_launch() { return cudaGetLastError() == cudaSuccess ? KL_OK : KL_ECUDA; }
+
+// SM count and resident blocks per SM of a kernel with BT threads.
+inline int device_slots(const void* kernel, int bt, int* sms, int* occ) {
+  *sms = sm_count();
+  if (*sms <= 0) return KL_ECUDA;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kernel, bt, 0) != cudaSuccess ||
+      *occ < 1)
+    return KL_ECUDA;
+  return KL_OK;
+}
+
+// Items of about equal cost.  chunk_units = 0: at least `per_slot` (12) items
+// per resident block, so that the queue drains within a small fraction of one
+// item; else chunks of that many units (suffix points or point pairs).
+inline Work make_work(const Plan& L, int bt, uint32_t units, int slots, uint32_t chunk_units) {
+  Work W;
+  W.n_pb = (L.np + bt - 1) / bt;
+  const uint64_t base = 12ull * W.n_pb;
+  if (chunk_units == 0) {
+    const uint64_t target = 12ull * (uint64_t)slots;
+    uint64_t n_chunks = (target + base - 1) / base;
+    if (n_chunks < 1) n_chunks = 1;
+    if (n_chunks > units) n_chunks = units;
+    W.chunk = (uint32_t)((units + n_chunks - 1) / n_chunks);
+  } else {
+    W.chunk = chunk_units < units ? chunk_units : units;
+  }
+  if (W.chunk < 1) W.chunk = 1;
+  W.n_chunks = (units + W.chunk - 1) / W.chunk;
+  W.n_items = (uint32_t)(base * W.n_chunks);
+  return W;
+}
+
+}  // namespace
