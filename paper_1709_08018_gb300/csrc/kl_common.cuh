@@ -818,9 +818,10 @@ inline int device_slots(const void* kernel, int bt, int* sms, int* occ) {
   return KL_OK;
 }
 
-// Items of about equal cost.  chunk_units = 0: at least `per_slot` (12) items
-// per resident block, so that the queue drains within a small fraction of one
-// item; else chunks of that many units (suffix points or point pairs).
+// Items of about equal cost.  chunk_units = 0: about 12 items per resident
+// block, so that the queue drains within a small fraction of one item, but no
+// chunk below 16 units; else chunks of that many units (suffix points or
+// point pairs).
 inline Work make_work(const Plan& L, int bt, uint32_t units, int slots, uint32_t chunk_units) {
   Work W;
   W.n_pb = (L.np + bt - 1) / bt;
@@ -828,8 +829,9 @@ inline Work make_work(const Plan& L, int bt, uint32_t units, int slots, uint32_t
   if (chunk_units == 0) {
     const uint64_t target = 12ull * (uint64_t)slots;
     uint64_t n_chunks = (target + base - 1) / base;
+    const uint64_t most = units / 16 > 0 ? units / 16 : 1;
+    if (n_chunks > most) n_chunks = most;
     if (n_chunks < 1) n_chunks = 1;
-    if (n_chunks > units) n_chunks = units;
     W.chunk = (uint32_t)((units + n_chunks - 1) / n_chunks);
   } else {
     W.chunk = chunk_units < units ? chunk_units : units;

@@ -88,3 +88,14 @@ def test_workspace_validation(kl):
         p = kl.params_init(2 + 0j, 2 + 0j, 18, 4096, 4096, (-1.5, 1.5, -1.5, 1.5))
         setattr(p, field, bad)
         assert kl.workspace_bytes(p) == 0, field
+
+
+def test_autotuner_default_split_matches_library(kl):
+    """The tuner's idea of the library's default prefix length gives the same
+    workspace as letting the library choose (prefix_len = 0)."""
+    from paper_1709_08018_gb300 import autotune
+    for d in range(2, 24):
+        p = kl.params_init(2 + 0j, 2 + 0j, d, 512, 512, (-1.5, 1.5, -1.5, 1.5))
+        auto = kl.workspace_bytes(p)
+        p.prefix_len = autotune.default_prefix_len(d, False)
+        assert kl.workspace_bytes(p) == auto, d

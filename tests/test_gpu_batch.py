@@ -56,7 +56,9 @@ def test_batch_equals_single_renders(kl, precision, bt):
         img, cnt = kl.render(p)
         assert np.array_equal(imgs[k], img.cpu().numpy().view(np.uint32)), k
         c = cnt.cpu().numpy()
-        assert np.array_equal(cnts[k], c), (k, cnts[k], c)
+        # in-window, dropped and FP64 words; the atomics counter depends on
+        # how the work is cut into items
+        assert np.array_equal(cnts[k][:3], c[:3]), (k, cnts[k], c)
         assert int(c[0]) + int(c[1]) == kl.word_count(depths[k])
 
 
