@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-lod", action="store_true")
     return ap.parse_args()
 
 
@@ -268,6 +269,37 @@ def batch_sweep(kl, dev, steps: int):
     return out
 
 
+def lod_config(kl, n_train: int = 64, n_test: int = 16):
+    """Learned level-of-detail pruning: the network trained by the library's
+    kernels on exact depth-22 renders of n_train groups (seed 1710), judged on
+    n_test held-out groups (seed 1711) at 8192^2 against the exact render."""
+    import torch
+    from paper_1709_08018_gb300 import lod
+    d, size, lo, hi, extent, under, margin = 22, 8192, 8, 15, 1.0 / 32, 32.0, 0.0
+    W = (-2.0, 2.0, -2.0, 2.0)
+    mk = lambda g: kl.params_init(g.ta, g.tb, d, size, size, W, kl.MIXED)
+    tr = [mk(g) for g, _ in klsynth.draw_groups(klsynth.LOD_TRAIN_SEED, n_train)]
+    te = [mk(g) for g, _ in klsynth.draw_groups(klsynth.LOD_HELDOUT_SEED, n_test)]
+    t0 = time.time()
+    x, t = lod.make_dataset(tr, lo, hi, per_level=60_000, seed=3, extent=extent)
+    t1 = time.time()
+    mlp, losses = lod.train(x, t, steps=10000, batch=16384, lr=2e-3, seed=5, under=under)
+    torch.cuda.synchronize()
+    t2 = time.time()
+    evals = [lod.evaluate(p, mlp, lo, hi, margin, repeats=3) for p in te]
+    s = lod.summarize(evals)
+    s.update({"workload": f"{n_test} held-out groups (seed 1711), depth 22 "
+                          f"({kl.word_count(d)} words each), 8192^2 over [-2,2]^2; network "
+                          f"trained on {n_train} groups (seed 1710)",
+              "levels": [lo, hi], "label_extent_px": extent, "under_weight": under,
+              "margin": margin, "train_samples": int(x.shape[0]), "train_steps": 10000,
+              "loss_first_last": [losses[0], losses[-1]], "label_seconds": t1 - t0,
+              "train_seconds": t2 - t1,
+              "words_per_s_pruned": n_test * kl.word_count(d) / (s["pruned_ms"] / 1000.0),
+              "words_per_s_exact": n_test * kl.word_count(d) / (s["exact_ms"] / 1000.0)})
+    return s
+
+
 def run_ours(args):
     import torch
     import paper_1709_08018_gb300 as kl
@@ -409,6 +441,10 @@ def run_ours(args):
             "speedup_mixed_over_fp64": fp64_step_ms / (total_ms / K)}
     if not args.no_batch:
         line["batch_sweep"] = batch_sweep(kl, dev, K)
+    if not args.no_lod:
+        line["lod"] = lod_config(kl)
+        line["lod"]["speedup_over_plain_fp64"] = (
+            line["lod"]["words_per_s_pruned"] / plain["words_per_s"])
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg)
     if rank == 0:

@@ -213,6 +213,101 @@ KL_API int kl_batch_replay(kl_batch* b, void* stream);
 /* Free the handle and its graph (after the work using it has finished). */
 KL_API void kl_batch_destroy(kl_batch* b);
 
+/* ---------------------------------------------------------------------------
+ * Level-of-detail network.  The paper's closing remark is that both rendering
+ * approaches need tricks to be accelerated (Sec. "Conclusions"); this library's
+ * trick is a small MLP that reads a prefix's normalised matrix and predicts how
+ * many more letters its subtree needs before its image falls into a single
+ * pixel, so that the enumeration can stop early (kl_render_lod).
+ *
+ * Model: 8 -> 64 -> 64 -> 1, ReLU after both hidden layers, BF16 weights and
+ * activations on the tensor cores with FP32 accumulation.  Parameters: one
+ * FP32 vector of KL_MLP_NPARAMS floats,
+ *   W1 [8][64] | b1 [64] | W2 [64][64] | b2 [64] | w3 [64] | b3
+ * with h_out = sum_in x_in W[in][out] + b_out.  Inputs x: [n][8] FP32 rows.
+ */
+#define KL_MLP_NPARAMS 4801
+
+/* y[i] = MLP(x[i]) for n rows (device pointers). */
+KL_API int kl_mlp_forward(const float* d_params, const float* d_x, uint64_t n, float* d_y,
+                          void* stream);
+
+/* Scratch bytes kl_mlp_grad needs for n rows. */
+KL_API size_t kl_mlp_scratch_bytes(uint64_t n);
+
+/* Loss and gradient of the weighted mean squared error over n rows with
+ * targets t: *d_loss = mean w_i (y_i - t_i)^2 with w_i = under_weight where
+ * y_i < t_i and 1 elsewhere (under_weight > 1 penalises predicting too few
+ * levels, the direction that prunes too early); d_grad = its gradient
+ * (KL_MLP_NPARAMS floats, same layout as the parameters).  Both are
+ * overwritten. */
+KL_API int kl_mlp_grad(const float* d_params, const float* d_x, const float* d_t, uint64_t n,
+                       float under_weight, float* d_grad, float* d_loss, void* d_scratch,
+                       size_t scratch_bytes, void* stream);
+
+/* One Adam step (Kingma and Ba, 2015) with bias correction for `step` >= 1,
+ * then d_grad is zeroed.  d_m, d_v: first and second moments (start at 0). */
+KL_API int kl_mlp_adam(float* d_params, float* d_m, float* d_v, float* d_grad, uint32_t step,
+                       float lr, float beta1, float beta2, float eps, void* stream);
+
+/* Level-of-detail labels and pruned render.
+ *
+ * Tree levels: a node at level k is a reduced prefix w_1 .. w_k (the letters
+ * applied last), numbered by its prefix slot: x = w_k, then the base-3 ranks
+ * of w_{k-1} .. w_1 (each among the letters other than the inverse of its
+ * right neighbour), most significant first: slot = x 3^(k-1) + r.  Its
+ * subtree is its 3^(d-k) words of length d (Sec. "Basic setup": the tree of
+ * words; the pruned tree of Sec. "Once-punctured torus groups").
+ * A node is resolved when the image of its subtree falls under one pixel
+ * (its words' bounding box narrower and lower than `extent` pixels, 1 by
+ * default), or no word falls inside the window.  Its label is 0 if resolved, else
+ * 1 + the largest label of its three children; at the deepest level hi an
+ * unresolved node has label 1.  Node arrays list levels lo..hi in order, each
+ * level in slot order (kl_lod_node_count(lo, hi) nodes).
+ * Requirements: 1 <= lo <= hi < depth, hi <= 15, depth - hi <= 9. */
+KL_API uint64_t kl_lod_node_count(uint32_t lo, uint32_t hi);
+
+/* Workspace bytes of kl_lod_labels (0 on invalid arguments). */
+KL_API size_t kl_lod_label_bytes(const kl_params* p, uint32_t lo, uint32_t hi);
+
+/* Exact render of *p (into d_image, d_counters as kl_render, prefix length
+ * hi) and, from the same pass, the labels (uint8) and the network input
+ * features (8 FP32 per node) of every node of levels lo..hi.  Features: the
+ * prefix matrix divided by the principal square root of its determinant,
+ * negated if needed so that Re tr > 0, then sign(v) log(1 + |v|) of the real
+ * and imaginary parts of p, q, r, s. */
+KL_API int kl_lod_labels(const kl_params* p, uint32_t lo, uint32_t hi, float extent,
+                         uint32_t* d_image, uint64_t* d_counters, float* d_features,
+                         uint8_t* d_labels, void* d_workspace, size_t workspace_bytes,
+                         void* stream);
+
+/* Workspace bytes of kl_render_lod (0 on invalid arguments). */
+KL_API size_t kl_lod_render_bytes(const kl_params* p, uint32_t lo, uint32_t hi);
+
+/* Render with the network pruning the enumeration (p->precision must be
+ * KL_MIXED).  From level lo to hi each active node is scored by the network
+ * (d_mlp: KL_MLP_NPARAMS floats).  A node with score + margin < 1/2 whose
+ * first, middle and last words in index order (the words taking the allowed
+ * letter of rank 0, 1, 2 at every step) fall into one pixel adds all 3^(d-k)
+ * words of its subtree to that pixel (all three outside the window: counts
+ * them dropped); the others expand; nodes still active at level hi are
+ * rendered exactly.  Every word is counted once (in d_counters, as
+ * kl_render).  d_stats (4 uint64): nodes scored, nodes pruned, level-hi nodes
+ * rendered exactly, 0.  Exact wherever the network's calls are right. */
+KL_API int kl_render_lod(const kl_params* p, uint32_t lo, uint32_t hi, const float* d_mlp,
+                         float margin, uint32_t* d_image, uint64_t* d_counters,
+                         uint64_t* d_stats, void* d_workspace, size_t workspace_bytes,
+                         void* stream);
+
+/* As kl_render_lod, with the true labels of kl_lod_labels (same p, lo, hi)
+ * taking the network's place: a node is pruned exactly when its label is 0.
+ * It measures what the pruned render loses by its splat alone, separately
+ * from the network's errors. */
+KL_API int kl_render_lod_labels(const kl_params* p, uint32_t lo, uint32_t hi,
+                                const uint8_t* d_labels, uint32_t* d_image, uint64_t* d_counters,
+                                uint64_t* d_stats, void* d_workspace, size_t workspace_bytes,
+                                void* stream);
+
 /* Size of the library's own device scratch array used by kl_render_noalloc. */
 #define KL_STATIC_SCRATCH_BYTES (32u << 20)
 

@@ -8,8 +8,9 @@ and fails loudly if it has not been built (``__graft_entry__.build()`` or
 ``python -m paper_1709_08018_gb300.build``).
 """
 from .binding import (  # noqa: F401
-    KL_CNT_ATOMICS, KL_CNT_DROPPED, KL_CNT_FP64_WORDS, KL_CNT_IN_WINDOW, KL_N_COUNTERS,
-    Batch, FP64, MIXED, KlError, Params, Renderer, decode_words, eval_words, exported_symbols,
-    grandma, lib, params_init, render, render_noalloc, seeds, set_profile_events, status_string, word_count,
-    workspace_bytes,
+    FP64, KL_CNT_ATOMICS, KL_CNT_DROPPED, KL_CNT_FP64_WORDS, KL_CNT_IN_WINDOW, KL_MLP_NPARAMS,
+    KL_N_COUNTERS, KL_STATIC_SCRATCH_BYTES, MIXED, Batch, KlError, LodRenderer, MlpTrainer, Params,
+    Renderer, lod_labels, lod_node_count,
+    decode_words, eval_words, exported_symbols, grandma, lib, mlp_forward, params_init, render,
+    render_noalloc, seeds, set_profile_events, status_string, word_count, workspace_bytes,
 )

@@ -15,7 +15,11 @@ KL_CNT_IN_WINDOW, KL_CNT_DROPPED, KL_CNT_FP64_WORDS, KL_CNT_ATOMICS, KL_N_COUNTE
 API = ("kl_status_string", "kl_word_count", "kl_grandma", "kl_seeds", "kl_params_init",
        "kl_decode_words", "kl_workspace_bytes", "kl_eval_words", "kl_render",
        "kl_batch_create", "kl_batch_workspace_bytes", "kl_batch_render", "kl_batch_capture",
-       "kl_batch_replay", "kl_batch_destroy", "kl_render_noalloc", "kl_set_profile_events")
+       "kl_batch_replay", "kl_batch_destroy", "kl_mlp_forward", "kl_mlp_scratch_bytes",
+       "kl_mlp_grad", "kl_mlp_adam", "kl_lod_node_count", "kl_lod_label_bytes", "kl_lod_labels",
+       "kl_lod_render_bytes", "kl_render_lod", "kl_render_lod_labels", "kl_render_noalloc",
+       "kl_set_profile_events")
+KL_MLP_NPARAMS = 4801
 KL_STATIC_SCRATCH_BYTES = 32 << 20
 
 
@@ -90,6 +94,29 @@ def lib():
         L.kl_batch_replay.restype = I
         L.kl_batch_destroy.argtypes = [P]
         L.kl_batch_destroy.restype = None
+        L.kl_mlp_forward.argtypes = [P, P, U64, P, P]
+        L.kl_mlp_forward.restype = I
+        L.kl_mlp_scratch_bytes.argtypes = [U64]
+        L.kl_mlp_scratch_bytes.restype = SZ
+        L.kl_mlp_grad.argtypes = [P, P, P, U64, ctypes.c_float, P, P, P, SZ, P]
+        L.kl_mlp_grad.restype = I
+        L.kl_mlp_adam.argtypes = [P, P, P, P, U32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                  ctypes.c_float, P]
+        L.kl_mlp_adam.restype = I
+        L.kl_lod_node_count.argtypes = [U32, U32]
+        L.kl_lod_node_count.restype = U64
+        L.kl_lod_label_bytes.argtypes = [ctypes.POINTER(Params), U32, U32]
+        L.kl_lod_label_bytes.restype = SZ
+        L.kl_lod_labels.argtypes = [ctypes.POINTER(Params), U32, U32, ctypes.c_float, P, P, P, P,
+                                    P, SZ, P]
+        L.kl_lod_labels.restype = I
+        L.kl_lod_render_bytes.argtypes = [ctypes.POINTER(Params), U32, U32]
+        L.kl_lod_render_bytes.restype = SZ
+        L.kl_render_lod.argtypes = [ctypes.POINTER(Params), U32, U32, P, ctypes.c_float, P, P, P,
+                                    P, SZ, P]
+        L.kl_render_lod.restype = I
+        L.kl_render_lod_labels.argtypes = [ctypes.POINTER(Params), U32, U32, P, P, P, P, P, SZ, P]
+        L.kl_render_lod_labels.restype = I
         L.kl_render_noalloc.argtypes = [ctypes.POINTER(Params), P, P, P]
         L.kl_render_noalloc.restype = I
         L.kl_set_profile_events.argtypes = [P, P]
@@ -279,6 +306,111 @@ class Batch:
                 pass
             _lib.kl_batch_destroy(h)
             self.handle = None
+
+
+def mlp_forward(params, x, stream=None):
+    """y = MLP(x): params (KL_MLP_NPARAMS,) float32, x (n, 8) float32, CUDA."""
+    torch = _torch()
+    n = x.shape[0]
+    y = torch.empty(n, dtype=torch.float32, device=x.device)
+    _check(lib().kl_mlp_forward(params.data_ptr(), x.data_ptr(), n, y.data_ptr(),
+                                _stream_handle(stream)), "kl_mlp_forward")
+    return y
+
+
+class MlpTrainer:
+    """Adam training of the MLP with the library's kernels (kl_mlp_grad +
+    kl_mlp_adam); params is updated in place."""
+
+    def __init__(self, params, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, under_weight=1.0):
+        torch = _torch()
+        self.params = params
+        self.under_weight = under_weight
+        self.m = torch.zeros_like(params)
+        self.v = torch.zeros_like(params)
+        self.grad = torch.zeros_like(params)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=params.device)
+        self.lr, self.b1, self.b2, self.eps = lr, beta1, beta2, eps
+        self.step_no = 0
+        self.scratch = None
+
+    def gradient(self, x, t, stream=None):
+        torch = _torch()
+        n = x.shape[0]
+        need = int(lib().kl_mlp_scratch_bytes(n))
+        if self.scratch is None or self.scratch.numel() < need:
+            self.scratch = torch.empty(need, dtype=torch.uint8, device=x.device)
+        _check(lib().kl_mlp_grad(self.params.data_ptr(), x.data_ptr(), t.data_ptr(), n,
+                                 self.under_weight, self.grad.data_ptr(), self.loss.data_ptr(),
+                                 self.scratch.data_ptr(), self.scratch.numel(),
+                                 _stream_handle(stream)), "kl_mlp_grad")
+        return self.grad, self.loss
+
+    def step(self, x, t, stream=None):
+        self.gradient(x, t, stream)
+        self.step_no += 1
+        _check(lib().kl_mlp_adam(self.params.data_ptr(), self.m.data_ptr(), self.v.data_ptr(),
+                                 self.grad.data_ptr(), self.step_no, self.lr, self.b1, self.b2,
+                                 self.eps, _stream_handle(stream)), "kl_mlp_adam")
+        return self.loss
+
+
+def lod_node_count(lo: int, hi: int) -> int:
+    return int(lib().kl_lod_node_count(lo, hi))
+
+
+def lod_labels(p: Params, lo: int, hi: int, extent: float = 1.0, workspace=None, stream=None,
+               device="cuda"):
+    """Exact render plus per-node labels (uint8) and features (n, 8) of levels
+    lo..hi (kl_lod_labels).  Returns (image, counters, features, labels)."""
+    torch = _torch()
+    n = lod_node_count(lo, hi)
+    need = int(lib().kl_lod_label_bytes(ctypes.byref(p), lo, hi))
+    if n == 0 or need == 0:
+        raise KlError(2, "kl_lod_label_bytes")
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=device)
+    image = torch.empty((p.height, p.width), dtype=torch.int32, device=device)
+    counters = torch.zeros(KL_N_COUNTERS, dtype=torch.int64, device=device)
+    feats = torch.empty((n, 8), dtype=torch.float32, device=device)
+    labels = torch.empty(n, dtype=torch.uint8, device=device)
+    _check(lib().kl_lod_labels(ctypes.byref(p), lo, hi, extent, image.data_ptr(),
+                               counters.data_ptr(),
+                               feats.data_ptr(), labels.data_ptr(), workspace.data_ptr(),
+                               workspace.numel(), _stream_handle(stream)), "kl_lod_labels")
+    return image, counters, feats, labels
+
+
+class LodRenderer:
+    """Holds the workspace and outputs of kl_render_lod for repeated renders."""
+
+    def __init__(self, p: Params, lo: int, hi: int, device="cuda"):
+        torch = _torch()
+        self.p, self.lo, self.hi = p, lo, hi
+        need = int(lib().kl_lod_render_bytes(ctypes.byref(p), lo, hi))
+        if need == 0:
+            raise KlError(2, "kl_lod_render_bytes")
+        self.workspace = torch.empty(need, dtype=torch.uint8, device=device)
+        self.image = torch.empty((p.height, p.width), dtype=torch.int32, device=device)
+        self.counters = torch.zeros(KL_N_COUNTERS, dtype=torch.int64, device=device)
+        self.stats = torch.zeros(4, dtype=torch.int64, device=device)
+
+    def __call__(self, mlp_params, margin: float = 0.0, stream=None):
+        _check(lib().kl_render_lod(ctypes.byref(self.p), self.lo, self.hi, mlp_params.data_ptr(),
+                                   margin, self.image.data_ptr(), self.counters.data_ptr(),
+                                   self.stats.data_ptr(), self.workspace.data_ptr(),
+                                   self.workspace.numel(), _stream_handle(stream)),
+               "kl_render_lod")
+        return self.image, self.counters, self.stats
+
+    def with_labels(self, labels, stream=None):
+        """The same render pruned by the true labels (kl_render_lod_labels)."""
+        _check(lib().kl_render_lod_labels(ctypes.byref(self.p), self.lo, self.hi,
+                                          labels.data_ptr(), self.image.data_ptr(),
+                                          self.counters.data_ptr(), self.stats.data_ptr(),
+                                          self.workspace.data_ptr(), self.workspace.numel(),
+                                          _stream_handle(stream)), "kl_render_lod_labels")
+        return self.image, self.counters, self.stats
 
 
 def set_profile_events(start=None, stop=None):

@@ -119,6 +119,16 @@ struct Work {
   uint32_t n_items;   // 12 * n_pb * n_chunks
 };
 
+// Per-prefix boxes of all words of a prefix's subtree (level-of-detail
+// labels), in fixed point: pixel coordinates times 256, floored, saturated to
+// +-2^30 for far words.
+struct BoxRef {
+  int* cmin;
+  int* cmax;
+  int* rmin;
+  int* rmax;
+};
+
 // ---------------------------------------------------------------------------
 // complex FP64 helpers (tables only; the per-word code spells out its ops)
 
@@ -554,16 +564,49 @@ __device__ __forceinline__ void item_of(uint32_t item, const Work& W, int& x, in
   u = allowed_letter(q % 3, (x + 2) & 3);
 }
 
+// Fixed-point box coordinate (1/256 pixel) of an FP64 pixel coordinate:
+// floor(256 u), saturated to +-2^30; NaN is reported through `ok`.
+__device__ __forceinline__ int box_coord64(double u, bool& ok) {
+  ok = ok && (u == u);
+  const double c = fmin(fmax(floor(256.0 * u), -1073741824.0), 1073741824.0);
+  return (int)c;
+}
+
+// The same for a local-frame FP32 coordinate: 256 axi + floor(256 uf).
+__device__ __forceinline__ int box_coord32(int axi, float uf) {
+  const int A = 1073741824;
+  if (!(fabsf(uf) < 2097152.0f)) return uf > 0.0f ? A : -A;  // |uf| >= 2^21
+  return 256 * axi + (int)floorf(256.0f * uf);
+}
+
+__device__ __forceinline__ void box_merge(const BoxRef& B, uint32_t slot, int c0, int c1, int r0,
+                                          int r1) {
+  if (c0 > c1) return;  // no finite word
+  atomicMin(B.cmin + slot, c0);
+  atomicMax(B.cmax + slot, c1);
+  atomicMin(B.rmin + slot, r0);
+  atomicMax(B.rmax + slot, r1);
+}
+
 // FP64 words of one prefix slot on suffix points [j0, j1) of one first letter.
+// BBOX: also merge the words' pixel box into the slot's box.
+template <bool BBOX = false>
 __device__ __forceinline__ void words64(const Pre64& k, bool direct, const double2* src,
                                         uint32_t j0, uint32_t j1, const View& V, Tally& t,
-                                        uint32_t* __restrict__ img) {
+                                        uint32_t* __restrict__ img, const BoxRef* B = nullptr,
+                                        uint32_t slot = 0) {
+  int c0 = 0x7FFFFFFF, c1 = -0x7FFFFFFF, r0 = 0x7FFFFFFF, r1 = -0x7FFFFFFF;
   if (direct) {
     for (uint32_t j = j0; j < j1; ++j) {
       double uu, vv;
       const double2 s = __ldg(src + j);
       uv_direct64(k, s.x, s.y, V, uu, vv);
       t.add(pixel64(uu, vv, V), img);
+      if (BBOX) {
+        bool ok = true;
+        const int cc = box_coord64(uu, ok), rr = box_coord64(vv, ok);
+        if (ok) { c0 = min(c0, cc); c1 = max(c1, cc); r0 = min(r0, rr); r1 = max(r1, rr); }
+      }
     }
   } else {
 #pragma unroll 2
@@ -572,9 +615,15 @@ __device__ __forceinline__ void words64(const Pre64& k, bool direct, const doubl
       const double2 s = __ldg(src + j);
       uv_pole64(k, s.x, s.y, uu, vv);
       t.add(pixel64(uu, vv, V), img);
+      if (BBOX) {
+        bool ok = true;
+        const int cc = box_coord64(uu, ok), rr = box_coord64(vv, ok);
+        if (ok) { c0 = min(c0, cc); c1 = max(c1, cc); r0 = min(r0, rr); r1 = max(r1, rr); }
+      }
     }
   }
   t.flush(img);
+  if (BBOX) box_merge(*B, slot, c0, c1, r0, r1);
 }
 
 // One FP64 item of a plain render: words of this thread's prefix on one chunk.
@@ -597,18 +646,21 @@ __device__ __forceinline__ void fp64_item(uint32_t item, const Work& Wk, const P
 // Mixed-mode FP64 fallback unit (kept out of line so that its registers do
 // not bind the FP32 loop): (fallback prefix, one of its three suffix letters,
 // a chunk of kFbChunk suffix points).  Chunks past the end are empty.
+template <bool BBOX = false>
 __device__ __noinline__ UnitTally fallback_unit(const Pre64* __restrict__ pre,
                                                 const uint32_t* __restrict__ flags,
                                                 const double2* __restrict__ suf, uint32_t slot,
                                                 uint32_t k, uint32_t c, uint32_t np, uint32_t ns,
-                                                View V, uint32_t* __restrict__ img) {
+                                                View V, uint32_t* __restrict__ img,
+                                                BoxRef B = BoxRef{}) {
   const int x = (int)(slot / np);
   const int u = allowed_letter((int)k, (x + 2) & 3);
   const uint32_t j0 = c * kFbChunk;
   if (j0 >= ns) return {0u, 0u, 0u};
   const uint32_t j1 = min(ns, j0 + kFbChunk);
   Tally t;
-  words64(pre[slot], flags[slot] & kDirect, suf + (size_t)u * ns, j0, j1, V, t, img);
+  words64<BBOX>(pre[slot], flags[slot] & kDirect, suf + (size_t)u * ns, j0, j1, V, t, img, &B,
+                slot);
   return {j1 - j0, t.in_window, t.atomics};
 }
 
@@ -623,17 +675,14 @@ __device__ __noinline__ UnitTally fallback_unit(const Pre64* __restrict__ pre,
 // out-of-window and non-finite words alike.  A pair whose two words are both
 // inside the window and in the pixel of the current run costs one predicated
 // compare chain and one add.
-template <int BT>
-__device__ __forceinline__ void mixed_item(uint32_t item, const Work& Wk, const Plan& L,
-                                           const View& V, const Tables& T, Tally& t,
-                                           uint32_t& words, uint32_t* __restrict__ img) {
-  int x, u;
-  uint32_t pb, c;
-  item_of(item, Wk, x, u, pb, c);
-  const uint32_t r = pb * BT + threadIdx.x;
-  if (r >= L.np) return;
-  const uint32_t slot = (uint32_t)x * L.np + r;
-  if (T.flags[slot] & kFallback) return;
+// Mixed words of prefix slot `slot` on suffix point pairs [k0, k1) of first
+// letter u (see the comment above for the pixel arithmetic).
+template <bool BBOX = false>
+__device__ __forceinline__ void mixed_slot_words(uint32_t slot, int u, uint32_t k0, uint32_t k1,
+                                                 const Plan& L, const View& V, const Tables& T,
+                                                 Tally& t, uint32_t& words,
+                                                 uint32_t* __restrict__ img,
+                                                 const BoxRef* B = nullptr) {
   const Pre32 k = T.pre32[slot];
   const f2 GR = pk(k.gr, k.gr), GI = pk(k.gi, k.gi);
   const f2 C1 = pk(k.c1, k.c1), C2 = pk(k.c2, k.c2), C3 = pk(k.c3, k.c3), C4 = pk(k.c4, k.c4);
@@ -641,7 +690,7 @@ __device__ __forceinline__ void mixed_item(uint32_t item, const Work& Wk, const 
   const f2 magic = 0x4B4000004B400000ull;  // (1.5 * 2^23, 1.5 * 2^23)
   const int W = (int)V.W;
   const float4* src = T.suf32p + (size_t)u * L.npairs;
-  const uint32_t k0 = c * Wk.chunk, k1 = min(L.npairs, k0 + Wk.chunk);
+  int bc0 = 0x7FFFFFFF, bc1 = -0x7FFFFFFF, br0 = 0x7FFFFFFF, br1 = -0x7FFFFFFF;
 #pragma unroll 2
   for (uint32_t e = k0; e < k1; ++e) {
     const float4 s = __ldg(src + e);
@@ -667,9 +716,40 @@ __device__ __forceinline__ void mixed_item(uint32_t item, const Work& Wk, const 
       t.add(oka ? pa : -1, img);
       t.add(okb ? pb2 : -1, img);
     }
+    if (BBOX) {
+      float ua, ub, va, vb;
+      upk(fma2(tx, rr, AX), ua, ub);
+      upk(fma2(ty, rr, AY), va, vb);
+      if (ua == ua && va == va) {
+        const int cc = box_coord32(k.axi, ua), rr2 = box_coord32(k.ayi, va);
+        bc0 = min(bc0, cc); bc1 = max(bc1, cc); br0 = min(br0, rr2); br1 = max(br1, rr2);
+      }
+      if (ub == ub && vb == vb) {
+        const int cc = box_coord32(k.axi, ub), rr2 = box_coord32(k.ayi, vb);
+        bc0 = min(bc0, cc); bc1 = max(bc1, cc); br0 = min(br0, rr2); br1 = max(br1, rr2);
+      }
+    }
   }
   words += min(2u * k1, L.ns) - 2u * k0;
   t.flush(img);
+  if (BBOX) box_merge(*B, slot, bc0, bc1, br0, br1);
+}
+
+// One FP32 item of a mixed render: this thread's prefix on one chunk.
+template <int BT, bool BBOX = false>
+__device__ __forceinline__ void mixed_item(uint32_t item, const Work& Wk, const Plan& L,
+                                           const View& V, const Tables& T, Tally& t,
+                                           uint32_t& words, uint32_t* __restrict__ img,
+                                           const BoxRef* B = nullptr) {
+  int x, u;
+  uint32_t pb, c;
+  item_of(item, Wk, x, u, pb, c);
+  const uint32_t r = pb * BT + threadIdx.x;
+  if (r >= L.np) return;
+  const uint32_t slot = (uint32_t)x * L.np + r;
+  if (T.flags[slot] & kFallback) return;
+  const uint32_t k0 = c * Wk.chunk, k1 = min(L.npairs, k0 + Wk.chunk);
+  mixed_slot_words<BBOX>(slot, u, k0, k1, L, V, T, t, words, img, B);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,156 @@
+"""Level-of-detail labels and the network-pruned render.
+
+  - with pruning switched off (margin +inf) the pruned render is the exact
+    render of the level-hi prefixes: the same image, bit for bit;
+  - with everything pruned at level lo, every word is still counted once;
+  - the labels obey their recursion, and level-hi labels agree with the
+    oracle's own test "the subtree's image is under `extent` pixels, or
+    misses the window";
+  - a network trained on a few groups renders held-out groups faster than
+    the exact render (the method without it, which evaluates every word) at
+    occupancy IoU >= 0.998, and pruning by the true labels keeps IoU >= 0.998
+    at the same extent.
+"""
+import numpy as np
+import pytest
+
+import klsynth
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kl():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("no CUDA device for a gpu-marked test")
+    from paper_1709_08018_gb300 import build
+    build.build()
+    import paper_1709_08018_gb300 as kl
+    return kl
+
+
+def group_params(kl, g, d, size, window=(-2.0, 2.0, -2.0, 2.0), **fields):
+    return kl.params_init(g.ta, g.tb, d, size, size, window, kl.MIXED, **fields)
+
+
+def test_unpruned_equals_exact_and_full_pruning_conserves(kl):
+    import torch
+    from paper_1709_08018_gb300 import lod
+    mlp = lod.init_params(1)
+    for g, d in [(klsynth.NEAR_CUSP, 14), (klsynth.draw_groups(1710, 1)[0][0], 13)]:
+        lo, hi = 4, 9
+        p = group_params(kl, g, d, 1024, prefix_len=hi)
+        img, cnt = kl.render(p)
+        ref = img.cpu().numpy().copy()
+        ref_c = cnt.cpu().numpy().copy()
+        r = kl.LodRenderer(p, lo, hi)
+        out, c, st = r(mlp, margin=1e30)       # never prune
+        assert np.array_equal(out.cpu().numpy(), ref)
+        assert np.array_equal(c.cpu().numpy()[:3], ref_c[:3])
+        st = st.cpu().numpy()
+        assert st[1] == 0 and st[2] == 4 * 3 ** (hi - 1)
+        out, c, st = r(mlp, margin=-1e30)      # every score says "prune"
+        c = c.cpu().numpy()
+        assert int(c[0]) + int(c[1]) == kl.word_count(d)
+        assert int(out.cpu().numpy().view(np.uint32).astype(np.int64).sum()) == int(c[0])
+        # nodes whose three representative words share a pixel are pruned at once
+        st = st.cpu().numpy()
+        assert st[1] > 0 and st[0] >= 4 * 3 ** (lo - 1)
+        torch.cuda.synchronize()
+
+
+def subtree_pixels(g, s, d, k, slot, window, size):
+    """Oracle pixel coordinates of all words of node `slot` at level k."""
+    nk = 3 ** (k - 1)
+    x, r = slot // nk, slot % nk
+    digits = []
+    for _ in range(k - 1):
+        digits.append(r % 3)
+        r //= 3
+    digits = digits[::-1]             # most significant first: w_{k-1} .. w_1
+    letters = [x]
+    for dg in digits:
+        ban = (letters[-1] + 2) % 4
+        letters.append([y for y in range(4) if y != ban][dg])
+    prefix = letters[::-1]            # w_1 .. w_k
+    # word index: mixed radix of the prefix, then all suffix digits
+    idx = prefix[0]
+    for j in range(1, k):
+        ban = (prefix[j - 1] + 2) % 4
+        idx = idx * 3 + [y for y in range(4) if y != ban].index(prefix[j])
+    m = d - k
+    base = idx * 3 ** m
+    ids = np.arange(base, base + 3 ** m, dtype=np.uint64)
+    z = oracle.evaluate(g, s, d, ids)
+    x0, x1, y0, y1 = window
+    u = (z.real - x0) * size / (x1 - x0)
+    v = (y1 - z.imag) * size / (y1 - y0)
+    return u, v
+
+
+def test_labels_recursion_and_oracle(kl):
+    group = klsynth.draw_groups(1710, 2)[1][0]
+    d, lo, hi, size, window = 12, 3, 8, 256, (-2.0, 2.0, -2.0, 2.0)
+    p = group_params(kl, group, d, size, window)
+    _, _, feats, labels = kl.lod_labels(p, lo, hi)
+    labels = labels.cpu().numpy().astype(int)
+    assert np.isfinite(feats.cpu().numpy()).all()
+    base = {}
+    acc = 0
+    for k in range(lo, hi + 1):
+        base[k] = acc
+        acc += 4 * 3 ** (k - 1)
+    assert acc == len(labels)
+    for k in range(lo, hi):
+        nk = 3 ** (k - 1)
+        for slot in range(4 * nk):
+            x, r = slot // nk, slot % nk
+            ch = []
+            for q in range(3):
+                y = [t for t in range(4) if t != (x + 2) % 4][q]
+                rk = x - (1 if x > (y + 2) % 4 else 0)
+                ch.append(labels[base[k + 1] + y * 3 * nk + rk * nk + r])
+            lab = labels[base[k] + slot]
+            if max(ch) > 0:
+                assert lab == 1 + max(ch)
+            else:
+                assert lab in (0, 1)
+    g, s = oracle.group(group.ta, group.tb)
+    agree = 0
+    nh = 4 * 3 ** (hi - 1)
+    ext = 256  # extent 1 pixel, in 1/256-pixel fixed point
+    for slot in range(nh):
+        u, v = subtree_pixels(g, s, d, hi, slot, window, size)
+        fin = np.isfinite(u) & np.isfinite(v)
+        if not fin.any():
+            resolved = True
+        else:
+            cu = np.floor(256.0 * u[fin]).astype(np.int64)
+            cv = np.floor(256.0 * v[fin]).astype(np.int64)
+            outside = cu.max() < 0 or cu.min() >= 256 * size or cv.max() < 0 or \
+                cv.min() >= 256 * size
+            small = cu.max() - cu.min() < ext and cv.max() - cv.min() < ext
+            resolved = outside or small
+        agree += (labels[base[hi] + slot] == 0) == resolved
+    assert agree >= 0.995 * nh, (agree, nh)
+
+
+def test_trained_network_gain(kl):
+    from paper_1709_08018_gb300 import lod
+    d, lo, hi, size, extent = 22, 8, 15, 8192, 1.0 / 32
+    train_groups = [g for g, _ in klsynth.draw_groups(klsynth.LOD_TRAIN_SEED, 16)]
+    test_groups = [g for g, _ in klsynth.draw_groups(klsynth.LOD_HELDOUT_SEED, 2)]
+    ptrain = [group_params(kl, g, d, size) for g in train_groups]
+    x, t = lod.make_dataset(ptrain, lo, hi, per_level=60_000, seed=3, extent=extent)
+    mlp, losses = lod.train(x, t, steps=10000, batch=16384, lr=2e-3, seed=5, under=32.0)
+    assert losses[-1] < 0.1 * losses[0]
+    for g in test_groups:
+        p = group_params(kl, g, d, size)
+        floor = lod.evaluate_labels(p, lo, hi, extent)
+        assert floor.words == kl.word_count(d) and floor.iou >= 0.998, floor
+        e = lod.evaluate(p, mlp, lo, hi, margin=0.0, repeats=2)
+        assert e.words == kl.word_count(d)
+        assert e.iou >= 0.998, e
+        assert e.pruned_ms < 0.8 * e.exact_ms, e
