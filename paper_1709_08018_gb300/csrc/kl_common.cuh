@@ -546,6 +546,14 @@ __device__ __forceinline__ void publish_counts(uint32_t in_window, uint32_t word
   }
 }
 
+// Per-warp queue: lane 0 takes the next item and broadcasts it (no block
+// barrier; warps proceed independently).
+__device__ __forceinline__ uint32_t next_item_warp(uint32_t* queue) {
+  uint32_t v = 0;
+  if ((threadIdx.x & 31) == 0) v = atomicAdd(queue, 1u);
+  return __shfl_sync(0xFFFFFFFFu, v, 0);
+}
+
 __device__ __forceinline__ uint32_t next_item(uint32_t* queue) {
   __shared__ uint32_t s_item;
   __syncthreads();
@@ -744,7 +752,7 @@ __device__ __forceinline__ void mixed_item(uint32_t item, const Work& Wk, const 
   int x, u;
   uint32_t pb, c;
   item_of(item, Wk, x, u, pb, c);
-  const uint32_t r = pb * BT + threadIdx.x;
+  const uint32_t r = pb * BT + (threadIdx.x % BT);
   if (r >= L.np) return;
   const uint32_t slot = (uint32_t)x * L.np + r;
   if (T.flags[slot] & kFallback) return;

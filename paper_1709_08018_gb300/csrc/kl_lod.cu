@@ -480,7 +480,7 @@ int build_tables_forced(const kl_params* p, const Plan& L, const View& V, const 
                         const Tables& T, cudaStream_t st) {
   if (cudaMemsetAsync(T.fbcount, 0, 2 * sizeof(uint32_t), st) != cudaSuccess) return KL_ECUDA;
   const uint32_t nParts = parts_count(L);
-  lod_parts_kernel<<<(nParts + 63) / 64, 64, 0, st>>>(G, L, (int)p->renorm_every, T);
+  lod_parts_kernel<<<(nParts + 31) / 32, 32, 0, st>>>(G, L, (int)p->renorm_every, T);
   if (check_launch() != KL_OK) return KL_ECUDA;
   const uint32_t n = combine_count(L);
   lod_combine_kernel<<<(n + 127) / 128, 128, 0, st>>>(V, L, p->parabolic_tol,

@@ -43,25 +43,27 @@ __global__ void __launch_bounds__(BT) render64_kernel(Tables T, Plan L, View V, 
   publish_counts(t.in_window, words, 0, t.atomics, counters);
 }
 
-// Mixed: the queue holds first the FP64 fallback items (BT units each: the
-// near-parabolic, direct-form and far prefixes), then the FP32 items.  Blocks
-// that draw fallback items keep the FP64 pipe busy while the others run FP32
-// work, so the fallback words overlap the FP32 words.
+// Mixed: the queue holds first the FP64 fallback items (32 units each: the
+// near-parabolic, direct-form and far prefixes), then the FP32 items (32
+// prefixes x one suffix chunk).  Each warp draws its own items, so warps never
+// wait for one another; warps that draw fallback items keep the FP64 pipe busy
+// while the others run FP32 work, so the fallback words overlap the FP32 words.
 template <int BT>
 __global__ void __launch_bounds__(BT, 1536 / BT) render_mixed_kernel(
     Tables T, Plan L, View V, Work Wk, uint32_t* __restrict__ img,
     unsigned long long* counters) {
   const uint32_t chunks = (L.ns + kFbChunk - 1) / kFbChunk;
   const uint32_t fb_units = 3u * chunks * (*T.fbcount);
-  const uint32_t n64 = (fb_units + BT - 1) / BT;
+  const uint32_t n64 = (fb_units + 31) / 32;
   const uint32_t total = n64 + Wk.n_items;
+  const uint32_t lane = threadIdx.x & 31;
   Tally t;
   uint32_t words = 0, fp64_words = 0;
   for (;;) {
-    const uint32_t item = next_item(T.fbcount + 1);
+    const uint32_t item = next_item_warp(T.fbcount + 1);
     if (item >= total) break;
     if (item < n64) {
-      const uint32_t unit = item * BT + threadIdx.x;
+      const uint32_t unit = item * 32 + lane;
       if (unit < fb_units) {
         const uint32_t e = unit / (3u * chunks), rem = unit % (3u * chunks);
         const uint32_t slot = (uint32_t)(T.fb[e] & 0xFFFFFFFFull);
@@ -74,7 +76,7 @@ __global__ void __launch_bounds__(BT, 1536 / BT) render_mixed_kernel(
       }
       continue;
     }
-    mixed_item<BT>(item - n64, Wk, L, V, T, t, words, img);
+    mixed_item<32>(item - n64, Wk, L, V, T, t, words, img);
   }
   publish_counts(t.in_window, words, fp64_words, t.atomics, counters);
 }
@@ -177,7 +179,7 @@ int build_tables(const kl_params* p, const Plan& L, const View& V, const Group& 
   const int mixed = p->precision == KL_MIXED;
   if (cudaMemsetAsync(T.fbcount, 0, 2 * sizeof(uint32_t), st) != cudaSuccess) return KL_ECUDA;
   const uint32_t nParts = parts_count(L);
-  parts_kernel<<<(nParts + 63) / 64, 64, 0, st>>>(G, L, (int)p->renorm_every, T);
+  parts_kernel<<<(nParts + 31) / 32, 32, 0, st>>>(G, L, (int)p->renorm_every, T);
   if (check_launch() != KL_OK) return KL_ECUDA;
   const uint32_t n = combine_count(L);
   combine_kernel<<<(n + 127) / 128, 128, 0, st>>>(V, L, p->parabolic_tol, mixed, T);
@@ -212,7 +214,8 @@ int launch_render(const kl_params* p, const Plan& L, const View& V, const Tables
   }
   if (device_slots((const void*)render_mixed_kernel<BT>, BT, &sms, &occ) != KL_OK)
     return KL_ECUDA;
-  const Work Wk = make_work(L, BT, L.npairs, sms * occ, p->chunk_pairs);
+  // warp-sized items (32 prefixes), about 12 per resident warp
+  const Work Wk = make_work(L, 32, L.npairs, sms * occ * (BT / 32), p->chunk_pairs);
   if (prof_mark(g_prof_start, s) != KL_OK) return KL_ECUDA;
   render_mixed_kernel<BT><<<sms * occ, BT, 0, s>>>(T, L, V, Wk, img, cnt);
   if (check_launch() != KL_OK) return KL_ECUDA;
