@@ -680,9 +680,11 @@ __device__ __noinline__ UnitTally fallback_unit(const Pre64* __restrict__ pre,
 // so col = bits(t) - kx with kx = 0x4B400000 - axi.  Any |uf| >= 2^22,
 // infinity or NaN gives a t whose bits put col outside [0, W) (|axi| < 2^20
 // and W <= 2^16), so one unsigned compare per coordinate rejects
-// out-of-window and non-finite words alike.  A pair whose two words are both
-// inside the window and in the pixel of the current run costs one predicated
-// compare chain and one add.
+// out-of-window and non-finite words alike.  Within one prefix kx and ky are
+// fixed, so two words share a pixel exactly when their t bits agree: the
+// current run keeps its pixel's (t_u, t_u) and (t_v, t_v) bit pairs, and a
+// pair of words that both fall in that pixel is settled by two 64-bit compares
+// and one add, without forming pixel ids.
 // Mixed words of prefix slot `slot` on suffix point pairs [k0, k1) of first
 // letter u (see the comment above for the pixel arithmetic).
 template <bool BBOX = false>
@@ -699,6 +701,9 @@ __device__ __forceinline__ void mixed_slot_words(uint32_t slot, int u, uint32_t 
   const int W = (int)V.W;
   const float4* src = T.suf32p + (size_t)u * L.npairs;
   int bc0 = 0x7FFFFFFF, bc1 = -0x7FFFFFFF, br0 = 0x7FFFFFFF, br1 = -0x7FFFFFFF;
+  // t bits of the current run's pixel, doubled; 0 (never a t value) = no
+  // in-window run.  Runs start afresh for every prefix (t.flush below).
+  f2 CU = 0, CV = 0;
 #pragma unroll 2
   for (uint32_t e = k0; e < k1; ++e) {
     const float4 s = __ldg(src + e);
@@ -710,19 +715,22 @@ __device__ __forceinline__ void mixed_slot_words(uint32_t slot, int u, uint32_t 
     const f2 rr = pk(rcp32(ma), rcp32(mb));
     const f2 tx = fma2(C1, wr, mul2(C2, wi));
     const f2 ty = fma2(C3, wr, mul2(C4, wi));
-    float tua, tub, tva, tvb;
-    upk(add2_rm(fma2(tx, rr, AX), magic), tua, tub);
-    upk(add2_rm(fma2(ty, rr, AY), magic), tva, tvb);
-    const int ca = __float_as_int(tua) - k.kx, cb = __float_as_int(tub) - k.kx;
-    const int ra = __float_as_int(tva) - k.ky, rb = __float_as_int(tvb) - k.ky;
-    const int pa = ra * W + ca, pb2 = rb * W + cb;
-    const bool oka = ((uint32_t)ca < V.W) & ((uint32_t)ra < V.H);
-    const bool okb = ((uint32_t)cb < V.W) & ((uint32_t)rb < V.H);
-    if (oka & okb & (pa == t.cur) & (pb2 == t.cur)) {
+    const f2 TU = add2_rm(fma2(tx, rr, AX), magic);
+    const f2 TV = add2_rm(fma2(ty, rr, AY), magic);
+    if ((TU == CU) & (TV == CV)) {
       t.run += 2;
     } else {
-      t.add(oka ? pa : -1, img);
-      t.add(okb ? pb2 : -1, img);
+      float tua, tub, tva, tvb;
+      upk(TU, tua, tub);
+      upk(TV, tva, tvb);
+      const int ca = __float_as_int(tua) - k.kx, cb = __float_as_int(tub) - k.kx;
+      const int ra = __float_as_int(tva) - k.ky, rb = __float_as_int(tvb) - k.ky;
+      const bool oka = ((uint32_t)ca < V.W) & ((uint32_t)ra < V.H);
+      const bool okb = ((uint32_t)cb < V.W) & ((uint32_t)rb < V.H);
+      t.add(oka ? ra * W + ca : -1, img);
+      t.add(okb ? rb * W + cb : -1, img);
+      CU = okb ? pk(tub, tub) : 0ull;
+      CV = okb ? pk(tvb, tvb) : 0ull;
     }
     if (BBOX) {
       float ua, ub, va, vb;
