@@ -269,16 +269,19 @@ def batch_sweep(kl, dev, steps: int):
     return out
 
 
-def lod_config(kl, n_train: int = 64, n_test: int = 16):
+def lod_config(kl, n_train: int = 64, n_test: int = 16, n_valid: int = 8):
     """Learned level-of-detail pruning: the network trained by the library's
-    kernels on exact depth-22 renders of n_train groups (seed 1710), judged on
-    n_test held-out groups (seed 1711) at 8192^2 against the exact render."""
+    kernels on exact depth-22 renders of n_train groups (seed 1710), its
+    pruning setting chosen on n_valid validation groups (seed 1712, target
+    IoU 0.9995), judged on n_test held-out groups (seed 1711) at 8192^2
+    against the exact render."""
     import torch
     from paper_1709_08018_gb300 import lod
-    d, size, lo, hi, extent, under, margin = 22, 8192, 8, 15, 1.0 / 32, 32.0, 0.0
+    d, size, lo, hi, extent, under = 22, 8192, 8, 15, 1.0 / 32, 32.0
     W = (-2.0, 2.0, -2.0, 2.0)
     mk = lambda g: kl.params_init(g.ta, g.tb, d, size, size, W, kl.MIXED)
     tr = [mk(g) for g, _ in klsynth.draw_groups(klsynth.LOD_TRAIN_SEED, n_train)]
+    va = [mk(g) for g, _ in klsynth.draw_groups(klsynth.LOD_VALID_SEED, n_valid)]
     te = [mk(g) for g, _ in klsynth.draw_groups(klsynth.LOD_HELDOUT_SEED, n_test)]
     t0 = time.time()
     x, t = lod.make_dataset(tr, lo, hi, per_level=60_000, seed=3, extent=extent)
@@ -286,13 +289,19 @@ def lod_config(kl, n_train: int = 64, n_test: int = 16):
     mlp, losses = lod.train(x, t, steps=10000, batch=16384, lr=2e-3, seed=5, under=under)
     torch.cuda.synchronize()
     t2 = time.time()
-    evals = [lod.evaluate(p, mlp, lo, hi, margin, repeats=3) for p in te]
+    tuned = lod.tune_prune(va, mlp, lo, hi, target=0.9995)
+    margin, edge = tuned["margin"], tuned["edge"]
+    evals = [lod.evaluate(p, mlp, lo, hi, margin, edge, repeats=3) for p in te]
     s = lod.summarize(evals)
     s.update({"workload": f"{n_test} held-out groups (seed 1711), depth 22 "
                           f"({kl.word_count(d)} words each), 8192^2 over [-2,2]^2; network "
-                          f"trained on {n_train} groups (seed 1710)",
+                          f"trained on {n_train} groups (seed 1710); pruning setting chosen "
+                          f"on {n_valid} validation groups (seed 1712)",
               "levels": [lo, hi], "label_extent_px": extent, "under_weight": under,
-              "margin": margin, "train_samples": int(x.shape[0]), "train_steps": 10000,
+              "margin": margin, "edge_px": edge,
+              "valid_settings": [{"margin": m, "edge_px": e, "iou_min": round(i, 6),
+                                  "ms": round(t, 3)} for m, e, i, t in tuned["tried"]],
+              "train_samples": int(x.shape[0]), "train_steps": 10000,
               "loss_first_last": [losses[0], losses[-1]], "label_seconds": t1 - t0,
               "train_seconds": t2 - t1,
               "words_per_s_pruned": n_test * kl.word_count(d) / (s["pruned_ms"] / 1000.0),

@@ -288,25 +288,28 @@ KL_API size_t kl_lod_render_bytes(const kl_params* p, uint32_t lo, uint32_t hi);
  * KL_MIXED).  From level lo to hi each active node is scored by the network
  * (d_mlp: KL_MLP_NPARAMS floats).  A node with score + margin < 1/2 whose
  * first, middle and last words in index order (the words taking the allowed
- * letter of rank 0, 1, 2 at every step) fall into one pixel adds all 3^(d-k)
- * words of its subtree to that pixel (all three outside the window: counts
+ * letter of rank 0, 1, 2 at every step) fall into one pixel, each at least
+ * `edge` pixels from that pixel's sides, adds all 3^(d-k) words of its
+ * subtree to that pixel (all three at least `edge` outside the window: counts
  * them dropped); the others expand; nodes still active at level hi are
- * rendered exactly.  Every word is counted once (in d_counters, as
- * kl_render).  d_stats (4 uint64): nodes scored, nodes pruned, level-hi nodes
- * rendered exactly, 0.  Exact wherever the network's calls are right. */
+ * rendered exactly.  With edge = the label extent the network was trained
+ * for (kl_lod_labels), a right prediction keeps every word in its own pixel.
+ * Every word is counted once (in d_counters, as kl_render).  d_stats (4
+ * uint64): nodes scored, nodes pruned, level-hi nodes rendered exactly, 0.
+ * KL_EINVAL unless 0 <= edge < 1/2. */
 KL_API int kl_render_lod(const kl_params* p, uint32_t lo, uint32_t hi, const float* d_mlp,
-                         float margin, uint32_t* d_image, uint64_t* d_counters,
+                         float margin, float edge, uint32_t* d_image, uint64_t* d_counters,
                          uint64_t* d_stats, void* d_workspace, size_t workspace_bytes,
                          void* stream);
 
 /* As kl_render_lod, with the true labels of kl_lod_labels (same p, lo, hi)
- * taking the network's place: a node is pruned exactly when its label is 0.
- * It measures what the pruned render loses by its splat alone, separately
- * from the network's errors. */
+ * taking the network's place: a node is pruned when its label is 0 and the
+ * edge test passes.  It measures what the pruned render loses by its splat
+ * alone, separately from the network's errors. */
 KL_API int kl_render_lod_labels(const kl_params* p, uint32_t lo, uint32_t hi,
-                                const uint8_t* d_labels, uint32_t* d_image, uint64_t* d_counters,
-                                uint64_t* d_stats, void* d_workspace, size_t workspace_bytes,
-                                void* stream);
+                                const uint8_t* d_labels, float edge, uint32_t* d_image,
+                                uint64_t* d_counters, uint64_t* d_stats, void* d_workspace,
+                                size_t workspace_bytes, void* stream);
 
 /* Size of the library's own device scratch array used by kl_render_noalloc. */
 #define KL_STATIC_SCRATCH_BYTES (32u << 20)

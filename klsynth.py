@@ -102,6 +102,9 @@ SAMPLE_SEED = 1709
 BATCH_SEED = 1709
 LOD_TRAIN_SEED = 1710
 LOD_HELDOUT_SEED = 1711
+# Validation groups for choosing the pruning setting, apart from both the
+# training and the held-out groups.
+LOD_VALID_SEED = 1712
 
 
 def draw_groups(seed: int, n: int, depth_lo: int = 12, depth_hi: int = 18

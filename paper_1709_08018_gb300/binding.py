@@ -112,10 +112,12 @@ def lib():
         L.kl_lod_labels.restype = I
         L.kl_lod_render_bytes.argtypes = [ctypes.POINTER(Params), U32, U32]
         L.kl_lod_render_bytes.restype = SZ
-        L.kl_render_lod.argtypes = [ctypes.POINTER(Params), U32, U32, P, ctypes.c_float, P, P, P,
+        L.kl_render_lod.argtypes = [ctypes.POINTER(Params), U32, U32, P, ctypes.c_float,
+                                    ctypes.c_float, P, P, P,
                                     P, SZ, P]
         L.kl_render_lod.restype = I
-        L.kl_render_lod_labels.argtypes = [ctypes.POINTER(Params), U32, U32, P, P, P, P, P, SZ, P]
+        L.kl_render_lod_labels.argtypes = [ctypes.POINTER(Params), U32, U32, P, ctypes.c_float, P,
+                                           P, P, P, SZ, P]
         L.kl_render_lod_labels.restype = I
         L.kl_render_noalloc.argtypes = [ctypes.POINTER(Params), P, P, P]
         L.kl_render_noalloc.restype = I
@@ -395,18 +397,20 @@ class LodRenderer:
         self.counters = torch.zeros(KL_N_COUNTERS, dtype=torch.int64, device=device)
         self.stats = torch.zeros(4, dtype=torch.int64, device=device)
 
-    def __call__(self, mlp_params, margin: float = 0.0, stream=None):
+    def __call__(self, mlp_params, margin: float = 0.0, edge: float = 0.0, stream=None):
+        """Pruned render; `edge`: the distance in pixels a pruned node's
+        representative words must keep from their pixel's sides."""
         _check(lib().kl_render_lod(ctypes.byref(self.p), self.lo, self.hi, mlp_params.data_ptr(),
-                                   margin, self.image.data_ptr(), self.counters.data_ptr(),
+                                   margin, edge, self.image.data_ptr(), self.counters.data_ptr(),
                                    self.stats.data_ptr(), self.workspace.data_ptr(),
                                    self.workspace.numel(), _stream_handle(stream)),
                "kl_render_lod")
         return self.image, self.counters, self.stats
 
-    def with_labels(self, labels, stream=None):
+    def with_labels(self, labels, edge: float = 0.0, stream=None):
         """The same render pruned by the true labels (kl_render_lod_labels)."""
         _check(lib().kl_render_lod_labels(ctypes.byref(self.p), self.lo, self.hi,
-                                          labels.data_ptr(), self.image.data_ptr(),
+                                          labels.data_ptr(), edge, self.image.data_ptr(),
                                           self.counters.data_ptr(), self.stats.data_ptr(),
                                           self.workspace.data_ptr(), self.workspace.numel(),
                                           _stream_handle(stream)), "kl_render_lod_labels")

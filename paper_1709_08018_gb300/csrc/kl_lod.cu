@@ -18,13 +18,17 @@
 //
 // Pruned render.  From level lo down, the network predicts each active
 // node's label from the 8 features of its det-normalised prefix matrix.  A
-// node predicted resolved (y + margin < 1/2) whose first, middle and last
-// words in index order (the two ends and the middle of its piece of the limit
-// set) fall into one pixel adds its 3^(D-k) words to that pixel (or, if all
-// three miss the window, counts them dropped); a sub-pixel piece that
-// straddles a pixel edge fails that check and is expanded instead.  The others expand to their children; nodes still active at
-// level hi are rendered exactly (all their words) by the mixed kernel.  Every
-// word is counted once.
+// node predicted resolved (y + margin < 1/2) is pruned when its first, middle
+// and last words in index order (the two ends and the middle of its piece of
+// the limit set) fall into one pixel, each at least `edge` pixels away from
+// that pixel's sides (or all three at least `edge` outside the window): it
+// adds its 3^(D-k) words to that pixel (or counts them dropped).  A resolved
+// node's words all lie within `extent` of one another, so with edge = extent
+// a right prediction never moves a word across a pixel edge; a node too near
+// an edge is expanded instead, and its smaller children are tried in turn.
+// The others expand to their children; nodes still active at level hi are
+// rendered exactly (all their words) by the mixed kernel.  Every word is
+// counted once.
 #include "kl_mlp_dev.cuh"
 
 namespace {
@@ -214,6 +218,21 @@ __global__ void features_kernel(Group G, LodPlan P, float* __restrict__ out) {
 // level-k node ending in letter x: the suffix of D - k letters that takes the
 // allowed letter of rank e at every step.
 constexpr int kReps = 3;
+constexpr int kNearEdge = -2;
+
+// Pixel id of pixel coordinates (u, v) if the point lies at least `edge`
+// inside that pixel; -1 if it lies at least `edge` outside the window (or is
+// not finite); kNearEdge otherwise.
+__device__ __forceinline__ int guarded_pixel(double u, double v, const View& V, double edge) {
+  if (!(fabs(u) < 4.0e9 && fabs(v) < 4.0e9)) return -1;
+  const double W = (double)V.W, H = (double)V.H;
+  if (u < -edge || v < -edge || u >= W + edge || v >= H + edge) return -1;
+  if (u < 0.0 || v < 0.0 || u >= W || v >= H) return kNearEdge;
+  const double fu = floor(u), fv = floor(v);
+  if (u - fu < edge || fu + 1.0 - u <= edge || v - fv < edge || fv + 1.0 - v <= edge)
+    return kNearEdge;
+  return (int)fv * (int)V.W + (int)fu;
+}
 
 __global__ void vstar_kernel(Group G, int D, int lo, int hi, double2* vstar) {
   const int x = threadIdx.x & 3, e = (threadIdx.x >> 2) % kReps;
@@ -250,7 +269,7 @@ __global__ void init_active_kernel(Group G, int k, uint32_t nk, Active* out, uin
 __global__ void __launch_bounds__(kLodThreads) expand_kernel(
     const float* __restrict__ mlp, const uint8_t* __restrict__ labels, Group G, View V, int D,
     int k, int hi, uint32_t nk,
-    float margin, const double2* __restrict__ vstar, const Active* __restrict__ in,
+    float margin, double edge, const double2* __restrict__ vstar, const Active* __restrict__ in,
     const uint32_t* __restrict__ in_count, Active* __restrict__ out, uint32_t* out_count,
     uint32_t* __restrict__ deferred, uint32_t* deferred_count, uint32_t* __restrict__ img,
     unsigned long long* counters, unsigned long long* stats) {
@@ -306,9 +325,9 @@ __global__ void __launch_bounds__(kLodThreads) expand_kernel(
         for (int e = 0; e < kReps; ++e) {
           const double2 v = vstar[(e * 4 + x) * (hi + 1) + k];
           const dc z = mobius(P, {v.x, v.y});
-          const int pe = pixel64((z.re - V.x0) * V.sx, (V.y1 - z.im) * V.sy, V);
+          const int pe = guarded_pixel((z.re - V.x0) * V.sx, (V.y1 - z.im) * V.sy, V, edge);
           if (e == 0) pix = pe;
-          else if (pe != pix) prune = false;
+          if (pe == kNearEdge || pe != pix) prune = false;
         }
       }
       if (prune) {
@@ -575,7 +594,7 @@ extern "C" size_t kl_lod_render_bytes(const kl_params* p, uint32_t lo, uint32_t 
 namespace {
 
 int render_lod_impl(const kl_params* p, uint32_t lo, uint32_t hi, const float* d_mlp,
-                    const uint8_t* d_labels, float margin, uint32_t* d_image,
+                    const uint8_t* d_labels, float margin, float edge, uint32_t* d_image,
                     uint64_t* d_counters, uint64_t* d_stats, void* d_workspace,
                     size_t workspace_bytes, void* stream) {
   LodPlan P;
@@ -583,6 +602,7 @@ int render_lod_impl(const kl_params* p, uint32_t lo, uint32_t hi, const float* d
   int st = lod_plan(p, lo, hi, &P, &L);
   if (st != KL_OK) return st;
   if (p->precision != KL_MIXED) return KL_EINVAL;
+  if (!(edge >= 0.0f && edge < 0.5f)) return KL_EINVAL;
   if ((!d_mlp && !d_labels) || !d_image || !d_counters || !d_stats || !d_workspace)
     return KL_EINVAL;
   if (((uintptr_t)d_workspace & 255u) != 0) return KL_EINVAL;
@@ -616,7 +636,7 @@ int render_lod_impl(const kl_params* p, uint32_t lo, uint32_t hi, const float* d
     const int cur = (k - (int)lo) & 1;
     expand_kernel<<<grid_for(4ull * P.p3[k], kLodThreads, 4), kLodThreads, 0, s>>>(
         d_mlp, d_labels ? d_labels + P.base[k] : nullptr, G, V, P.D, k, (int)hi, P.p3[k],
-        d_mlp ? margin : 0.0f, vstar, act[cur], counts + k, act[cur ^ 1],
+        d_mlp ? margin : 0.0f, (double)edge, vstar, act[cur], counts + k, act[cur ^ 1],
         counts + k + 1, deferred, counts + 32, d_image, cnt, stats);
     if (check_launch() != KL_OK) return KL_ECUDA;
   }
@@ -633,19 +653,19 @@ int render_lod_impl(const kl_params* p, uint32_t lo, uint32_t hi, const float* d
 }  // namespace
 
 extern "C" int kl_render_lod(const kl_params* p, uint32_t lo, uint32_t hi, const float* d_mlp,
-                             float margin, uint32_t* d_image, uint64_t* d_counters,
+                             float margin, float edge, uint32_t* d_image, uint64_t* d_counters,
                              uint64_t* d_stats, void* d_workspace, size_t workspace_bytes,
                              void* stream) {
   if (!d_mlp) return KL_EINVAL;
-  return render_lod_impl(p, lo, hi, d_mlp, nullptr, margin, d_image, d_counters, d_stats,
+  return render_lod_impl(p, lo, hi, d_mlp, nullptr, margin, edge, d_image, d_counters, d_stats,
                          d_workspace, workspace_bytes, stream);
 }
 
 extern "C" int kl_render_lod_labels(const kl_params* p, uint32_t lo, uint32_t hi,
-                                    const uint8_t* d_labels, uint32_t* d_image,
+                                    const uint8_t* d_labels, float edge, uint32_t* d_image,
                                     uint64_t* d_counters, uint64_t* d_stats, void* d_workspace,
                                     size_t workspace_bytes, void* stream) {
   if (!d_labels) return KL_EINVAL;
-  return render_lod_impl(p, lo, hi, nullptr, d_labels, 0.0f, d_image, d_counters, d_stats,
-                         d_workspace, workspace_bytes, stream);
+  return render_lod_impl(p, lo, hi, nullptr, d_labels, 0.0f, edge, d_image, d_counters,
+                         d_stats, d_workspace, workspace_bytes, stream);
 }

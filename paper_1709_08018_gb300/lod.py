@@ -68,8 +68,11 @@ def make_dataset(params: Sequence[kb.Params], lo: int, hi: int, per_level: int, 
 
 def train(x, t, steps: int, batch: int, lr: float, seed: int, init=None, under: float = 1.0):
     """Adam on the (weighted) mean squared error of the label, random
-    mini-batches; `under` > 1 weighs predictions below the label (too-early
+    mini-batches, learning rate decayed from `lr` to 0 along a half cosine
+    (so that the final parameters do not carry the mini-batch noise of a
+    constant rate); `under` > 1 weighs predictions below the label (too-early
     prunes) more."""
+    import math
     import torch
     params = init_params(seed) if init is None else init.clone()
     tr = kb.MlpTrainer(params, lr=lr, under_weight=under)
@@ -78,6 +81,7 @@ def train(x, t, steps: int, batch: int, lr: float, seed: int, init=None, under: 
     n = x.shape[0]
     losses = []
     for s in range(steps):
+        tr.lr = lr * 0.5 * (1.0 + math.cos(math.pi * s / steps))
         idx = torch.randint(0, n, (min(batch, n),), generator=gen, device="cuda")
         loss = tr.step(x[idx].contiguous(), t[idx].contiguous())
         if s % 50 == 0 or s == steps - 1:
@@ -114,35 +118,7 @@ def _time(fn, repeats: int = 3) -> float:
     return best
 
 
-def evaluate(p: kb.Params, mlp, lo: int, hi: int, margin: float, repeats: int = 3) -> Eval:
-    """Pruned against exact render of one group (both timed with CUDA events)."""
-    r = kb.Renderer(p)
-    exact_ms = _time(lambda: r(), repeats)
-    exact = r.image.clone()
-    lod = kb.LodRenderer(p, lo, hi)
-    pruned_ms = _time(lambda: lod(mlp, margin), repeats)
-    img, cnt, st = lod(mlp, margin)
-    a, b = exact != 0, img != 0
-    inter = int((a & b).sum())
-    union = int((a | b).sum())
-    st = st.cpu().tolist()
-    c = cnt.cpu().tolist()
-    return Eval(iou=inter / union if union else 1.0, missed=int((a & ~b).sum()),
-                extra=int((b & ~a).sum()), occupied=int(a.sum()), exact_ms=exact_ms,
-                pruned_ms=pruned_ms, nodes=st[0], pruned_nodes=st[1], deferred=st[2],
-                words=c[0] + c[1])
-
-
-def evaluate_labels(p: kb.Params, lo: int, hi: int, extent: float = 1.0) -> Eval:
-    """Pruning by the true labels against the exact render: what the splat
-    loses when every prune decision is right."""
-    r = kb.Renderer(p)
-    exact_ms = _time(lambda: r(), 1)
-    exact = r.image.clone()
-    _, _, _, labels = kb.lod_labels(p, lo, hi, extent=extent)
-    lod = kb.LodRenderer(p, lo, hi)
-    pruned_ms = _time(lambda: lod.with_labels(labels), 1)
-    img, cnt, st = lod.with_labels(labels)
+def _compare(exact, img, cnt, st, exact_ms, pruned_ms) -> Eval:
     a, b = exact != 0, img != 0
     inter, union = int((a & b).sum()), int((a | b).sum())
     st, c = st.cpu().tolist(), cnt.cpu().tolist()
@@ -150,6 +126,68 @@ def evaluate_labels(p: kb.Params, lo: int, hi: int, extent: float = 1.0) -> Eval
                 extra=int((b & ~a).sum()), occupied=int(a.sum()), exact_ms=exact_ms,
                 pruned_ms=pruned_ms, nodes=st[0], pruned_nodes=st[1], deferred=st[2],
                 words=c[0] + c[1])
+
+
+def evaluate(p: kb.Params, mlp, lo: int, hi: int, margin: float, edge: float = 0.0,
+             repeats: int = 3) -> Eval:
+    """Pruned against exact render of one group (both timed with CUDA events)."""
+    r = kb.Renderer(p)
+    exact_ms = _time(lambda: r(), repeats)
+    exact = r.image.clone()
+    lod = kb.LodRenderer(p, lo, hi)
+    pruned_ms = _time(lambda: lod(mlp, margin, edge), repeats)
+    img, cnt, st = lod(mlp, margin, edge)
+    return _compare(exact, img, cnt, st, exact_ms, pruned_ms)
+
+
+def evaluate_labels(p: kb.Params, lo: int, hi: int, extent: float = 1.0) -> Eval:
+    """Pruning by the true labels (edge guard = the label extent) against the
+    exact render: what the splat loses when every prune decision is right."""
+    r = kb.Renderer(p)
+    exact_ms = _time(lambda: r(), 1)
+    exact = r.image.clone()
+    _, _, _, labels = kb.lod_labels(p, lo, hi, extent=extent)
+    lod = kb.LodRenderer(p, lo, hi)
+    pruned_ms = _time(lambda: lod.with_labels(labels, extent), 1)
+    img, cnt, st = lod.with_labels(labels, extent)
+    return _compare(exact, img, cnt, st, exact_ms, pruned_ms)
+
+
+# Pruning settings tried by tune_prune: margin (added to the score before the
+# 1/2 threshold; negative prunes more) x edge guard in pixels (larger sends
+# more near-edge nodes down the tree).
+PRUNE_MARGINS = (-1.4, -1.2, -1.0, -0.8, -0.6, -0.4, -0.2, 0.0)
+PRUNE_EDGES = (0.0, 1 / 512, 1 / 128)
+
+
+def tune_prune(params: Sequence[kb.Params], mlp, lo: int, hi: int, target: float = 0.9995,
+               margins=PRUNE_MARGINS, edges=PRUNE_EDGES) -> Dict:
+    """The fastest (margin, edge) setting whose pruned renders of `params`
+    all reach occupancy IoU >= target against their exact renders (the
+    setting with the best worst-case IoU if none does).  `params` are
+    validation groups, apart from both the training and the held-out groups.
+    Returns {"margin", "edge", "tried": [(margin, edge, worst IoU, ms)]}."""
+    exact, lods = [], []
+    for p in params:
+        r = kb.Renderer(p)
+        r()
+        exact.append(r.image != 0)
+        lods.append(kb.LodRenderer(p, lo, hi))
+        del r
+    tried = []
+    for margin in margins:
+        for edge in edges:
+            worst, ms = 1.0, 0.0
+            for occ, L in zip(exact, lods):
+                ms += _time(lambda: L(mlp, margin, edge), 1)
+                img, _, _ = L(mlp, margin, edge)
+                b = img != 0
+                union = int((occ | b).sum())
+                worst = min(worst, int((occ & b).sum()) / union if union else 1.0)
+            tried.append((margin, edge, worst, ms))
+    ok = [t for t in tried if t[2] >= target]
+    best = min(ok, key=lambda t: t[3]) if ok else max(tried, key=lambda t: t[2])
+    return {"margin": best[0], "edge": best[1], "tried": tried}
 
 
 def summarize(evals: List[Eval]) -> Dict:
@@ -164,4 +202,7 @@ def summarize(evals: List[Eval]) -> Dict:
             "speedup": float(sum(e.exact_ms for e in evals) / sum(e.pruned_ms for e in evals)),
             "nodes_scored": int(sum(e.nodes for e in evals)),
             "nodes_pruned": int(sum(e.pruned_nodes for e in evals)),
-            "deferred_nodes": int(sum(e.deferred for e in evals))}
+            "deferred_nodes": int(sum(e.deferred for e in evals)),
+            "per_group": [{"iou": round(e.iou, 6), "exact_ms": round(e.exact_ms, 3),
+                           "pruned_ms": round(e.pruned_ms, 3), "nodes": e.nodes,
+                           "pruned": e.pruned_nodes, "deferred": e.deferred} for e in evals]}

@@ -99,3 +99,19 @@ def test_autotuner_default_split_matches_library(kl):
         auto = kl.workspace_bytes(p)
         p.prefix_len = autotune.default_prefix_len(d, False)
         assert kl.workspace_bytes(p) == auto, d
+
+
+def test_pruned_render_rejects_bad_edge(kl):
+    """The edge guard must lie in [0, 1/2); the check comes before any device
+    call (the pointers below are never dereferenced)."""
+    import ctypes
+    p = kl.params_init(2 + 0j, 2 + 0j, 22, 8192, 8192, (-2.0, 2.0, -2.0, 2.0), kl.MIXED)
+    fake = 0x1000
+    L = kl.binding.lib()
+    for edge in (-0.01, 0.5, 0.7, float("nan")):
+        st = L.kl_render_lod(ctypes.byref(p), 8, 15, fake, 0.0, edge, fake, fake, fake, fake,
+                             1 << 30, None)
+        assert st == 1, edge  # KL_EINVAL
+        st = L.kl_render_lod_labels(ctypes.byref(p), 8, 15, fake, edge, fake, fake, fake, fake,
+                                    1 << 30, None)
+        assert st == 1, edge
