@@ -240,7 +240,9 @@ KL_API size_t kl_mlp_scratch_bytes(uint64_t n);
  * y_i < t_i and 1 elsewhere (under_weight > 1 penalises predicting too few
  * levels, the direction that prunes too early); d_grad = its gradient
  * (KL_MLP_NPARAMS floats, same layout as the parameters).  Both are
- * overwritten. */
+ * overwritten.  The partial sums are added in a fixed order (no floating-
+ * point atomics), so equal inputs give bit-identical results on one GPU
+ * model. */
 KL_API int kl_mlp_grad(const float* d_params, const float* d_x, const float* d_t, uint64_t n,
                        float under_weight, float* d_grad, float* d_loss, void* d_scratch,
                        size_t scratch_bytes, void* stream);

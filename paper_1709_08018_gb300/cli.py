@@ -2,9 +2,15 @@
 
   python -m paper_1709_08018_gb300.cli --config gasket-d18-4096 --precision mixed \
       [--repeat N] [--out image.npy]
+  python -m paper_1709_08018_gb300.cli --batch 32 [--repeat N]
+  python -m paper_1709_08018_gb300.cli --lod [--train-groups 4] [--train-steps 300] [--repeat N]
 
 Prints the counters and the device time of the last render.  With --repeat N
 the render runs N times (the first ones serve as warm-up for profilers).
+--batch G renders the first G groups of the seeded 256-group sweep (depth
+12..18, 1024^2 each) in one batched launch.  --lod trains the pruning network
+briefly on a few seeded groups (labels, gradient and Adam kernels) and runs
+the pruned depth-22 render of one held-out group at 8192^2.
 """
 import argparse
 import os
@@ -33,7 +39,15 @@ def main(argv=None):
     ap.add_argument("--prefix-len", type=int, default=0)
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--out")
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--lod", action="store_true")
+    ap.add_argument("--train-groups", type=int, default=4)
+    ap.add_argument("--train-steps", type=int, default=300)
     a = ap.parse_args(argv)
+    if a.batch:
+        return run_batch(a, kl, klsynth, torch)
+    if a.lod:
+        return run_lod(a, kl, klsynth, torch)
     c = named[a.config]
     ta = a.ta if a.ta is not None else c.group.ta
     tb = a.tb if a.tb is not None else c.group.tb
@@ -55,6 +69,46 @@ def main(argv=None):
           f"{e0.elapsed_time(e1):.3f} ms")
     if a.out:
         np.save(a.out, r.image.cpu().numpy().view(np.uint32))
+
+
+def run_batch(a, kl, klsynth, torch):
+    cfgs = klsynth.batch_configs(256)[:a.batch]
+    ps = [kl.params_init(c.group.ta, c.group.tb, c.depth, c.width, c.height, c.window, kl.MIXED)
+          for c in cfgs]
+    b = kl.Batch(ps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(a.repeat):
+        b.counters.zero_()
+        e0.record()
+        b.render()
+        e1.record()
+    torch.cuda.synchronize()
+    cnt = b.counters.sum(0).cpu().tolist()
+    words = sum(c.n_words for c in cfgs)
+    print(f"batch of {a.batch} groups: words {words}, in-window {cnt[0]}, dropped {cnt[1]}, "
+          f"fp64 words {cnt[2]}, atomics {cnt[3]}, {e0.elapsed_time(e1):.3f} ms")
+
+
+def run_lod(a, kl, klsynth, torch):
+    from paper_1709_08018_gb300 import lod
+    d, size, lo, hi, extent = 22, 8192, 8, 15, 1.0 / 32
+    W = (-2.0, 2.0, -2.0, 2.0)
+    mk = lambda g: kl.params_init(g.ta, g.tb, d, size, size, W, kl.MIXED)
+    tr = [mk(g) for g, _ in klsynth.draw_groups(klsynth.LOD_TRAIN_SEED, a.train_groups)]
+    x, t = lod.make_dataset(tr, lo, hi, per_level=20_000, seed=3, extent=extent)
+    mlp, losses = lod.train(x, t, steps=a.train_steps, batch=16384, lr=2e-3, seed=5, under=32.0)
+    g = klsynth.draw_groups(klsynth.LOD_HELDOUT_SEED, 1)[0][0]
+    L = kl.LodRenderer(mk(g), lo, hi)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(a.repeat):
+        e0.record()
+        img, cnt, st = L(mlp, -0.8, 1.0 / 512)
+        e1.record()
+    torch.cuda.synchronize()
+    st, cnt = st.cpu().tolist(), cnt.cpu().tolist()
+    print(f"lod d={d} {size}^2 levels {lo}..{hi}: loss {losses[0]:.3g} -> {losses[-1]:.3g}, "
+          f"nodes {st[0]}, pruned {st[1]}, deferred {st[2]}, words {cnt[0] + cnt[1]}, "
+          f"{e0.elapsed_time(e1):.3f} ms")
 
 
 if __name__ == "__main__":

@@ -198,15 +198,27 @@ __global__ void reduce_labels_kernel(uint32_t nk, const int4* __restrict__ cbox,
   }
 }
 
-__global__ void features_kernel(Group G, LodPlan P, float* __restrict__ out) {
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < P.total;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    int k = P.lo;
-    while (k < P.hi && i >= P.base[k + 1]) ++k;
-    const uint32_t slot = (uint32_t)(i - P.base[k]);
+// Features of the level-k nodes.  As for the render's prefixes, each node
+// matrix is one product P = H L of a tail (the q innermost letters) and a head
+// (the other k - q) from two small tables built first by part_entry, instead
+// of k - 1 products per node.
+__global__ void feature_parts_kernel(Group G, Plan Lk, int renorm, Tables T) {
+  const uint32_t n = 4u * Lk.p3_q1 + (Lk.p > Lk.q ? 4u * Lk.p3_pq : 0u);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    part_entry(G, Lk, renorm, i, T);
+}
+
+__global__ void features_kernel(Plan Lk, Tables T, float* __restrict__ out) {
+  const uint32_t n = 4u * Lk.np;
+  for (uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x; slot < n;
+       slot += gridDim.x * blockDim.x) {
+    const uint32_t x = slot / Lk.np, r = slot % Lk.np;
+    const PartM& TL = T.Lt[x * Lk.p3_q1 + r / Lk.p3_pq];
+    const M2 P =
+        Lk.p > Lk.q ? mmul(T.Ht[(uint32_t)TL.edge * Lk.p3_pq + r % Lk.p3_pq], TL.m) : TL.m;
     float f[8];
-    node_features(node_matrix(G, k, slot, P.p3[k]), f);
-    for (int j = 0; j < 8; ++j) out[i * 8 + j] = f[j];
+    node_features(P, f);
+    for (int j = 0; j < 8; ++j) out[(size_t)slot * 8 + j] = f[j];
   }
 }
 
@@ -472,7 +484,8 @@ RenderLayout render_layout(const LodPlan& P, const Plan& L) {
 }
 
 int build_tables_forced(const kl_params* p, const Plan& L, const View& V, const Group& G,
-                        const Tables& T, cudaStream_t st);
+                        const Tables& T, cudaStream_t st, const uint32_t* slots,
+                        const uint32_t* n_slots);
 
 unsigned grid_for(uint64_t n, int threads, int cap_per_sm) {
   const int sms = sm_count();
@@ -495,12 +508,34 @@ __global__ void lod_combine_kernel(View V, Plan L, double ptol, int mixed, Table
     combine_entry(V, L, ptol, mixed, idx, T, 0u, T.fb, T.fbcount);
 }
 
+// The pruned render needs the prefix constants of the deferred level-hi
+// nodes only: the entries of the `n` slots listed in `slots`, then every
+// suffix point.
+__global__ void lod_combine_listed_kernel(View V, Plan L, double ptol, int mixed, Tables T,
+                                          const uint32_t* __restrict__ slots,
+                                          const uint32_t* __restrict__ n_slots) {
+  const uint32_t n = *n_slots, total = n + 4u * L.ns;
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += gridDim.x * blockDim.x) {
+    const uint32_t idx = e < n ? slots[e] : 4u * L.np + (e - n);
+    combine_entry(V, L, ptol, mixed, idx, T, 0u, T.fb, T.fbcount);
+  }
+}
+
+// Tables of *p for the split (prefix hi, suffix D - hi): every prefix slot,
+// or, with `slots`, only the listed ones.
 int build_tables_forced(const kl_params* p, const Plan& L, const View& V, const Group& G,
-                        const Tables& T, cudaStream_t st) {
+                        const Tables& T, cudaStream_t st, const uint32_t* slots,
+                        const uint32_t* n_slots) {
   if (cudaMemsetAsync(T.fbcount, 0, 2 * sizeof(uint32_t), st) != cudaSuccess) return KL_ECUDA;
   const uint32_t nParts = parts_count(L);
   lod_parts_kernel<<<(nParts + 31) / 32, 32, 0, st>>>(G, L, (int)p->renorm_every, T);
   if (check_launch() != KL_OK) return KL_ECUDA;
+  if (slots) {
+    lod_combine_listed_kernel<<<grid_for(combine_count(L), 128, 8), 128, 0, st>>>(
+        V, L, p->parabolic_tol, p->precision == KL_MIXED, T, slots, n_slots);
+    return check_launch();
+  }
   const uint32_t n = combine_count(L);
   lod_combine_kernel<<<(n + 127) / 128, 128, 0, st>>>(V, L, p->parabolic_tol,
                                                        p->precision == KL_MIXED, T);
@@ -555,7 +590,7 @@ extern "C" int kl_lod_labels(const kl_params* p, uint32_t lo, uint32_t hi, float
     return KL_ECUDA;
   box_init_kernel<<<grid_for(nh, 256, 8), 256, 0, s>>>(B, nh);
   if (check_launch() != KL_OK) return KL_ECUDA;
-  st = build_tables_forced(&q, L, V, G, T, s);
+  st = build_tables_forced(&q, L, V, G, T, s, nullptr, nullptr);
   if (st != KL_OK) return st;
   int sms = 0, occ = 0;
   const bool mixed = p->precision == KL_MIXED;
@@ -580,8 +615,23 @@ extern "C" int kl_lod_labels(const kl_params* p, uint32_t lo, uint32_t hi, float
         lvl_box + P.base[k], d_labels + P.base[k]);
     if (check_launch() != KL_OK) return KL_ECUDA;
   }
-  features_kernel<<<grid_for(P.total, 128, 16), 128, 0, s>>>(G, P, d_features);
-  return check_launch();
+  // the render tables are no longer needed: their tail and head arrays hold
+  // each level's (smaller) feature tables in turn
+  for (int k = (int)lo; k <= (int)hi; ++k) {
+    Plan Lk = L;
+    Lk.p = k;
+    Lk.q = (k + 1) / 2;
+    Lk.np = pow3u(k - 1);
+    Lk.p3_q1 = pow3u(Lk.q - 1);
+    Lk.p3_pq = pow3u(k - Lk.q);
+    const uint32_t nparts = 4u * Lk.p3_q1 + (k > Lk.q ? 4u * Lk.p3_pq : 0u);
+    feature_parts_kernel<<<(nparts + 63) / 64, 64, 0, s>>>(G, Lk, (int)p->renorm_every, T);
+    if (check_launch() != KL_OK) return KL_ECUDA;
+    features_kernel<<<grid_for(4ull * Lk.np, 128, 16), 128, 0, s>>>(Lk, T,
+                                                                    d_features + P.base[k] * 8);
+    if (check_launch() != KL_OK) return KL_ECUDA;
+  }
+  return KL_OK;
 }
 
 extern "C" size_t kl_lod_render_bytes(const kl_params* p, uint32_t lo, uint32_t hi) {
@@ -640,7 +690,7 @@ int render_lod_impl(const kl_params* p, uint32_t lo, uint32_t hi, const float* d
         counts + k + 1, deferred, counts + 32, d_image, cnt, stats);
     if (check_launch() != KL_OK) return KL_ECUDA;
   }
-  st = build_tables_forced(&q, L, V, G, T, s);
+  st = build_tables_forced(&q, L, V, G, T, s, deferred, counts + 32);
   if (st != KL_OK) return st;
   int sms = 0, occ = 0;
   if (device_slots((const void*)deferred_render_kernel<128>, 128, &sms, &occ) != KL_OK)

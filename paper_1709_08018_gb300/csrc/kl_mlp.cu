@@ -38,13 +38,22 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(const float* __restric
   }
 }
 
+// Gradients are summed in a fixed order, so that a training run repeats
+// bit for bit: every warp of mlp_backward_kernel and every block of
+// mlp_wgrad_kernel writes its partial sums to scratch, and mlp_reduce_kernel
+// adds them up in index order.  Per-warp partial of the backward pass:
+// db1 [64] | db2 [64] | dw3 [64] | db3 | loss.
+constexpr int kBwdPart = 3 * kHid + 2;
+constexpr int kWgPart = kHid * kHid + kIn * kHid;  // dW2 [64][64] | dW1 [8][64]
+constexpr int kBwdMaxBlocks = 512, kWgMaxBlocks = 256;
+
 // Forward + backward of 16-row tiles.  Per-parameter gradients of the
 // biases and w3, and the loss, are accumulated in registers over all tiles
 // of the warp and reduced once; the activations the weight gradients need
 // (H1, dH2 and dH1, BF16) go to scratch for mlp_wgrad_kernel.
 __global__ void __launch_bounds__(128) mlp_backward_kernel(
     const float* __restrict__ P, const float* __restrict__ x, const float* __restrict__ tgt,
-    uint64_t n, float under, float* __restrict__ grad, float* __restrict__ loss,
+    uint64_t n, float under, float* __restrict__ part,
     __nv_bfloat16* __restrict__ h1s, __nv_bfloat16* __restrict__ dh2s,
     __nv_bfloat16* __restrict__ dh1s) {
   __shared__ MlpSmem S;
@@ -138,21 +147,22 @@ __global__ void __launch_bounds__(128) mlp_backward_kernel(
     gb3 += __shfl_xor_sync(0xFFFFFFFFu, gb3, o);
     lsum += __shfl_xor_sync(0xFFFFFFFFu, lsum, o);
   }
+  float* out = part + (blockIdx.x * (size_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * kBwdPart;
   if (g == 0) {
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       const int j = 8 * t + 2 * c;
-      atomicAdd(grad + OFF_B1 + j, gb1[2 * t]);
-      atomicAdd(grad + OFF_B1 + j + 1, gb1[2 * t + 1]);
-      atomicAdd(grad + OFF_B2 + j, gb2[2 * t]);
-      atomicAdd(grad + OFF_B2 + j + 1, gb2[2 * t + 1]);
-      atomicAdd(grad + OFF_W3 + j, gw3[2 * t]);
-      atomicAdd(grad + OFF_W3 + j + 1, gw3[2 * t + 1]);
+      out[j] = gb1[2 * t];
+      out[j + 1] = gb1[2 * t + 1];
+      out[kHid + j] = gb2[2 * t];
+      out[kHid + j + 1] = gb2[2 * t + 1];
+      out[2 * kHid + j] = gw3[2 * t];
+      out[2 * kHid + j + 1] = gw3[2 * t + 1];
     }
   }
   if (lane == 0) {
-    atomicAdd(grad + OFF_B3, gb3);
-    atomicAdd(loss, lsum * inv_n);
+    out[3 * kHid] = gb3;
+    out[3 * kHid + 1] = lsum * inv_n;
   }
 }
 
@@ -170,11 +180,11 @@ __device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16* p, uint64_t str
 // Weight gradients, split over the batch: dW2 = H1^T dH2 (64x64) and
 // dW1 = X^T dH1 (8x64), K = the batch rows.  Block = 5 warps: warps 0..3 own
 // the 16-row m-tiles of dW2, warp 4 the (padded) m-tile of dW1; each block
-// takes one row range, accumulates in registers and adds its partial once.
+// takes one row range, accumulates in registers and writes its partial once.
 __global__ void __launch_bounds__(160) mlp_wgrad_kernel(
     const float* __restrict__ x, uint64_t n, const __nv_bfloat16* __restrict__ h1s,
     const __nv_bfloat16* __restrict__ dh2s, const __nv_bfloat16* __restrict__ dh1s,
-    uint64_t rows_per_block, float* __restrict__ grad) {
+    uint64_t rows_per_block, float* __restrict__ part) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
   const uint64_t r_begin = blockIdx.x * rows_per_block;
   const uint64_t r_end = min(n, r_begin + rows_per_block);
@@ -209,20 +219,50 @@ __global__ void __launch_bounds__(160) mlp_wgrad_kernel(
       mma_bf16(acc[t], a0, a1, a2, a3, b0, b1);
     }
   }
+  float* out = part + (size_t)blockIdx.x * kWgPart;
 #pragma unroll
   for (int t = 0; t < 8; ++t) {
     const int col = 8 * t + 2 * c;
     if (warp < 4) {
       const int m = 16 * warp + g;
-      atomicAdd(grad + OFF_W2 + m * kHid + col, acc[t][0]);
-      atomicAdd(grad + OFF_W2 + m * kHid + col + 1, acc[t][1]);
-      atomicAdd(grad + OFF_W2 + (m + 8) * kHid + col, acc[t][2]);
-      atomicAdd(grad + OFF_W2 + (m + 8) * kHid + col + 1, acc[t][3]);
+      out[m * kHid + col] = acc[t][0];
+      out[m * kHid + col + 1] = acc[t][1];
+      out[(m + 8) * kHid + col] = acc[t][2];
+      out[(m + 8) * kHid + col + 1] = acc[t][3];
     } else {
-      atomicAdd(grad + OFF_W1 + g * kHid + col, acc[t][0]);
-      atomicAdd(grad + OFF_W1 + g * kHid + col + 1, acc[t][1]);
+      out[kHid * kHid + g * kHid + col] = acc[t][0];
+      out[kHid * kHid + g * kHid + col + 1] = acc[t][1];
     }
   }
+}
+
+// grad[i] (and the loss) = the sum of the partials in block / warp order.
+__global__ void mlp_reduce_kernel(const float* __restrict__ bwd, int n_bwd,
+                                  const float* __restrict__ wg, int n_wg,
+                                  float* __restrict__ grad, float* __restrict__ loss) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > KL_MLP_NPARAMS) return;
+  const float* src;
+  int stride, count;
+  if (i == KL_MLP_NPARAMS) {                       // the loss
+    src = bwd + 3 * kHid + 1; stride = kBwdPart; count = n_bwd;
+  } else if (i < OFF_B1) {                         // W1
+    src = wg + kHid * kHid + i; stride = kWgPart; count = n_wg;
+  } else if (i < OFF_W2) {                         // b1
+    src = bwd + (i - OFF_B1); stride = kBwdPart; count = n_bwd;
+  } else if (i < OFF_B2) {                         // W2
+    src = wg + (i - OFF_W2); stride = kWgPart; count = n_wg;
+  } else if (i < OFF_W3) {                         // b2
+    src = bwd + kHid + (i - OFF_B2); stride = kBwdPart; count = n_bwd;
+  } else if (i < OFF_B3) {                         // w3
+    src = bwd + 2 * kHid + (i - OFF_W3); stride = kBwdPart; count = n_bwd;
+  } else {                                         // b3
+    src = bwd + 3 * kHid; stride = kBwdPart; count = n_bwd;
+  }
+  float acc = 0.0f;
+  for (int b = 0; b < count; ++b) acc += src[(size_t)b * stride];
+  if (i == KL_MLP_NPARAMS) *loss = acc;
+  else grad[i] = acc;
 }
 
 __global__ void adam_kernel(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
@@ -254,7 +294,9 @@ extern "C" int kl_mlp_forward(const float* d_params, const float* d_x, uint64_t 
 }
 
 extern "C" size_t kl_mlp_scratch_bytes(uint64_t n) {
-  return 3 * align256((size_t)n * kHid * sizeof(__nv_bfloat16));
+  return 3 * align256((size_t)n * kHid * sizeof(__nv_bfloat16)) +
+         align256((size_t)kBwdMaxBlocks * 4 * kBwdPart * sizeof(float)) +
+         align256((size_t)kWgMaxBlocks * kWgPart * sizeof(float));
 }
 
 extern "C" int kl_mlp_grad(const float* d_params, const float* d_x, const float* d_t, uint64_t n,
@@ -267,25 +309,30 @@ extern "C" int kl_mlp_grad(const float* d_params, const float* d_x, const float*
   cudaStream_t s = (cudaStream_t)stream;
   const int sms = sm_count();
   if (sms <= 0) return KL_ECUDA;
-  if (cudaMemsetAsync(d_grad, 0, KL_MLP_NPARAMS * sizeof(float), s) != cudaSuccess) return KL_ECUDA;
-  if (cudaMemsetAsync(d_loss, 0, sizeof(float), s) != cudaSuccess) return KL_ECUDA;
   const size_t part = align256((size_t)n * kHid * sizeof(__nv_bfloat16));
-  __nv_bfloat16* h1s = (__nv_bfloat16*)d_scratch;
-  __nv_bfloat16* dh2s = (__nv_bfloat16*)((char*)d_scratch + part);
-  __nv_bfloat16* dh1s = (__nv_bfloat16*)((char*)d_scratch + 2 * part);
+  char* base = (char*)d_scratch;
+  __nv_bfloat16* h1s = (__nv_bfloat16*)base;
+  __nv_bfloat16* dh2s = (__nv_bfloat16*)(base + part);
+  __nv_bfloat16* dh1s = (__nv_bfloat16*)(base + 2 * part);
+  float* bwd_part = (float*)(base + 3 * part);
+  float* wg_part =
+      (float*)(base + 3 * part + align256((size_t)kBwdMaxBlocks * 4 * kBwdPart * sizeof(float)));
+  // backward: 4 warps per block, 16-row tiles, at most 4 blocks per SM
   const uint64_t tiles = (n + 15) / 16, blocks = (tiles + 3) / 4;
-  const unsigned grid = (unsigned)(blocks < (uint64_t)sms * 4 ? blocks : (uint64_t)sms * 4);
-  mlp_backward_kernel<<<grid, 128, 0, s>>>(d_params, d_x, d_t, n, under_weight, d_grad, d_loss,
-                                           h1s, dh2s, dh1s);
+  uint64_t grid = blocks < (uint64_t)sms * 4 ? blocks : (uint64_t)sms * 4;
+  if (grid > (uint64_t)kBwdMaxBlocks) grid = kBwdMaxBlocks;
+  mlp_backward_kernel<<<(unsigned)grid, 128, 0, s>>>(d_params, d_x, d_t, n, under_weight,
+                                                     bwd_part, h1s, dh2s, dh1s);
   if (check_launch() != KL_OK) return KL_ECUDA;
-  uint64_t rows_per_block = 1024;
-  uint64_t wblocks = (n + rows_per_block - 1) / rows_per_block;
-  if (wblocks > (uint64_t)sms * 4) {
-    rows_per_block = ((n + sms * 4 - 1) / (sms * 4) + 15) / 16 * 16;
-    wblocks = (n + rows_per_block - 1) / rows_per_block;
-  }
+  // weight gradients: row ranges of at least 64 rows, at most kWgMaxBlocks of them
+  uint64_t rows_per_block = (n + kWgMaxBlocks - 1) / kWgMaxBlocks;
+  rows_per_block = rows_per_block < 64 ? 64 : (rows_per_block + 15) / 16 * 16;
+  const uint64_t wblocks = (n + rows_per_block - 1) / rows_per_block;
   mlp_wgrad_kernel<<<(unsigned)wblocks, 160, 0, s>>>(d_x, n, h1s, dh2s, dh1s, rows_per_block,
-                                                     d_grad);
+                                                     wg_part);
+  if (check_launch() != KL_OK) return KL_ECUDA;
+  mlp_reduce_kernel<<<(KL_MLP_NPARAMS + 1 + 127) / 128, 128, 0, s>>>(
+      bwd_part, (int)grid * 4, wg_part, (int)wblocks, d_grad, d_loss);
   return check_launch();
 }
 

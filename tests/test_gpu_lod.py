@@ -138,6 +138,52 @@ def test_labels_recursion_and_oracle(kl):
     assert agree >= 0.995 * nh, (agree, nh)
 
 
+def node_letters(k, slot):
+    """w_1 .. w_k of level-k node `slot` (x = w_k, ranks of w_{k-1} .. w_1)."""
+    nk = 3 ** (k - 1)
+    x, r = slot // nk, slot % nk
+    digits = []
+    for _ in range(k - 1):
+        digits.append(r % 3)
+        r //= 3
+    letters = [x]
+    for dg in digits[::-1]:
+        ban = (letters[-1] + 2) % 4
+        letters.append([y for y in range(4) if y != ban][dg])
+    return letters[::-1]
+
+
+def test_features_against_oracle(kl):
+    """Features of sampled nodes of every level: the product of the oracle's
+    generator matrices over the node's letters, divided by the principal root
+    of its determinant, sign-canonicalised (Re tr > 0), then sign(v) log1p|v|."""
+    group = klsynth.draw_groups(1710, 3)[2][0]
+    d, lo, hi = 14, 3, 10
+    p = group_params(kl, group, d, 512)
+    _, _, feats, _ = kl.lod_labels(p, lo, hi)
+    feats = feats.cpu().numpy()
+    g, _ = oracle.group(group.ta, group.tb)
+    M = oracle.as_matrices(g)
+    rng = np.random.default_rng(7)
+    base = 0
+    for k in range(lo, hi + 1):
+        n = 4 * 3 ** (k - 1)
+        for slot in sorted(set(rng.integers(0, n, 64).tolist()) | {0, n - 1}):
+            P = np.eye(2, dtype=complex)
+            for w in node_letters(k, slot):
+                P = P @ M[w]
+            P = P / np.sqrt(np.linalg.det(P))
+            v = np.array([P[0, 0].real, P[0, 0].imag, P[0, 1].real, P[0, 1].imag,
+                          P[1, 0].real, P[1, 0].imag, P[1, 1].real, P[1, 1].imag])
+            if v[0] + v[6] < 0:
+                v = -v
+            want = np.sign(v) * np.log1p(np.abs(v))
+            np.testing.assert_allclose(feats[base + slot], want, rtol=1e-5, atol=1e-5,
+                                       err_msg=f"level {k} slot {slot}")
+        base += n
+    assert base == feats.shape[0]
+
+
 def test_trained_network_gain(kl):
     from paper_1709_08018_gb300 import lod
     d, lo, hi, size, extent = 22, 8, 15, 8192, 1.0 / 32

@@ -90,3 +90,20 @@ def test_training_reduces_loss(kl):
     # the loss value reported by the last step is that of the parameters before it
     final = mlp.loss_and_grad(params.double().cpu().numpy(), x, t)[0]
     assert final < 0.1 * first, (first, loss, final)
+
+
+def test_training_is_deterministic(kl):
+    """Gradients are summed in a fixed order: two runs from the same start on
+    the same batches give bit-identical losses and parameters."""
+    import torch
+    p, x, t = setup(20000, 11)
+    X = torch.tensor(x, dtype=torch.float32, device="cuda")
+    T = torch.tensor(t, dtype=torch.float32, device="cuda")
+    runs = []
+    for _ in range(2):
+        params = torch.tensor(p * 0.5, dtype=torch.float32, device="cuda")
+        tr = kl.MlpTrainer(params, lr=3e-3, under_weight=4.0)
+        losses = [float(tr.step(X, T).item()) for _ in range(20)]
+        runs.append((losses, params.cpu().numpy().copy()))
+    assert runs[0][0] == runs[1][0]
+    assert np.array_equal(runs[0][1], runs[1][1])
