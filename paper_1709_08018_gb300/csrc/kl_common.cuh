@@ -313,8 +313,9 @@ __device__ __forceinline__ void decode_word(uint64_t i, int d, int* w) {
 //      time, slot (z = w_{p+so+1}, ranks).
 // The combine pass then forms every prefix matrix P = H L (one 2x2 product)
 // and its pole-form constants, and every suffix point v = So(Si) (one map).
-// Each L, H and So matrix is renormalised to det 1 every `renorm` letters and
-// at its end; P is not renormalised (its determinant enters beta explicitly).
+// Each L, H and So matrix is renormalised to det 1 after every `renorm`
+// letters (a shorter product of det-1 generators has det 1 up to rounding);
+// P is not renormalised (its determinant enters beta explicitly).
 // The slot numbering is the same as for a single-level decode: a prefix slot
 // (x, r) has r = r_L 3^(p-q) + r_H, a suffix slot (u, j) has
 // j = j_So 3^si + rank(z) 3^(si-1) + j_Si.
@@ -351,7 +352,6 @@ __device__ void part_entry(const Group& G, const Plan& L, int renorm, uint32_t i
       right = w;
       if (renorm > 0 && (++used % renorm) == 0) renormalise(P);
     }
-    if (renorm > 0 && (used % renorm) != 0) renormalise(P);
     if (tail) {
       PartM e;
       e.m = P;
@@ -377,7 +377,6 @@ __device__ void part_entry(const Group& G, const Plan& L, int renorm, uint32_t i
       left = w;
       if (renorm > 0 && (++used % renorm) == 0) renormalise(S);
     }
-    if (renorm > 0 && (used % renorm) != 0) renormalise(S);
     PartM e;
     e.m = S;
     e.edge = left;
@@ -544,6 +543,38 @@ __device__ __forceinline__ void publish_counts(uint32_t in_window, uint32_t word
     if (c) atomicAdd(counters + KL_CNT_FP64_WORDS, c);
     if (e) atomicAdd(counters + KL_CNT_ATOMICS, e);
   }
+}
+
+// Programmatic dependent launch: a kernel launched with launch_dependent may
+// start while the kernel before it in the stream is still running; pdl_wait
+// blocks until that kernel has completed and its writes are visible, and
+// must come before any read of them.  pdl_trigger lets the next dependent
+// launch start early.  Launched the ordinary way, both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Image clearing carried by another launch: `words` uint32 at `img` (none if
+// 0), and the counters (if not null).
+struct Clear {
+  uint32_t* img = nullptr;
+  size_t words = 0;
+  unsigned long long* counters = nullptr;
+};
+
+// Zero words [0, n) of p (4-byte aligned) with 16-byte stores; thread t of
+// `threads` takes every threads-th vector.
+__device__ __forceinline__ void clear_words(uint32_t* p, size_t n, size_t t, size_t threads) {
+  const size_t head = (((16u - ((uintptr_t)p & 15u)) & 15u) / 4u) < n
+                          ? ((16u - ((uintptr_t)p & 15u)) & 15u) / 4u
+                          : n;
+  if (t < head) p[t] = 0u;
+  uint4* v = reinterpret_cast<uint4*>(p + head);
+  const size_t nv = (n - head) / 4;
+  for (size_t i = t; i < nv; i += threads) v[i] = make_uint4(0u, 0u, 0u, 0u);
+  const size_t tail = head + 4 * nv;
+  if (tail + t < n) p[tail + t] = 0u;
 }
 
 // Per-warp queue: lane 0 takes the next item and broadcasts it (no block
@@ -770,6 +801,25 @@ __device__ __forceinline__ void mixed_item(uint32_t item, const Work& Wk, const 
 
 // ---------------------------------------------------------------------------
 // host helpers
+
+// Launch `k` as a programmatic dependent of the previous kernel in stream s
+// (it must call pdl_wait before reading that kernel's output).
+template <typename... Params, typename... Args>
+int launch_dependent(void (*k)(Params...), dim3 grid, dim3 block, cudaStream_t s,
+                     Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, k, static_cast<Args&&>(args)...) != cudaSuccess) return KL_ECUDA;
+  return KL_OK;
+}
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 

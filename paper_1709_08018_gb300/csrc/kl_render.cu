@@ -9,14 +9,38 @@ namespace {
 // ---------------------------------------------------------------------------
 // table passes
 
-__global__ void parts_kernel(Group G, Plan L, int renorm, Tables T) {
-  const uint32_t total = parts_count(L);
-  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += gridDim.x * blockDim.x)
-    part_entry(G, L, renorm, idx, T);
+constexpr uint32_t kPartLanes = 8;
+
+// The first launch of a render.  Blocks [0, part_blocks) build the parts
+// tables (and block 0 resets the fallback count, the work queue and the
+// counters); the blocks after them clear the image.  The parts work is a few
+// thousand short FP64 chains, far from filling the GPU, so the clearing runs
+// beside it and a render needs no separate memset.
+__global__ void parts_kernel(Group G, Plan L, int renorm, Tables T, Clear C,
+                             uint32_t part_blocks) {
+  pdl_trigger();
+  if (blockIdx.x < part_blocks) {
+    if (blockIdx.x == 0) {
+      if (threadIdx.x < 2) T.fbcount[threadIdx.x] = 0u;
+      if (C.counters && threadIdx.x < KL_N_COUNTERS) C.counters[threadIdx.x] = 0ull;
+    }
+    // kPartLanes entries per block: each entry is one long chain of dependent
+    // FP64 operations, so spreading the entries over more SMs shortens the
+    // launch more than filling warps does
+    const uint32_t total = parts_count(L);
+    if (threadIdx.x < kPartLanes)
+      for (uint32_t idx = blockIdx.x * kPartLanes + threadIdx.x; idx < total;
+           idx += part_blocks * kPartLanes)
+        part_entry(G, L, renorm, idx, T);
+    return;
+  }
+  clear_words(C.img, C.words, (size_t)(blockIdx.x - part_blocks) * blockDim.x + threadIdx.x,
+              (size_t)(gridDim.x - part_blocks) * blockDim.x);
 }
 
 __global__ void combine_kernel(View V, Plan L, double ptol, int mixed, Tables T) {
+  pdl_trigger();
+  pdl_wait();
   const uint32_t total = combine_count(L);
   for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += gridDim.x * blockDim.x)
@@ -33,6 +57,7 @@ template <int BT>
 __global__ void __launch_bounds__(BT) render64_kernel(Tables T, Plan L, View V, Work Wk,
                                                       uint32_t* __restrict__ img,
                                                       unsigned long long* counters) {
+  pdl_wait();
   Tally t;
   uint32_t words = 0;
   for (;;) {
@@ -52,6 +77,7 @@ template <int BT>
 __global__ void __launch_bounds__(BT, 1536 / BT) render_mixed_kernel(
     Tables T, Plan L, View V, Work Wk, uint32_t* __restrict__ img,
     unsigned long long* counters) {
+  pdl_wait();
   const uint32_t chunks = (L.ns + kFbChunk - 1) / kFbChunk;
   const uint32_t fb_units = 3u * chunks * (*T.fbcount);
   const uint32_t n64 = (fb_units + 31) / 32;
@@ -174,16 +200,26 @@ int prof_mark(cudaEvent_t e, cudaStream_t s) {
   return cudaEventRecord(e, s) == cudaSuccess ? KL_OK : KL_ECUDA;
 }
 
+// Tables of a render: parts (with the image clearing of C riding along),
+// then combine, launched as a programmatic dependent of parts.
 int build_tables(const kl_params* p, const Plan& L, const View& V, const Group& G,
-                 const Tables& T, cudaStream_t st) {
+                 const Tables& T, cudaStream_t st, const Clear& C = Clear{}) {
   const int mixed = p->precision == KL_MIXED;
-  if (cudaMemsetAsync(T.fbcount, 0, 2 * sizeof(uint32_t), st) != cudaSuccess) return KL_ECUDA;
   const uint32_t nParts = parts_count(L);
-  parts_kernel<<<(nParts + 31) / 32, 32, 0, st>>>(G, L, (int)p->renorm_every, T);
+  const uint32_t part_blocks = (nParts + kPartLanes - 1) / kPartLanes;
+  uint32_t clear_blocks = 0;
+  if (C.words) {
+    const int sms = sm_count();
+    if (sms <= 0) return KL_ECUDA;
+    const size_t need = (C.words / 4 + 31) / 32;  // 16-byte stores, 32-thread blocks
+    clear_blocks = (uint32_t)(need < (size_t)sms * 8 ? (need > 0 ? need : 1) : (size_t)sms * 8);
+  }
+  parts_kernel<<<part_blocks + clear_blocks, 32, 0, st>>>(G, L, (int)p->renorm_every, T, C,
+                                                          part_blocks);
   if (check_launch() != KL_OK) return KL_ECUDA;
   const uint32_t n = combine_count(L);
-  combine_kernel<<<(n + 127) / 128, 128, 0, st>>>(V, L, p->parabolic_tol, mixed, T);
-  return check_launch();
+  return launch_dependent(combine_kernel, dim3((n + 127) / 128), dim3(128), st, V, L,
+                          p->parabolic_tol, mixed, T);
 }
 
 int validate(const kl_params* p, size_t ws_bytes, void* ws, Plan* L) {
@@ -208,8 +244,9 @@ int launch_render(const kl_params* p, const Plan& L, const View& V, const Tables
     if (device_slots((const void*)render64_kernel<BT>, BT, &sms, &occ) != KL_OK) return KL_ECUDA;
     const Work Wk = make_work(L, BT, L.ns, sms * occ, 2u * p->chunk_pairs);
     if (prof_mark(g_prof_start, s) != KL_OK) return KL_ECUDA;
-    render64_kernel<BT><<<sms * occ, BT, 0, s>>>(T, L, V, Wk, img, cnt);
-    if (check_launch() != KL_OK) return KL_ECUDA;
+    if (launch_dependent(render64_kernel<BT>, dim3(sms * occ), dim3(BT), s, T, L, V, Wk, img,
+                         cnt) != KL_OK)
+      return KL_ECUDA;
     return prof_mark(g_prof_stop, s);
   }
   if (device_slots((const void*)render_mixed_kernel<BT>, BT, &sms, &occ) != KL_OK)
@@ -217,8 +254,9 @@ int launch_render(const kl_params* p, const Plan& L, const View& V, const Tables
   // warp-sized items (32 prefixes), about 12 per resident warp
   const Work Wk = make_work(L, 32, L.npairs, sms * occ * (BT / 32), p->chunk_pairs);
   if (prof_mark(g_prof_start, s) != KL_OK) return KL_ECUDA;
-  render_mixed_kernel<BT><<<sms * occ, BT, 0, s>>>(T, L, V, Wk, img, cnt);
-  if (check_launch() != KL_OK) return KL_ECUDA;
+  if (launch_dependent(render_mixed_kernel<BT>, dim3(sms * occ), dim3(BT), s, T, L, V, Wk, img,
+                       cnt) != KL_OK)
+    return KL_ECUDA;
   return prof_mark(g_prof_stop, s);
 }
 
@@ -282,21 +320,23 @@ extern "C" int kl_render(const kl_params* p, uint32_t* d_image, uint64_t* d_coun
   if (!d_image) return KL_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned long long* cnt = (unsigned long long*)d_counters;
-  if (!p->accumulate) {
-    if (cudaMemsetAsync(d_image, 0, (size_t)p->width * p->height * sizeof(uint32_t), s) !=
-        cudaSuccess)
-      return KL_ECUDA;
-    if (cnt && cudaMemsetAsync(cnt, 0, KL_N_COUNTERS * sizeof(uint64_t), s) != cudaSuccess)
-      return KL_ECUDA;
-  }
   const View V = make_view(p);
   const Group G = make_group(p);
   if (L.d == 1) {
+    if (!p->accumulate) {
+      if (cudaMemsetAsync(d_image, 0, (size_t)p->width * p->height * sizeof(uint32_t), s) !=
+          cudaSuccess)
+        return KL_ECUDA;
+      if (cnt && cudaMemsetAsync(cnt, 0, KL_N_COUNTERS * sizeof(uint64_t), s) != cudaSuccess)
+        return KL_ECUDA;
+    }
     render_single_letter_kernel<<<1, 32, 0, s>>>(G, V, d_image, cnt);
     return check_launch();
   }
   const Tables T = carve(L, d_workspace);
-  st = build_tables(p, L, V, G, T, s);
+  Clear C{};
+  if (!p->accumulate) C = {d_image, (size_t)p->width * p->height, cnt};
+  st = build_tables(p, L, V, G, T, s, C);
   if (st != KL_OK) return st;
   switch (p->block_threads) {
     case 64: return launch_render<64>(p, L, V, T, d_image, cnt, s);
