@@ -132,11 +132,15 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+RENDER_SOURCES = ("paper_1709_08018_gb300/csrc/kl_common.cuh",
+                  "paper_1709_08018_gb300/csrc/kl_render.cu", "include/kl.h")
+
+
 def source_hash():
+    """Hash of the sources the single-render kernels are built from."""
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1709_08018_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, f), "rb") as fh:
+    for f in RENDER_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 

@@ -81,7 +81,19 @@ __device__ M2 node_matrix(const Group& G, int k, uint32_t slot, uint32_t nk) {
 // Re tr > 0 (a zero trace takes the sign of the first nonzero entry), then
 // sign(v) log(1 + |v|) for each real part and imaginary part.
 __device__ void node_features(M2 P, float* f) {
-  renormalise(P);
+  // P / k with k the principal square root of d = det P: |k|^2 = |d|, so
+  // 1 / k = conj(k) / |d| (two square roots and two refined reciprocals;
+  // |d| is near 1 for these products, so no scaling against overflow)
+  const dc d = mdet(P);
+  const double r = sqrt(d.re * d.re + d.im * d.im);
+  if (r > 0.0) {
+    const double t = sqrt(0.5 * (r + fabs(d.re)));
+    const double h = 0.5 * rcp64(t);
+    const dc k = d.re >= 0.0 ? dc{t, d.im * h} : dc{fabs(d.im) * h, copysign(t, d.im)};
+    const double ir = rcp64(r);
+    const dc ik = {k.re * ir, -k.im * ir};
+    P.p = cmul(P.p, ik); P.q = cmul(P.q, ik); P.r = cmul(P.r, ik); P.s = cmul(P.s, ik);
+  }
   double v[8];
   from_m2(P, v);
   double lead = v[0] + v[6];

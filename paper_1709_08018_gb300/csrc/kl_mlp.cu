@@ -39,9 +39,9 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(const float* __restric
 }
 
 // Gradients are summed in a fixed order, so that a training run repeats
-// bit for bit: every warp of mlp_backward_kernel and every block of
-// mlp_wgrad_kernel writes its partial sums to scratch, and mlp_reduce_kernel
-// adds them up in index order.  Per-warp partial of the backward pass:
+// bit for bit: every block of mlp_backward_kernel and of mlp_wgrad_kernel
+// writes its partial sums to scratch, and mlp_reduce_kernel adds them up in a
+// fixed order.  Per-block partial of the backward pass:
 // db1 [64] | db2 [64] | dw3 [64] | db3 | loss.
 constexpr int kBwdPart = 3 * kHid + 2;
 constexpr int kWgPart = kHid * kHid + kIn * kHid;  // dW2 [64][64] | dW1 [8][64]
@@ -147,7 +147,9 @@ __global__ void __launch_bounds__(128) mlp_backward_kernel(
     gb3 += __shfl_xor_sync(0xFFFFFFFFu, gb3, o);
     lsum += __shfl_xor_sync(0xFFFFFFFFu, lsum, o);
   }
-  float* out = part + (blockIdx.x * (size_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * kBwdPart;
+  // the block's four warp partials, added in warp order: one partial per block
+  __shared__ float wp[4][kBwdPart];
+  float* out = wp[threadIdx.x >> 5];
   if (g == 0) {
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
@@ -164,6 +166,9 @@ __global__ void __launch_bounds__(128) mlp_backward_kernel(
     out[3 * kHid] = gb3;
     out[3 * kHid + 1] = lsum * inv_n;
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kBwdPart; i += blockDim.x)
+    part[(size_t)blockIdx.x * kBwdPart + i] = ((wp[0][i] + wp[1][i]) + wp[2][i]) + wp[3][i];
 }
 
 __device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16* p, uint64_t stride, uint64_t n,
@@ -236,12 +241,14 @@ __global__ void __launch_bounds__(160) mlp_wgrad_kernel(
   }
 }
 
-// grad[i] (and the loss) = the sum of the partials in block / warp order.
-__global__ void mlp_reduce_kernel(const float* __restrict__ bwd, int n_bwd,
-                                  const float* __restrict__ wg, int n_wg,
-                                  float* __restrict__ grad, float* __restrict__ loss) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i > KL_MLP_NPARAMS) return;
+// grad[i] (and, for i = KL_MLP_NPARAMS, the loss) = the sum of the partials
+// of output i: one block per output, thread t takes partials t, t + 128, ...
+// in order, then a fixed reduction tree.
+__global__ void __launch_bounds__(128) mlp_reduce_kernel(const float* __restrict__ bwd, int n_bwd,
+                                                         const float* __restrict__ wg, int n_wg,
+                                                         float* __restrict__ grad,
+                                                         float* __restrict__ loss) {
+  const int i = blockIdx.x;
   const float* src;
   int stride, count;
   if (i == KL_MLP_NPARAMS) {                       // the loss
@@ -260,9 +267,16 @@ __global__ void mlp_reduce_kernel(const float* __restrict__ bwd, int n_bwd,
     src = bwd + 3 * kHid; stride = kBwdPart; count = n_bwd;
   }
   float acc = 0.0f;
-  for (int b = 0; b < count; ++b) acc += src[(size_t)b * stride];
-  if (i == KL_MLP_NPARAMS) *loss = acc;
-  else grad[i] = acc;
+  for (int b = threadIdx.x; b < count; b += blockDim.x) acc += src[(size_t)b * stride];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+  __shared__ float ws[4];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const float v = (ws[0] + ws[1]) + (ws[2] + ws[3]);
+    if (i == KL_MLP_NPARAMS) *loss = v;
+    else grad[i] = v;
+  }
 }
 
 __global__ void adam_kernel(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
@@ -295,7 +309,7 @@ extern "C" int kl_mlp_forward(const float* d_params, const float* d_x, uint64_t 
 
 extern "C" size_t kl_mlp_scratch_bytes(uint64_t n) {
   return 3 * align256((size_t)n * kHid * sizeof(__nv_bfloat16)) +
-         align256((size_t)kBwdMaxBlocks * 4 * kBwdPart * sizeof(float)) +
+         align256((size_t)kBwdMaxBlocks * kBwdPart * sizeof(float)) +
          align256((size_t)kWgMaxBlocks * kWgPart * sizeof(float));
 }
 
@@ -316,7 +330,7 @@ extern "C" int kl_mlp_grad(const float* d_params, const float* d_x, const float*
   __nv_bfloat16* dh1s = (__nv_bfloat16*)(base + 2 * part);
   float* bwd_part = (float*)(base + 3 * part);
   float* wg_part =
-      (float*)(base + 3 * part + align256((size_t)kBwdMaxBlocks * 4 * kBwdPart * sizeof(float)));
+      (float*)(base + 3 * part + align256((size_t)kBwdMaxBlocks * kBwdPart * sizeof(float)));
   // backward: 4 warps per block, 16-row tiles, at most 4 blocks per SM
   const uint64_t tiles = (n + 15) / 16, blocks = (tiles + 3) / 4;
   uint64_t grid = blocks < (uint64_t)sms * 4 ? blocks : (uint64_t)sms * 4;
@@ -331,8 +345,8 @@ extern "C" int kl_mlp_grad(const float* d_params, const float* d_x, const float*
   mlp_wgrad_kernel<<<(unsigned)wblocks, 160, 0, s>>>(d_x, n, h1s, dh2s, dh1s, rows_per_block,
                                                      wg_part);
   if (check_launch() != KL_OK) return KL_ECUDA;
-  mlp_reduce_kernel<<<(KL_MLP_NPARAMS + 1 + 127) / 128, 128, 0, s>>>(
-      bwd_part, (int)grid * 4, wg_part, (int)wblocks, d_grad, d_loss);
+  mlp_reduce_kernel<<<KL_MLP_NPARAMS + 1, 128, 0, s>>>(bwd_part, (int)grid, wg_part,
+                                                       (int)wblocks, d_grad, d_loss);
   return check_launch();
 }
 
