@@ -313,6 +313,36 @@ def lod_config(kl, n_train: int = 64, n_test: int = 16, n_valid: int = 8):
     return s
 
 
+def make_barrier(world: int):
+    """A barrier over all ranks (a no-op for one process)."""
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+    return barrier
+
+
+def make_max_over_ranks(world: int, device):
+    """x -> the maximum of x over all ranks (all_reduce MAX on `device`)."""
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return max_over_ranks
+
+
+def job_rate(world: int, words_per_step: int, steps: int, local_ms: float, max_over_ranks):
+    """Whole-job throughput of `world` replicas: every rank renders
+    words_per_step words per step; the job's time is the slowest rank's.
+    Returns (words/s over all ranks, job milliseconds)."""
+    total_ms = max_over_ranks(local_ms)
+    return world * words_per_step * steps / (total_ms / 1000.0), total_ms
+
+
 def run_ours(args):
     import torch
     import paper_1709_08018_gb300 as kl
@@ -326,18 +356,8 @@ def run_ours(args):
     cfg, config = workload()
     N = cfg.n_words
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier = make_barrier(world)
+    max_over_ranks = make_max_over_ranks(world, dev)
 
     p = kl.params_init(cfg.group.ta, cfg.group.tb, cfg.depth, cfg.width, cfg.height,
                        cfg.window, kl.MIXED)
@@ -374,8 +394,7 @@ def run_ours(args):
     clocks = sampler.summary()
     step_ms = [st0[k].elapsed_time(st1[k]) for k in range(K)]
     kern_ms = [kn0[k].elapsed_time(kn1[k]) for k in range(K)]
-    total_ms = max_over_ranks(sum(step_ms))
-    value = world * N * K / (total_ms / 1000.0)
+    value, total_ms = job_rate(world, N, K, sum(step_ms), max_over_ranks)
     cnt = r.counters.cpu().tolist()
     fp64_words = int(cnt[2])
 
@@ -415,8 +434,8 @@ def run_ours(args):
         host_cnt.copy_(r.counters, non_blocking=True)
         e1[k].record(stream)
     torch.cuda.synchronize(dev)
-    e2e_ms = max_over_ranks(sum(e0[k].elapsed_time(e1[k]) for k in range(KE)))
-    e2e_value = world * N * KE / (e2e_ms / 1000.0)
+    e2e_value, e2e_ms = job_rate(world, N, KE, sum(e0[k].elapsed_time(e1[k]) for k in range(KE)),
+                                 max_over_ranks)
 
     pk = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
