@@ -714,8 +714,9 @@ __device__ __noinline__ UnitTally fallback_unit(const Pre64* __restrict__ pre,
 // out-of-window and non-finite words alike.  Within one prefix kx and ky are
 // fixed, so two words share a pixel exactly when their t bits agree: the
 // current run keeps its pixel's (t_u, t_u) and (t_v, t_v) bit pairs, and a
-// pair of words that both fall in that pixel is settled by two 64-bit compares
-// and one add, without forming pixel ids.
+// pair of words that both fall in that pixel is settled by two 64-bit compares,
+// without forming pixel ids; the run's length is taken from the pair index
+// when the run ends.
 // Mixed words of prefix slot `slot` on suffix point pairs [k0, k1) of first
 // letter u (see the comment above for the pixel arithmetic).
 template <bool BBOX = false>
@@ -735,7 +736,8 @@ __device__ __forceinline__ void mixed_slot_words(uint32_t slot, int u, uint32_t 
   // t bits of the current run's pixel, doubled; 0 (never a t value) = no
   // in-window run.  Runs start afresh for every prefix (t.flush below).
   f2 CU = 0, CV = 0;
-#pragma unroll 2
+  uint32_t e_run = k0;  // pairs [e_run, e) took the fast path into the current run
+#pragma unroll 4
   for (uint32_t e = k0; e < k1; ++e) {
     const float4 s = __ldg(src + e);
     const f2 wr = add2(pk(s.x, s.y), GR);
@@ -748,9 +750,9 @@ __device__ __forceinline__ void mixed_slot_words(uint32_t slot, int u, uint32_t 
     const f2 ty = fma2(C3, wr, mul2(C4, wi));
     const f2 TU = add2_rm(fma2(tx, rr, AX), magic);
     const f2 TV = add2_rm(fma2(ty, rr, AY), magic);
-    if ((TU == CU) & (TV == CV)) {
-      t.run += 2;
-    } else {
+    if (!((TU == CU) & (TV == CV))) {
+      t.run += 2u * (e - e_run);
+      e_run = e + 1;
       float tua, tub, tva, tvb;
       upk(TU, tua, tub);
       upk(TV, tva, tvb);
@@ -777,6 +779,7 @@ __device__ __forceinline__ void mixed_slot_words(uint32_t slot, int u, uint32_t 
       }
     }
   }
+  t.run += 2u * (k1 - e_run);
   words += min(2u * k1, L.ns) - 2u * k0;
   t.flush(img);
   if (BBOX) box_merge(*B, slot, bc0, bc1, br0, br1);
