@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-lod", action="store_true")
+    ap.add_argument("--no-tiling", action="store_true")
     return ap.parse_args()
 
 
@@ -230,6 +231,37 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "words/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def tiling_config(kl, dev, steps: int, flush):
+    """Tiling mode of the bench group: every node of the word tree, all
+    lengths 1..18 (2 (3^18 - 1) = 774,840,976 words), mixed, 4096^2; one
+    kl_render call per step, L2 flushed between steps."""
+    import torch
+    cfg = klsynth.C2
+    p = kl.params_init(cfg.group.ta, cfg.group.tb, cfg.depth, cfg.width, cfg.height, cfg.window,
+                       kl.MIXED, mode=kl.TILING)
+    r = kl.Renderer(p, device=dev)
+    for _ in range(3):
+        r()
+    K = max(3, min(steps, 20))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    torch.cuda.synchronize(dev)
+    for k in range(K):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record()
+        r()
+        ev[k][1].record()
+    torch.cuda.synchronize(dev)
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    words = 2 * (3 ** cfg.depth - 1)
+    cnt = r.counters.cpu().tolist()
+    assert int(cnt[0]) + int(cnt[1]) == words
+    return {"workload": "tiling mode: every node of the word tree of the gasket ta=tb=2, "
+                        "lengths 1..18, 4096x4096 uint32, window [-1.5,1.5]^2, mixed",
+            "words_per_step": words, "ms_per_step": ms, "words_per_s": words / (ms / 1000.0),
+            "steps": K, "fp64_words": int(cnt[2])}
 
 
 def batch_sweep(kl, dev, steps: int):
@@ -471,6 +503,8 @@ def run_ours(args):
                          "fp64_words": fp64_words, "atomics": int(cnt[3])},
             "plain_fp64": plain,
             "speedup_mixed_over_fp64": fp64_step_ms / (total_ms / K)}
+    if not args.no_tiling:
+        line["tiling"] = tiling_config(kl, dev, K, flush)
     if not args.no_batch:
         line["batch_sweep"] = batch_sweep(kl, dev, K)
     if not args.no_lod:

@@ -65,6 +65,13 @@ typedef enum {
                     FP64; the per-word map in FP32 in a per-prefix local frame */
 } kl_precision;
 
+/* Which words a render draws (Sec. "Implementation": the two drawing modes). */
+typedef enum {
+  KL_LIMIT_SET = 0,  /* the words of length exactly d: N_d = 4 3^(d-1) */
+  KL_TILING = 1      /* every node of the word tree: all lengths 1 .. d,
+                        sum_k N_k = 2 (3^d - 1) words, each drawn at its own value */
+} kl_mode;
+
 #define KL_MAX_DEPTH 40          /* N_40 = 4 * 3^39 < 2^64 */
 #define KL_MAX_IMAGE_SIDE 65536  /* width and height limit */
 
@@ -93,6 +100,9 @@ typedef struct {
                               (0 = 128); a tuning knob, results do not depend on it */
   uint32_t chunk_pairs;    /* suffix-point pairs per work item (FP64: twice as many points);
                               0 = choose; a tuning knob, results do not depend on it */
+  uint32_t mode;           /* kl_mode: KL_LIMIT_SET (default) or KL_TILING; kl_render and
+                              kl_render_noalloc only (the batch and level-of-detail calls
+                              take KL_LIMIT_SET; kl_eval_words evaluates length-d words) */
 } kl_params;
 
 /* Counters written by kl_render (uint64 each). */
@@ -144,7 +154,8 @@ KL_API int kl_decode_words(uint32_t depth, const uint64_t* d_index, uint64_t n, 
                     void* stream);
 
 /* Bytes of device workspace kl_render and kl_eval_words need for *p
- * (prefix-matrix and suffix-point tables).  0 on invalid parameters. */
+ * (prefix-matrix and suffix-point tables; in KL_TILING mode the largest
+ * over the lengths 1 .. d).  0 on invalid parameters. */
 KL_API size_t kl_workspace_bytes(const kl_params* p);
 
 /* Word values, computed with exactly the arithmetic kl_render uses for *p (its
@@ -159,7 +170,10 @@ KL_API int kl_eval_words(const kl_params* p, const uint64_t* d_index, uint64_t n
 
 /* Render: every reduced word of length p->depth is decoded from its index,
  * evaluated and counted into the pixel it falls in (Sec. "Implementation",
- * "limit set" mode: words of length exactly d).  d_image: width*height uint32,
+ * "limit set" mode: words of length exactly d).  In KL_TILING mode the words
+ * of every length 1 .. d are drawn, each length as a render of its own into
+ * the same image and counters (the prefix length field applies to length d;
+ * shorter lengths choose their own).  d_image: width*height uint32,
  * row-major, row 0 at y1; counts wrap modulo 2^32.  d_counters: KL_N_COUNTERS
  * uint64 (may be NULL).  Unless p->accumulate, the image and counters are
  * zeroed first (on `stream`).  d_workspace as for kl_eval_words.  Words whose

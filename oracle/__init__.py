@@ -13,6 +13,8 @@ Parity status per function (what pins it is in ``tests/test_oracle_pins.py``):
   eval           pinned: the paper's abA orbit order, independent matrix
                  products, the Fuchsian circle, tree walk = per-word bitwise
   render         pinned: brute-force render from the scan, hit conservation
+  render_tiling  pinned: brute-force scan over every length 1 .. d, the node
+                 count 2 (3^d - 1)
   mlp (numpy)    pinned: central finite differences, closed-form tiny nets
 """
 from .oracle import *  # noqa: F401,F403

@@ -124,6 +124,24 @@ class Render:
     edge_total: int          # edge words found (may exceed the stored k)
 
 
+def render_tiling(gens, seeds8, d: int, window: Sequence[float], width: int, height: int,
+                  mode: str = "tree", threads: Optional[int] = None, eta: float = 0.0,
+                  edge_cap: int = 1 << 16) -> Render:
+    """Tiling mode (Sec. "Implementation", the second drawing mode): every node
+    of the word tree drawn at its own value, i.e. the words of every length
+    1 .. d; the sum of the renders of each length (edge words of all lengths
+    logged together, their indices relative to their own length)."""
+    parts = [render(gens, seeds8, k, window, width, height, mode=mode, threads=threads, eta=eta,
+                    edge_cap=edge_cap) for k in range(1, d + 1)]
+    img = np.zeros((height, width), dtype=np.uint32)
+    for r in parts:
+        img += r.image
+    return Render(img, sum(r.in_window for r in parts), sum(r.dropped for r in parts),
+                  np.concatenate([r.edge_idx for r in parts]),
+                  np.concatenate([r.edge_uv for r in parts]).reshape(-1, 2),
+                  sum(r.edge_total for r in parts))
+
+
 def render(gens, seeds8, d: int, window: Sequence[float], width: int, height: int,
            mode: str = "tree", threads: Optional[int] = None, eta: float = 0.0,
            edge_cap: int = 1 << 16, i0: int = 0, i1: Optional[int] = None,

@@ -9,6 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libkl.so")
 
 FP64, MIXED = 0, 1
+LIMIT_SET, TILING = 0, 1  # kl_mode
 KL_CNT_IN_WINDOW, KL_CNT_DROPPED, KL_CNT_FP64_WORDS, KL_CNT_ATOMICS, KL_N_COUNTERS = 0, 1, 2, 3, 4
 
 # Every function include/kl.h declares, in declaration order.
@@ -42,6 +43,7 @@ class Params(ctypes.Structure):
         ("accumulate", ctypes.c_uint32),
         ("block_threads", ctypes.c_uint32),
         ("chunk_pairs", ctypes.c_uint32),
+        ("mode", ctypes.c_uint32),
     ]
 
 

@@ -138,5 +138,6 @@ extern "C" int kl_params_init(kl_params* p, double ta_re, double ta_im, double t
   p->parabolic_tol = 1e-6;
   p->prefix_len = 0;
   p->accumulate = 0;
+  p->mode = KL_LIMIT_SET;
   return KL_OK;
 }

@@ -222,42 +222,73 @@ int build_tables(const kl_params* p, const Plan& L, const View& V, const Group& 
                           p->parabolic_tol, mixed, T);
 }
 
+// Length k of a tiling render of *p: a limit-set render of the words of
+// length k; the caller's prefix length applies to length d only.
+kl_params length_params(const kl_params* p, uint32_t k) {
+  kl_params q = *p;
+  q.depth = k;
+  q.mode = KL_LIMIT_SET;
+  if (k != p->depth) q.prefix_len = 0;
+  return q;
+}
+
+// Workspace bytes of *p (tiling: the largest over its lengths), or 0.
+size_t plan_bytes(const kl_params* p) {
+  if (!p || !valid_view(p)) return 0;
+  if (p->mode != KL_LIMIT_SET && p->mode != KL_TILING) return 0;
+  Plan L;
+  if (make_plan(p, &L, false) != KL_OK) return 0;
+  size_t most = L.total;
+  if (p->mode == KL_TILING) {
+    for (uint32_t k = 1; k < p->depth; ++k) {
+      const kl_params q = length_params(p, k);
+      if (make_plan(&q, &L, false) != KL_OK) return 0;
+      most = L.total > most ? L.total : most;
+    }
+  }
+  return most;
+}
+
 int validate(const kl_params* p, size_t ws_bytes, void* ws, Plan* L) {
   if (!p || !valid_view(p)) return KL_EINVAL;
   if (p->precision != KL_FP64 && p->precision != KL_MIXED) return KL_EINVAL;
+  if (p->mode != KL_LIMIT_SET && p->mode != KL_TILING) return KL_EINVAL;
   if (!(p->parabolic_tol >= 0.0)) return KL_EINVAL;
   const int st = make_plan(p, L, false);
   if (st != KL_OK) return st;
   if (L->d > 1) {
     if (!ws) return KL_EINVAL;
     if (((uintptr_t)ws & 255u) != 0) return KL_EINVAL;
-    if (ws_bytes < L->total) return KL_ENOSPACE;
+    const size_t need = plan_bytes(p);
+    if (need == 0) return KL_EINVAL;
+    if (ws_bytes < need) return KL_ENOSPACE;
   }
   return KL_OK;
 }
 
 template <int BT>
 int launch_render(const kl_params* p, const Plan& L, const View& V, const Tables& T,
-                  uint32_t* img, unsigned long long* cnt, cudaStream_t s) {
+                  uint32_t* img, unsigned long long* cnt, cudaStream_t s, bool profile) {
+  const cudaEvent_t ev0 = profile ? g_prof_start : nullptr, ev1 = profile ? g_prof_stop : nullptr;
   int sms = 0, occ = 0;
   if (p->precision == KL_FP64) {
     if (device_slots((const void*)render64_kernel<BT>, BT, &sms, &occ) != KL_OK) return KL_ECUDA;
     const Work Wk = make_work(L, BT, L.ns, sms * occ, 2u * p->chunk_pairs);
-    if (prof_mark(g_prof_start, s) != KL_OK) return KL_ECUDA;
+    if (prof_mark(ev0, s) != KL_OK) return KL_ECUDA;
     if (launch_dependent(render64_kernel<BT>, dim3(sms * occ), dim3(BT), s, T, L, V, Wk, img,
                          cnt) != KL_OK)
       return KL_ECUDA;
-    return prof_mark(g_prof_stop, s);
+    return prof_mark(ev1, s);
   }
   if (device_slots((const void*)render_mixed_kernel<BT>, BT, &sms, &occ) != KL_OK)
     return KL_ECUDA;
   // warp-sized items (32 prefixes), about 12 per resident warp
   const Work Wk = make_work(L, 32, L.npairs, sms * occ * (BT / 32), p->chunk_pairs);
-  if (prof_mark(g_prof_start, s) != KL_OK) return KL_ECUDA;
+  if (prof_mark(ev0, s) != KL_OK) return KL_ECUDA;
   if (launch_dependent(render_mixed_kernel<BT>, dim3(sms * occ), dim3(BT), s, T, L, V, Wk, img,
                        cnt) != KL_OK)
     return KL_ECUDA;
-  return prof_mark(g_prof_stop, s);
+  return prof_mark(ev1, s);
 }
 
 }  // namespace
@@ -265,12 +296,7 @@ int launch_render(const kl_params* p, const Plan& L, const View& V, const Tables
 // ---------------------------------------------------------------------------
 // C ABI
 
-extern "C" size_t kl_workspace_bytes(const kl_params* p) {
-  if (!p || !valid_view(p)) return 0;
-  Plan L;
-  if (make_plan(p, &L, false) != KL_OK) return 0;
-  return L.total;
-}
+extern "C" size_t kl_workspace_bytes(const kl_params* p) { return plan_bytes(p); }
 
 extern "C" int kl_decode_words(uint32_t depth, const uint64_t* d_index, uint64_t n,
                                uint8_t* d_letters, void* stream) {
@@ -312,14 +338,14 @@ extern "C" int kl_eval_words(const kl_params* p, const uint64_t* d_index, uint64
   return check_launch();
 }
 
-extern "C" int kl_render(const kl_params* p, uint32_t* d_image, uint64_t* d_counters,
-                         void* d_workspace, size_t workspace_bytes, void* stream) {
+namespace {
+
+// One limit-set render of *p (already validated).
+int render_length(const kl_params* p, uint32_t* d_image, unsigned long long* cnt,
+                  void* d_workspace, cudaStream_t s, bool profile) {
   Plan L;
-  int st = validate(p, workspace_bytes, d_workspace, &L);
+  int st = make_plan(p, &L, false);
   if (st != KL_OK) return st;
-  if (!d_image) return KL_EINVAL;
-  cudaStream_t s = (cudaStream_t)stream;
-  unsigned long long* cnt = (unsigned long long*)d_counters;
   const View V = make_view(p);
   const Group G = make_group(p);
   if (L.d == 1) {
@@ -339,10 +365,34 @@ extern "C" int kl_render(const kl_params* p, uint32_t* d_image, uint64_t* d_coun
   st = build_tables(p, L, V, G, T, s, C);
   if (st != KL_OK) return st;
   switch (p->block_threads) {
-    case 64: return launch_render<64>(p, L, V, T, d_image, cnt, s);
-    case 256: return launch_render<256>(p, L, V, T, d_image, cnt, s);
-    default: return launch_render<128>(p, L, V, T, d_image, cnt, s);
+    case 64: return launch_render<64>(p, L, V, T, d_image, cnt, s, profile);
+    case 256: return launch_render<256>(p, L, V, T, d_image, cnt, s, profile);
+    default: return launch_render<128>(p, L, V, T, d_image, cnt, s, profile);
   }
+}
+
+}  // namespace
+
+extern "C" int kl_render(const kl_params* p, uint32_t* d_image, uint64_t* d_counters,
+                         void* d_workspace, size_t workspace_bytes, void* stream) {
+  Plan L;
+  int st = validate(p, workspace_bytes, d_workspace, &L);
+  if (st != KL_OK) return st;
+  if (!d_image) return KL_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long* cnt = (unsigned long long*)d_counters;
+  if (p->mode == KL_TILING) {
+    // the longest words first (they clear the image unless accumulating),
+    // then every shorter length added in
+    for (uint32_t k = p->depth; k >= 1; --k) {
+      kl_params q = length_params(p, k);
+      q.accumulate = k == p->depth ? p->accumulate : 1u;
+      st = render_length(&q, d_image, cnt, d_workspace, s, k == p->depth);
+      if (st != KL_OK) return st;
+    }
+    return KL_OK;
+  }
+  return render_length(p, d_image, cnt, d_workspace, s, true);
 }
 
 extern "C" int kl_set_profile_events(void* ev_start, void* ev_stop) {

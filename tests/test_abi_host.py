@@ -115,3 +115,25 @@ def test_pruned_render_rejects_bad_edge(kl):
         st = L.kl_render_lod_labels(ctypes.byref(p), 8, 15, fake, edge, fake, fake, fake, fake,
                                     1 << 30, None)
         assert st == 1, edge
+
+
+def test_tiling_workspace_and_rejections(kl):
+    """Tiling takes the largest table of its lengths; the batch and the
+    level-of-detail calls take limit-set parameters only (checked before any
+    device call)."""
+    import ctypes
+    for d in (1, 2, 9, 10, 11, 18, 20):
+        p = kl.params_init(2 + 0j, 2 + 0j, d, 512, 512, (-1.5, 1.5, -1.5, 1.5))
+        one = kl.workspace_bytes(p)
+        p.mode = kl.TILING
+        most = max(kl.workspace_bytes(kl.params_init(2 + 0j, 2 + 0j, k, 512, 512,
+                                                     (-1.5, 1.5, -1.5, 1.5)))
+                   for k in range(1, d + 1))
+        assert kl.workspace_bytes(p) == max(one, most)
+    p.mode = 2
+    assert kl.workspace_bytes(p) == 0
+    L = kl.binding.lib()
+    p = kl.params_init(2 + 0j, 2 + 0j, 12, 64, 64, (-1.5, 1.5, -1.5, 1.5), mode=kl.TILING)
+    h = ctypes.c_void_p()
+    assert L.kl_batch_create(ctypes.byref(p), 1, ctypes.byref(h)) == 1
+    assert L.kl_lod_label_bytes(ctypes.byref(p), 3, 8) == 0

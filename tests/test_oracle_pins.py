@@ -284,3 +284,21 @@ def test_gasket_config_words_all_in_window():
     # columns 511 and 512) may fall on one side.
     img = r.image.astype(np.int64)
     assert np.array_equal(img[:, :511], img[:, 513:][:, ::-1])
+
+
+@pytest.mark.parametrize("ta,tb,d", [(*GASKET, 5), (*NEAR_CUSP, 5)])
+def test_tiling_render_matches_brute_force_scan_over_all_lengths(ta, tb, d):
+    """Tiling mode draws every node of the tree: the paper's scan at every
+    length 1 .. d, each word at its own value; 2 (3^d - 1) nodes in all."""
+    G, seeds, g, s = mats(ta, tb)
+    window = (-1.37, 1.41, -1.29, 1.33)
+    img = np.zeros((48, 64), dtype=np.int64)
+    dropped = 0
+    for k in range(1, d + 1):
+        i, dr = brute_render(G, seeds, k, window, 64, 48)
+        img += i
+        dropped += dr
+    r = oracle.render_tiling(g, s, d, window, 64, 48, threads=2)
+    assert np.array_equal(r.image.astype(np.int64), img)
+    assert r.dropped == dropped
+    assert r.in_window + r.dropped == 2 * (3 ** d - 1)
