@@ -15,6 +15,9 @@ Parity status per function (what pins it is in ``tests/test_oracle_pins.py``):
   render         pinned: brute-force render from the scan, hit conservation
   render_tiling  pinned: brute-force scan over every length 1 .. d, the node
                  count 2 (3^d - 1)
+  fsa_count,     pinned: the paper's scan written out in Python (set and
+  render_fsa     image), the closed-form counts 4 3^(d-1) (once-punctured
+                 torus table) and 3 2^(d-1) (Klein four-group table)
   mlp (numpy)    pinned: central finite differences, closed-form tiny nets
 """
 from .oracle import *  # noqa: F401,F403

@@ -478,3 +478,82 @@ OR_EXPORT int or_decode_many(int d, const uint64_t* idx, uint64_t n, uint8_t* ou
   }
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* General presentations (Sec. "Cayley Multiplication Tables", Sec.         */
+/* "Implementation"): the paper's own scan over every index n of the        */
+/* unpruned m-ary tree of depth d.  n is written as d base-m digits, most   */
+/* significant first, each plus one (symbols 1 .. m; 0 is the identity);    */
+/* the string is kept if the run of the indexed Cayley table over it, read  */
+/* right to left from state 0, never reaches the crash state 0.  A kept     */
+/* string w_1 .. w_d (letter code = symbol - 1) is drawn at its word value: */
+/* the seed of w_d, then the maps of w_d, ..., w_1.                         */
+
+#define OR_FSA_MAX 9
+
+/* 1 if the symbols s[0..d-1] survive the table run, else 0. */
+static int fsa_run(int m, const uint8_t* table, const uint8_t* s, int d) {
+  int state = 0;
+  for (int k = d - 1; k >= 0; --k) {
+    state = table[state * (m + 1) + s[k]];
+    if (state == 0) return 0;
+  }
+  return 1;
+}
+
+/* Kept strings of the scan (counted by scanning; m^d <= 2^40). */
+OR_EXPORT int or_fsa_count(int m, const uint8_t* table, int d, uint64_t* out) {
+  if (m < 1 || m > OR_FSA_MAX || d < 1 || d > 40) return -1;
+  double total = pow((double)m, (double)d);
+  if (total > 1099511627776.0) return -1;
+  uint64_t n_idx = 1;
+  for (int k = 0; k < d; ++k) n_idx *= (uint64_t)m;
+  uint8_t s[64];
+  uint64_t kept = 0;
+  for (uint64_t n = 0; n < n_idx; ++n) {
+    uint64_t r = n;
+    for (int k = d - 1; k >= 0; --k) { s[k] = (uint8_t)(r % (uint64_t)m + 1); r /= (uint64_t)m; }
+    kept += (uint64_t)fsa_run(m, table, s, d);
+  }
+  *out = kept;
+  return 0;
+}
+
+/* Render of the kept strings of the scan of indices [i0, i1).  gens: m
+ * matrices of 8 doubles, seeds: m points of 2 doubles.  counters[0] +=
+ * in-window words, counters[1] += dropped kept words; edge words as in
+ * or_render_indexed, logged with their scan index n. */
+OR_EXPORT int or_render_fsa(int m, const uint8_t* table, const double* gens,
+                            const double* seeds2, int d, const double* window, int width,
+                            int height, uint64_t i0, uint64_t i1, uint32_t* image,
+                            uint64_t* counters, double eta, uint64_t* edge_idx,
+                            double* edge_uv, uint64_t edge_cap, uint64_t* edge_count) {
+  if (m < 1 || m > OR_FSA_MAX || d < 1 || d > 40 || width <= 0 || height <= 0) return -1;
+  for (int k = 0; k < (m + 1) * (m + 1); ++k)
+    if (table[k] > m) return -1;
+  uint64_t n_idx = 1;
+  for (int k = 0; k < d; ++k) {
+    if (n_idx > (1ull << 40) / (uint64_t)m) return -1;
+    n_idx *= (uint64_t)m;
+  }
+  if (i1 > n_idx || i0 > i1) return -1;
+  mat2 g[OR_FSA_MAX]; cx seeds[OR_FSA_MAX];
+  for (int x = 0; x < m; ++x) {
+    g[x] = mat_load(gens + 8 * x);
+    seeds[x] = cx_make(seeds2[2 * x], seeds2[2 * x + 1]);
+  }
+  view_t v = make_view(window, width, height, eta);
+  uint64_t dummy = 0;
+  sink_t sk = {image, 0, 0, edge_idx, edge_uv, edge_cap, edge_count ? edge_count : &dummy};
+  uint8_t s[64], w[64];
+  for (uint64_t n = i0; n < i1; ++n) {
+    uint64_t r = n;
+    for (int k = d - 1; k >= 0; --k) { s[k] = (uint8_t)(r % (uint64_t)m + 1); r /= (uint64_t)m; }
+    if (!fsa_run(m, table, s, d)) continue;
+    for (int k = 0; k < d; ++k) w[k] = (uint8_t)(s[k] - 1);
+    splat(&v, &sk, n, word_value(g, seeds, w, d));
+  }
+  counters[0] += sk.in_window;
+  counters[1] += sk.dropped;
+  return 0;
+}

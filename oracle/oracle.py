@@ -35,6 +35,10 @@ def lib():
         L.or_render_indexed.argtypes = [P, P, I, P, I, I, U64, U64, P, P, D, P, P, U64, P]
         L.or_render_indexed.restype = I
         L.or_render_tree.argtypes = [P, P, I, P, I, I, I, I, I, P, P, D, P, P, U64, P]
+        L.or_fsa_count.argtypes = [I, P, I, P]
+        L.or_fsa_count.restype = I
+        L.or_render_fsa.argtypes = [I, P, P, P, I, P, I, I, U64, U64, P, P, D, P, P, U64, P]
+        L.or_render_fsa.restype = I
         L.or_tree_jobs.argtypes = [I]
         L.or_tree_jobs.restype = I
         L.or_render_tree.restype = I
@@ -175,6 +179,50 @@ def render(gens, seeds8, d: int, window: Sequence[float], width: int, height: in
                                  _ptr(ecount))
     else:
         raise ValueError(mode)
+    if rc != 0:
+        raise ValueError("bad render arguments")
+    k = int(min(int(ecount[0]), cap))
+    return Render(img, int(cnt[0]), int(cnt[1]), eidx[:k].copy(),
+                  euv[:2 * k].reshape(k, 2).copy(), int(ecount[0]))
+
+
+# ---------------------------------------------------------------------------
+# general presentations (the paper's scan of the unpruned m-ary tree)
+
+def fsa_count(m: int, table, d: int) -> int:
+    """Strings of d symbols (1..m) that survive the run of the indexed table
+    (rows = states 0..m, columns = symbols 0..m), counted by the scan."""
+    t = np.ascontiguousarray(np.asarray(table, dtype=np.uint8).reshape(m + 1, m + 1))
+    out = np.zeros(1, dtype=np.uint64)
+    if lib().or_fsa_count(m, _ptr(t), d, _ptr(out)) != 0:
+        raise ValueError("bad table or depth")
+    return int(out[0])
+
+
+def render_fsa(m: int, table, gens, seeds, d: int, window: Sequence[float], width: int,
+               height: int, eta: float = 0.0, edge_cap: int = 1 << 16, i0: int = 0,
+               i1: Optional[int] = None) -> Render:
+    """Hit image of the kept strings of the scan of [i0, i1) (Sec.
+    "Implementation"): gens = m matrices [[p, q], [r, s]] (complex), seeds = m
+    points; edge words logged with their scan index."""
+    t = np.ascontiguousarray(np.asarray(table, dtype=np.uint8).reshape(m + 1, m + 1))
+    g = np.zeros((m, 8))
+    for x in range(m):
+        M = np.asarray(gens[x], dtype=complex).reshape(2, 2)
+        g[x] = [M[0, 0].real, M[0, 0].imag, M[0, 1].real, M[0, 1].imag,
+                M[1, 0].real, M[1, 0].imag, M[1, 1].real, M[1, 1].imag]
+    sd = np.array([[complex(z).real, complex(z).imag] for z in seeds], dtype=np.float64)
+    win = np.ascontiguousarray(window, dtype=np.float64)
+    img = np.zeros((height, width), dtype=np.uint32)
+    cnt = np.zeros(2, dtype=np.uint64)
+    cap = edge_cap if eta > 0 else 0
+    eidx = np.zeros(max(cap, 1), dtype=np.uint64)
+    euv = np.zeros(2 * max(cap, 1), dtype=np.float64)
+    ecount = np.zeros(1, dtype=np.uint64)
+    i1 = m ** d if i1 is None else i1
+    rc = lib().or_render_fsa(m, _ptr(t), _ptr(np.ascontiguousarray(g)), _ptr(sd), d, _ptr(win),
+                             width, height, i0, i1, _ptr(img), _ptr(cnt), eta, _ptr(eidx),
+                             _ptr(euv), cap, _ptr(ecount))
     if rc != 0:
         raise ValueError("bad render arguments")
     k = int(min(int(ecount[0]), cap))

@@ -302,3 +302,72 @@ def test_tiling_render_matches_brute_force_scan_over_all_lengths(ta, tb, d):
     assert np.array_equal(r.image.astype(np.int64), img)
     assert r.dropped == dropped
     assert r.in_window + r.dropped == 2 * (3 ** d - 1)
+
+
+# --------------------------------------------------------------------------
+# general presentations: the paper's scan with the indexed table
+
+# Klein four-group as Moebius maps of determinant one: a(z) = -z, b(z) = 1/z,
+# ab(z) = -1/z (symbols 1, 2, 3 of the table fixture); each squares to -I.
+KLEIN = [np.array([[1j, 0], [0, -1j]]), np.array([[0, 1j], [1j, 0]]),
+         np.array([[0, -1 + 0j], [1 + 0j, 0]])]
+
+
+def test_klein_generators_satisfy_the_table():
+    """The fixture's products: a b = ab, a ab = b, b ab = a (up to sign), and
+    every letter squares to the identity (the crash state)."""
+    a, b, c = KLEIN
+    I = np.eye(2)
+    for x in KLEIN:
+        assert np.allclose(x @ x, -I)
+        assert np.isclose(np.linalg.det(x), 1)
+    for x, y, z in [(a, b, c), (a, c, b), (b, c, a)]:
+        assert np.allclose(x @ y, z) or np.allclose(x @ y, -z)
+
+
+@pytest.mark.parametrize("d", range(1, 9))
+def test_fsa_counts(d):
+    t11 = golden_table("t11_indexed_cayley.txt")
+    k4 = golden_table("klein4_indexed_cayley.txt")
+    assert oracle.fsa_count(4, t11, d) == 4 * 3 ** (d - 1)
+    assert oracle.fsa_count(3, k4, d) == 3 * 2 ** (d - 1)
+
+
+def brute_render_table(G, seeds, table, m, d, window, W, H):
+    x0, x1, y0, y1 = window
+    img = np.zeros((H, W), dtype=np.int64)
+    dropped = kept = 0
+    for _, w in paper_scan.reduced_words_by_scan(d, table=table, m=m):
+        kept += 1
+        z = paper_scan.word_value(G, seeds, w)
+        u = (z.real - x0) * (W / (x1 - x0))
+        v = (y1 - z.imag) * (H / (y1 - y0))
+        if 0 <= u < W and 0 <= v < H:
+            img[int(np.floor(v)), int(np.floor(u))] += 1
+        else:
+            dropped += 1
+    return img, dropped, kept
+
+
+def test_fsa_render_klein_four_matches_the_scan():
+    k4 = golden_table("klein4_indexed_cayley.txt")
+    seeds = [0.31 + 0.17j, -0.43 + 0.29j, 0.12 - 0.61j]
+    window = (-4.1, 3.9, -3.7, 4.3)
+    img, dropped, kept = brute_render_table(KLEIN, seeds, k4, 3, 7, window, 80, 60)
+    r = oracle.render_fsa(3, k4, KLEIN, seeds, 7, window, 80, 60)
+    assert np.array_equal(r.image.astype(np.int64), img)
+    assert r.dropped == dropped and r.in_window + r.dropped == kept == 3 * 2 ** 6
+
+
+@pytest.mark.parametrize("ta,tb,d", [(*GASKET, 6), (*NEAR_CUSP, 5)])
+def test_fsa_render_of_the_torus_table_matches_the_scan_and_the_limit_set(ta, tb, d):
+    G, seeds, g, s = mats(ta, tb)
+    t11 = golden_table("t11_indexed_cayley.txt")
+    window = (-1.37, 1.41, -1.29, 1.33)
+    img, dropped, kept = brute_render_table(G, seeds, t11, 4, d, window, 64, 48)
+    r = oracle.render_fsa(4, t11, G, seeds, d, window, 64, 48)
+    assert np.array_equal(r.image.astype(np.int64), img)
+    assert r.dropped == dropped and kept == oracle.word_count(d)
+    # the same words as the reduced-index render, with the same arithmetic
+    ref = oracle.render(g, s, d, window, 64, 48, mode="indexed")
+    assert np.array_equal(r.image, ref.image)
