@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-lod", action="store_true")
     ap.add_argument("--no-tiling", action="store_true")
+    ap.add_argument("--no-scan", action="store_true")
     return ap.parse_args()
 
 
@@ -262,6 +263,51 @@ def tiling_config(kl, dev, steps: int, flush):
                         "lengths 1..18, 4096x4096 uint32, window [-1.5,1.5]^2, mixed",
             "words_per_step": words, "ms_per_step": ms, "words_per_s": words / (ms / 1000.0),
             "steps": K, "fp64_words": int(cnt[2])}
+
+
+def scan_config(kl, dev, flush):
+    """The paper's own enumeration for a general presentation (kl_render_fsa):
+    the unpruned 4-ary tree of depth 14 of the gasket group scanned and
+    filtered by the indexed Cayley table, FP64, against the reduced-index
+    render of the same words (FP64 and mixed)."""
+    import torch
+    import oracle
+    d, W = 14, 4096
+    window = (-1.5, 1.5, -1.5, 1.5)
+    g, s = oracle.group(klsynth.GASKET.ta, klsynth.GASKET.tb)
+    table = [[0, 1, 2, 3, 4], [1, 1, 2, 0, 4], [2, 1, 2, 3, 0], [3, 0, 2, 3, 4], [4, 1, 0, 3, 4]]
+    f = kl.fsa(table, [m.tolist() for m in oracle.as_matrices(g)], oracle.as_points(s))
+    p = kl.params_init(klsynth.GASKET.ta, klsynth.GASKET.tb, d, W, W, window, kl.FP64)
+    img = torch.empty((W, W), dtype=torch.int32, device=dev)
+    cnt = torch.zeros(kl.KL_N_COUNTERS, dtype=torch.int64, device=dev)
+
+    def timed(fn, K=5):
+        for _ in range(2):
+            fn()
+        ms = []
+        for k in range(K):
+            flush.fill_(k & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize(dev)
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+    scan_ms = timed(lambda: kl.render_fsa(f, p, img, cnt))
+    kept = int(cnt[2].item())
+    r64 = kl.Renderer(p, device=dev)
+    reduced64_ms = timed(lambda: r64())
+    pm = kl.params_init(klsynth.GASKET.ta, klsynth.GASKET.tb, d, W, W, window, kl.MIXED)
+    rm = kl.Renderer(pm, device=dev)
+    reduced_mixed_ms = timed(lambda: rm())
+    return {"workload": "gasket ta=tb=2, all 4^14 strings of the unpruned tree scanned and "
+                        "filtered by the indexed Cayley table, FP64, 4096^2",
+            "strings": 4 ** d, "kept_words": kept, "ms": scan_ms,
+            "strings_per_s": 4 ** d / (scan_ms / 1000.0),
+            "kept_words_per_s": kept / (scan_ms / 1000.0),
+            "reduced_index_fp64_ms": reduced64_ms, "reduced_index_mixed_ms": reduced_mixed_ms,
+            "speedup_reduced_index_mixed_over_scan": scan_ms / reduced_mixed_ms}
 
 
 def batch_sweep(kl, dev, steps: int):
@@ -505,6 +551,8 @@ def run_ours(args):
             "speedup_mixed_over_fp64": fp64_step_ms / (total_ms / K)}
     if not args.no_tiling:
         line["tiling"] = tiling_config(kl, dev, K, flush)
+    if not args.no_scan:
+        line["paper_scan"] = scan_config(kl, dev, flush)
     if not args.no_batch:
         line["batch_sweep"] = batch_sweep(kl, dev, K)
     if not args.no_lod:

@@ -327,6 +327,40 @@ KL_API int kl_render_lod_labels(const kl_params* p, uint32_t lo, uint32_t hi,
                                 uint64_t* d_counters, uint64_t* d_stats, void* d_workspace,
                                 size_t workspace_bytes, void* stream);
 
+/* General presentations (Sec. "Cayley Multiplication Tables" and Sec.
+ * "Implementation"): the paper's own enumeration, for any group given by an
+ * indexed Cayley table.  Every index n in [0, m^d) of the unpruned m-ary tree
+ * is written as d base-m digits, each plus one (symbols 1..m; 0 is the
+ * identity), the first digit most significant; the string is kept when the
+ * run of the table over it, read right to left from state 0, never reaches
+ * the crash state 0.  A kept string w_1 .. w_d (letter = symbol - 1) is drawn
+ * at its word value: the seed of w_d, then the maps of w_d, ..., w_1. */
+#define KL_FSA_MAX_LETTERS 9
+#define KL_FSA_WORKSPACE_BYTES 256u
+
+typedef struct {
+  uint32_t m;   /* letters (symbols 1..m), 1 .. KL_FSA_MAX_LETTERS */
+  uint8_t table[(KL_FSA_MAX_LETTERS + 1) * (KL_FSA_MAX_LETTERS + 1)];
+                /* indexed table, row-major with row stride KL_FSA_MAX_LETTERS + 1:
+                   table[state * 10 + symbol] = next state (0..m, 0 = crash) for
+                   states and symbols 0..m; the run starts in state 0 */
+  double gens[KL_FSA_MAX_LETTERS * 8];  /* letter k's matrix (p, q, r, s as re, im) */
+  double seeds[KL_FSA_MAX_LETTERS * 2]; /* seed point of each first-applied letter */
+} kl_fsa;
+
+/* Strings of length `depth` kept by the table run (host only, no GPU):
+ * counted by the states of the run, not by scanning.  KL_ERANGE unless
+ * 1 <= depth <= 32 and m^depth <= 2^40; KL_EINVAL on a table entry > m. */
+KL_API int kl_fsa_count(const kl_fsa* f, uint32_t depth, uint64_t* count);
+
+/* Render of the kept strings of depth p->depth with the view, image size and
+ * accumulate flag of *p (its gens, seeds and mode are not used; precision
+ * must be KL_FP64).  Counters as kl_render (KL_CNT_FP64_WORDS = kept words).
+ * d_workspace: at least KL_FSA_WORKSPACE_BYTES, 256-byte aligned. */
+KL_API int kl_render_fsa(const kl_fsa* f, const kl_params* p, uint32_t* d_image,
+                         uint64_t* d_counters, void* d_workspace, size_t workspace_bytes,
+                         void* stream);
+
 /* Size of the library's own device scratch array used by kl_render_noalloc. */
 #define KL_STATIC_SCRATCH_BYTES (32u << 20)
 

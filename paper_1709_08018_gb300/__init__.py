@@ -10,7 +10,8 @@ and fails loudly if it has not been built (``__graft_entry__.build()`` or
 from .binding import (  # noqa: F401
     FP64, KL_CNT_ATOMICS, KL_CNT_DROPPED, KL_CNT_FP64_WORDS, KL_CNT_IN_WINDOW, KL_MLP_NPARAMS,
     KL_N_COUNTERS, KL_STATIC_SCRATCH_BYTES, LIMIT_SET, MIXED, TILING, Batch, KlError,
-    LodRenderer, MlpTrainer, Params, Renderer, lod_labels, lod_node_count,
+    LodRenderer, MlpTrainer, Params, Renderer, lod_labels, lod_node_count, Fsa, fsa, fsa_count,
+    render_fsa,
     decode_words, eval_words, exported_symbols, grandma, lib, mlp_forward, params_init, render,
     render_noalloc, seeds, set_profile_events, status_string, word_count, workspace_bytes,
 )

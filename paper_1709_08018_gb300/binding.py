@@ -18,8 +18,8 @@ API = ("kl_status_string", "kl_word_count", "kl_grandma", "kl_seeds", "kl_params
        "kl_batch_create", "kl_batch_workspace_bytes", "kl_batch_render", "kl_batch_capture",
        "kl_batch_replay", "kl_batch_destroy", "kl_mlp_forward", "kl_mlp_scratch_bytes",
        "kl_mlp_grad", "kl_mlp_adam", "kl_lod_node_count", "kl_lod_label_bytes", "kl_lod_labels",
-       "kl_lod_render_bytes", "kl_render_lod", "kl_render_lod_labels", "kl_render_noalloc",
-       "kl_set_profile_events")
+       "kl_lod_render_bytes", "kl_render_lod", "kl_render_lod_labels", "kl_fsa_count",
+       "kl_render_fsa", "kl_render_noalloc", "kl_set_profile_events")
 KL_MLP_NPARAMS = 4801
 KL_STATIC_SCRATCH_BYTES = 32 << 20
 
@@ -45,6 +45,60 @@ class Params(ctypes.Structure):
         ("chunk_pairs", ctypes.c_uint32),
         ("mode", ctypes.c_uint32),
     ]
+
+
+KL_FSA_MAX_LETTERS = 9
+KL_FSA_WORKSPACE_BYTES = 256
+
+
+class Fsa(ctypes.Structure):
+    """Mirror of ``kl_fsa``: a group given by m Moebius generators, seeds and
+    an indexed Cayley table (row stride KL_FSA_MAX_LETTERS + 1)."""
+    _fields_ = [
+        ("m", ctypes.c_uint32),
+        ("table", ctypes.c_uint8 * ((KL_FSA_MAX_LETTERS + 1) ** 2)),
+        ("gens", ctypes.c_double * (KL_FSA_MAX_LETTERS * 8)),
+        ("seeds", ctypes.c_double * (KL_FSA_MAX_LETTERS * 2)),
+    ]
+
+
+def fsa(table, gens, seeds) -> Fsa:
+    """A kl_fsa from an (m+1) x (m+1) table, m 2x2 complex matrices and m seeds."""
+    m = len(gens)
+    f = Fsa()
+    f.m = m
+    for r, row in enumerate(table):
+        for c, v in enumerate(row):
+            f.table[r * (KL_FSA_MAX_LETTERS + 1) + c] = int(v)
+    for x, M in enumerate(gens):
+        vals = [M[0][0], M[0][1], M[1][0], M[1][1]]
+        for k, z in enumerate(vals):
+            f.gens[8 * x + 2 * k] = complex(z).real
+            f.gens[8 * x + 2 * k + 1] = complex(z).imag
+    for x, z in enumerate(seeds):
+        f.seeds[2 * x] = complex(z).real
+        f.seeds[2 * x + 1] = complex(z).imag
+    return f
+
+
+def fsa_count(f: Fsa, depth: int) -> int:
+    out = ctypes.c_uint64()
+    _check(lib().kl_fsa_count(ctypes.byref(f), depth, ctypes.byref(out)), "kl_fsa_count")
+    return int(out.value)
+
+
+def render_fsa(f: Fsa, p: "Params", image=None, counters=None, stream=None, device="cuda"):
+    """kl_render_fsa with the view, size, depth and accumulate flag of p."""
+    torch = _torch()
+    if image is None:
+        image = torch.empty((p.height, p.width), dtype=torch.int32, device=device)
+    if counters is None:
+        counters = torch.zeros(KL_N_COUNTERS, dtype=torch.int64, device=image.device)
+    ws = torch.empty(KL_FSA_WORKSPACE_BYTES, dtype=torch.uint8, device=image.device)
+    _check(lib().kl_render_fsa(ctypes.byref(f), ctypes.byref(p), image.data_ptr(),
+                               counters.data_ptr(), ws.data_ptr(), ws.numel(),
+                               _stream_handle(stream)), "kl_render_fsa")
+    return image, counters
 
 
 class KlError(RuntimeError):
@@ -121,6 +175,10 @@ def lib():
         L.kl_render_lod_labels.argtypes = [ctypes.POINTER(Params), U32, U32, P, ctypes.c_float, P,
                                            P, P, P, SZ, P]
         L.kl_render_lod_labels.restype = I
+        L.kl_fsa_count.argtypes = [ctypes.POINTER(Fsa), U32, ctypes.POINTER(ctypes.c_uint64)]
+        L.kl_fsa_count.restype = I
+        L.kl_render_fsa.argtypes = [ctypes.POINTER(Fsa), ctypes.POINTER(Params), P, P, P, SZ, P]
+        L.kl_render_fsa.restype = I
         L.kl_render_noalloc.argtypes = [ctypes.POINTER(Params), P, P, P]
         L.kl_render_noalloc.restype = I
         L.kl_set_profile_events.argtypes = [P, P]

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libkl.so")
-SOURCES = ["kl_render.cu", "kl_batch.cu", "kl_mlp.cu", "kl_lod.cu", "kl_host.cpp"]
+SOURCES = ["kl_render.cu", "kl_batch.cu", "kl_mlp.cu", "kl_lod.cu", "kl_fsa.cu", "kl_host.cpp"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

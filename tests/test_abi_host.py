@@ -137,3 +137,46 @@ def test_tiling_workspace_and_rejections(kl):
     h = ctypes.c_void_p()
     assert L.kl_batch_create(ctypes.byref(p), 1, ctypes.byref(h)) == 1
     assert L.kl_lod_label_bytes(ctypes.byref(p), 3, 8) == 0
+
+
+def _klein():
+    return [[[1j, 0], [0, -1j]], [[0, 1j], [1j, 0]], [[0, -1], [1, 0]]]
+
+
+def test_fsa_count_agrees_with_the_oracle_scan(kl):
+    from conftest import golden_table
+    t11 = golden_table("t11_indexed_cayley.txt")
+    k4 = golden_table("klein4_indexed_cayley.txt")
+    g, s = oracle.group(2 + 0j, 2 + 0j)
+    torus = kl.fsa(t11, [m.tolist() for m in oracle.as_matrices(g)], oracle.as_points(s))
+    klein = kl.fsa(k4, _klein(), [0.3 + 0.2j, -0.4 + 0.3j, 0.1 - 0.6j])
+    for d in range(1, 9):
+        assert kl.fsa_count(torus, d) == oracle.fsa_count(4, t11, d) == 4 * 3 ** (d - 1)
+        assert kl.fsa_count(klein, d) == oracle.fsa_count(3, k4, d)
+    assert kl.fsa_count(torus, 20) == 4 * 3 ** 19          # beyond any scan
+    # a table with a free letter: every string of length d survives
+    free = kl.fsa([[0, 1], [0, 1]], [[[1, 1], [0, 1]]], [0j])
+    assert kl.fsa_count(free, 12) == 1
+    free2 = kl.fsa([[0, 1, 2], [0, 1, 2], [0, 1, 2]], _klein()[:2], [0j, 0j])
+    assert kl.fsa_count(free2, 10) == 2 ** 10
+
+
+def test_fsa_rejects_bad_input(kl):
+    from conftest import golden_table
+    k4 = golden_table("klein4_indexed_cayley.txt")
+    f = kl.fsa(k4, _klein(), [0j, 0j, 0j])
+    for d, status in [(0, 2), (33, 2), (26, 2)]:     # 3^26 > 2^40
+        with pytest.raises(kl.KlError) as e:
+            kl.fsa_count(f, d)
+        assert e.value.status == status
+    f.table[1 * 10 + 2] = 7                            # entry > m
+    with pytest.raises(kl.KlError):
+        kl.fsa_count(f, 4)
+    f = kl.fsa(k4, _klein(), [0j, 0j, 0j])
+    f.m = 10
+    with pytest.raises(kl.KlError):
+        kl.fsa_count(f, 4)
+    f.m = 3
+    f.gens[5] = float("nan")
+    with pytest.raises(kl.KlError):
+        kl.fsa_count(f, 4)
