@@ -271,13 +271,13 @@ def scan_config(kl, dev, flush):
     filtered by the indexed Cayley table, FP64, against the reduced-index
     render of the same words (FP64 and mixed)."""
     import torch
-    import oracle
     d, W = 14, 4096
     window = (-1.5, 1.5, -1.5, 1.5)
-    g, s = oracle.group(klsynth.GASKET.ta, klsynth.GASKET.tb)
+    # the indexed Cayley table of the once-punctured torus (Sec. "Cayley
+    # Multiplication Tables"): states and symbols I, a, b, A, B = 0..4
     table = [[0, 1, 2, 3, 4], [1, 1, 2, 0, 4], [2, 1, 2, 3, 0], [3, 0, 2, 3, 4], [4, 1, 0, 3, 4]]
-    f = kl.fsa(table, [m.tolist() for m in oracle.as_matrices(g)], oracle.as_points(s))
     p = kl.params_init(klsynth.GASKET.ta, klsynth.GASKET.tb, d, W, W, window, kl.FP64)
+    f = kl.fsa_from_params(table, p)
     img = torch.empty((W, W), dtype=torch.int32, device=dev)
     cnt = torch.zeros(kl.KL_N_COUNTERS, dtype=torch.int64, device=dev)
 

@@ -81,6 +81,21 @@ def fsa(table, gens, seeds) -> Fsa:
     return f
 
 
+def fsa_from_params(table, p: "Params") -> Fsa:
+    """A kl_fsa with the four letters a, b, A, B of p (its generators and
+    seeds) and the given (5 x 5) indexed table."""
+    f = Fsa()
+    f.m = 4
+    for r, row in enumerate(table):
+        for c, v in enumerate(row):
+            f.table[r * (KL_FSA_MAX_LETTERS + 1) + c] = int(v)
+    for k in range(32):
+        f.gens[k] = p.gens[k]
+    for k in range(8):
+        f.seeds[k] = p.seeds[k]
+    return f
+
+
 def fsa_count(f: Fsa, depth: int) -> int:
     out = ctypes.c_uint64()
     _check(lib().kl_fsa_count(ctypes.byref(f), depth, ctypes.byref(out)), "kl_fsa_count")

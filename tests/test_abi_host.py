@@ -180,3 +180,16 @@ def test_fsa_rejects_bad_input(kl):
     f.gens[5] = float("nan")
     with pytest.raises(kl.KlError):
         kl.fsa_count(f, 4)
+
+
+def test_fsa_from_params_carries_the_group(kl):
+    from conftest import golden_table
+    t11 = golden_table("t11_indexed_cayley.txt")
+    p = kl.params_init(1.91 + 0.05j, 1.91 + 0.05j, 10, 64, 64, (-2.0, 2.0, -2.0, 2.0))
+    f = kl.fsa_from_params(t11, p)
+    g, s = oracle.group(1.91 + 0.05j, 1.91 + 0.05j)
+    h = kl.fsa(t11, [m.tolist() for m in oracle.as_matrices(g)], oracle.as_points(s))
+    assert f.m == h.m == 4 and bytes(f.table) == bytes(h.table)
+    assert np.allclose(list(f.gens)[:32], list(h.gens)[:32], rtol=1e-14, atol=1e-15)
+    assert np.allclose(list(f.seeds)[:8], list(h.seeds)[:8], rtol=1e-12, atol=1e-13)
+    assert kl.fsa_count(f, 10) == oracle.word_count(10)
