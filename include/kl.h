@@ -138,6 +138,16 @@ KL_API int kl_grandma(double ta_re, double ta_im, double tb_re, double tb_im, do
  * attracting finite fixed point.  Host only. */
 KL_API int kl_seeds(const double* gens, double* seeds_out);
 
+/* Maskit's slice (the once-punctured torus groups with b parabolic): a(z) =
+ * mu + 1/z, b(z) = z + 2, written as matrices of determinant one, and their
+ * inverses, into gens_out (32 doubles); tr(a b A B) = -2 for every mu.  The
+ * group of the paper's example is mu = -0.097 + 1.838 i.  seeds_out (8
+ * doubles): the attracting fixed points of a and A; b and B fix only
+ * infinity, so they get the fixed point of the parabolic commutator a b A B,
+ * a finite limit point.  Host only.  KL_EDEGENERATE if a fixed point is not
+ * finite. */
+KL_API int kl_maskit(double mu_re, double mu_im, double* gens_out, double* seeds_out);
+
 /* Fill *p: generators and seeds from the traces, the given depth, image and
  * window, and defaults for the rest (precision KL_FP64, renorm_every 8,
  * parabolic_tol 1e-6, prefix_len 0, accumulate 0).  Host only. */

@@ -557,3 +557,42 @@ OR_EXPORT int or_render_fsa(int m, const uint8_t* table, const double* gens,
   counters[1] += sk.dropped;
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Maskit's slice ("Indra's Pearls", ch. 9), the group of the paper's       */
+/* example: a(z) = mu + 1/z and b(z) = z + 2.  As matrices of determinant   */
+/* one: a = i [[mu, 1], [1, 0]] and b = [[1, 2], [0, 1]]; A, B their        */
+/* inverses.  Seeds: a and A by or_seeds' rule; b and B fix only infinity,  */
+/* so they take the fixed point of the parabolic commutator a b A B, a     */
+/* finite limit point.                                                     */
+
+static mat2 mat_mul(mat2 x, mat2 y) {
+  mat2 o;
+  o.p = cx_add(cx_mul(x.p, y.p), cx_mul(x.q, y.r));
+  o.q = cx_add(cx_mul(x.p, y.q), cx_mul(x.q, y.s));
+  o.r = cx_add(cx_mul(x.r, y.p), cx_mul(x.s, y.r));
+  o.s = cx_add(cx_mul(x.r, y.q), cx_mul(x.s, y.s));
+  return o;
+}
+
+OR_EXPORT int or_maskit(double mu_re, double mu_im, double* gens, double* seeds) {
+  cx i = cx_make(0.0, 1.0), mu = cx_make(mu_re, mu_im);
+  mat2 a, b;
+  a.p = cx_mul(i, mu); a.q = i; a.r = i; a.s = cx_make(0.0, 0.0);
+  b.p = cx_make(1.0, 0.0); b.q = cx_make(2.0, 0.0); b.r = cx_make(0.0, 0.0);
+  b.s = cx_make(1.0, 0.0);
+  mat2 all[4];
+  all[0] = a; all[1] = b; all[2] = mat_inverse_unimodular(a); all[3] = mat_inverse_unimodular(b);
+  for (int x = 0; x < 4; ++x) mat_store(&all[x], gens + 8 * x);
+  /* seeds of a and A: or_seeds on a generator list whose b slots repeat a */
+  double tmp[32], s4[8];
+  for (int x = 0; x < 4; ++x) mat_store(&all[x & 2], tmp + 8 * x);
+  if (or_seeds(tmp, s4) != 0) return -1;
+  seeds[0] = s4[0]; seeds[1] = s4[1]; seeds[4] = s4[4]; seeds[5] = s4[5];
+  mat2 k = mat_mul(mat_mul(all[0], all[1]), mat_mul(all[2], all[3]));
+  if (k.r.re == 0.0 && k.r.im == 0.0) return -1;
+  cx zk = cx_div(cx_sub(k.p, k.s), cx_scale(k.r, 2.0));
+  seeds[2] = seeds[6] = zk.re;
+  seeds[3] = seeds[7] = zk.im;
+  return 0;
+}

@@ -35,6 +35,8 @@ def lib():
         L.or_render_indexed.argtypes = [P, P, I, P, I, I, U64, U64, P, P, D, P, P, U64, P]
         L.or_render_indexed.restype = I
         L.or_render_tree.argtypes = [P, P, I, P, I, I, I, I, I, P, P, D, P, P, U64, P]
+        L.or_maskit.argtypes = [D, D, P, P]
+        L.or_maskit.restype = I
         L.or_fsa_count.argtypes = [I, P, I, P]
         L.or_fsa_count.restype = I
         L.or_render_fsa.argtypes = [I, P, P, P, I, P, I, I, U64, U64, P, P, D, P, P, U64, P]
@@ -228,3 +230,13 @@ def render_fsa(m: int, table, gens, seeds, d: int, window: Sequence[float], widt
     k = int(min(int(ecount[0]), cap))
     return Render(img, int(cnt[0]), int(cnt[1]), eidx[:k].copy(),
                   euv[:2 * k].reshape(k, 2).copy(), int(ecount[0]))
+
+
+def maskit(mu: complex) -> Tuple[np.ndarray, np.ndarray]:
+    """Maskit's slice group a(z) = mu + 1/z, b(z) = z + 2: (32 generator
+    doubles, 8 seed doubles); see or_maskit."""
+    g = np.zeros(32)
+    s = np.zeros(8)
+    if lib().or_maskit(mu.real, mu.imag, _ptr(g), _ptr(s)) != 0:
+        raise ValueError("degenerate Maskit group")
+    return g, s

@@ -13,7 +13,8 @@ LIMIT_SET, TILING = 0, 1  # kl_mode
 KL_CNT_IN_WINDOW, KL_CNT_DROPPED, KL_CNT_FP64_WORDS, KL_CNT_ATOMICS, KL_N_COUNTERS = 0, 1, 2, 3, 4
 
 # Every function include/kl.h declares, in declaration order.
-API = ("kl_status_string", "kl_word_count", "kl_grandma", "kl_seeds", "kl_params_init",
+API = ("kl_status_string", "kl_word_count", "kl_grandma", "kl_seeds", "kl_maskit",
+       "kl_params_init",
        "kl_decode_words", "kl_workspace_bytes", "kl_eval_words", "kl_render",
        "kl_batch_create", "kl_batch_workspace_bytes", "kl_batch_render", "kl_batch_capture",
        "kl_batch_replay", "kl_batch_destroy", "kl_mlp_forward", "kl_mlp_scratch_bytes",
@@ -144,6 +145,8 @@ def lib():
         L.kl_grandma.restype = I
         L.kl_seeds.argtypes = [P, P]
         L.kl_seeds.restype = I
+        L.kl_maskit.argtypes = [D, D, P, P]
+        L.kl_maskit.restype = I
         L.kl_params_init.argtypes = [ctypes.POINTER(Params), D, D, D, D, U32, U32, U32, D, D, D, D]
         L.kl_params_init.restype = I
         L.kl_decode_words.argtypes = [U32, P, U64, P, P]
@@ -232,6 +235,27 @@ def seeds(gens) -> np.ndarray:
     out = np.zeros(8, dtype=np.float64)
     _check(lib().kl_seeds(g.ctypes.data, out.ctypes.data), "kl_seeds")
     return out
+
+
+def maskit(mu: complex):
+    """Maskit's slice group a(z) = mu + 1/z, b(z) = z + 2 (kl_maskit):
+    (32 generator doubles, 8 seed doubles)."""
+    g = np.zeros(32, dtype=np.float64)
+    s = np.zeros(8, dtype=np.float64)
+    _check(lib().kl_maskit(mu.real, mu.imag, g.ctypes.data, s.ctypes.data), "kl_maskit")
+    return g, s
+
+
+def params_group(gens, seeds8, depth: int, width: int, height: int, window: Sequence[float],
+                 precision: int = FP64, **fields) -> Params:
+    """Parameters for the caller's own generators and seeds (32 and 8
+    doubles), with the same defaults as params_init."""
+    p = params_init(2 + 0j, 2 + 0j, depth, width, height, window, precision, **fields)
+    for k in range(32):
+        p.gens[k] = float(gens[k])
+    for k in range(8):
+        p.seeds[k] = float(seeds8[k])
+    return p
 
 
 def params_init(ta: complex, tb: complex, depth: int, width: int, height: int,

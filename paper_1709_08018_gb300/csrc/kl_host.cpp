@@ -90,29 +90,77 @@ extern "C" int kl_grandma(double ta_re, double ta_im, double tb_re, double tb_im
   return KL_OK;
 }
 
-// Attracting fixed point of each generator.  Fixed points solve
-// r z^2 + (s - p) z - q = 0; since |M'(z)| = 1 / |r z + s|^2 for det 1, the
-// attracting one maximises |r z + s|.  Equal values (a parabolic map, double
-// root) take the "+" root.  r = 0: the finite fixed point q / (s - p), which
-// attracts only if |p| < |s|.
+namespace {
+
+// Attracting fixed point of m.  Fixed points solve r z^2 + (s - p) z - q = 0;
+// since |M'(z)| = 1 / |r z + s|^2 for det 1, the attracting one maximises
+// |r z + s|.  Equal values (a parabolic map, double root) take the "+" root.
+// r = 0: the finite fixed point q / (s - p), which attracts only if |p| < |s|.
+int attracting_fixed_point(const Mobius& m, cplx* out) {
+  cplx z;
+  if (m.r == cplx(0.0, 0.0)) {
+    if (!(std::abs(m.p) < std::abs(m.s))) return KL_EDEGENERATE;
+    z = m.q / (m.s - m.p);
+  } else {
+    const cplx h = m.p - m.s;
+    const cplx root = std::sqrt(h * h + 4.0 * m.q * m.r);
+    const cplx plus = (h + root) / (2.0 * m.r);
+    const cplx minus = (h - root) / (2.0 * m.r);
+    z = std::abs(m.r * minus + m.s) > std::abs(m.r * plus + m.s) ? minus : plus;
+  }
+  if (!finite(z)) return KL_EDEGENERATE;
+  *out = z;
+  return KL_OK;
+}
+
+Mobius compose(const Mobius& x, const Mobius& y) {  // x after y
+  return Mobius{x.p * y.p + x.q * y.r, x.p * y.q + x.q * y.s, x.r * y.p + x.s * y.r,
+                x.r * y.q + x.s * y.s};
+}
+
+}  // namespace
+
 extern "C" int kl_seeds(const double* gens, double* seeds_out) {
   if (!gens || !seeds_out) return KL_EINVAL;
   for (int x = 0; x < 4; ++x) {
-    const Mobius m = get(gens + 8 * x);
     cplx z;
-    if (m.r == cplx(0.0, 0.0)) {
-      if (!(std::abs(m.p) < std::abs(m.s))) return KL_EDEGENERATE;
-      z = m.q / (m.s - m.p);
-    } else {
-      const cplx h = m.p - m.s;
-      const cplx root = std::sqrt(h * h + 4.0 * m.q * m.r);
-      const cplx plus = (h + root) / (2.0 * m.r);
-      const cplx minus = (h - root) / (2.0 * m.r);
-      z = std::abs(m.r * minus + m.s) > std::abs(m.r * plus + m.s) ? minus : plus;
-    }
-    if (!finite(z)) return KL_EDEGENERATE;
+    const int st = attracting_fixed_point(get(gens + 8 * x), &z);
+    if (st != KL_OK) return st;
     seeds_out[2 * x] = z.real();
     seeds_out[2 * x + 1] = z.imag();
+  }
+  return KL_OK;
+}
+
+// Maskit's slice (Mumford-Series-Wright, "Indra's Pearls", ch. 9): a(z) =
+// mu + 1/z and b(z) = z + 2, i.e. a = [[-i mu, -i], [-i, 0]] and
+// b = [[1, 2], [0, 1]], both of determinant one, with tr(a b A B) = -2 for
+// every mu (a once-punctured torus group when discrete).  Seeds: a and A as
+// kl_seeds; b and B fix only infinity, so their words start from the fixed
+// point of the parabolic commutator a b A B instead, a finite point of the
+// limit set (fixed points of parabolic elements are limit points).
+extern "C" int kl_maskit(double mu_re, double mu_im, double* gens_out, double* seeds_out) {
+  if (!gens_out || !seeds_out) return KL_EINVAL;
+  const cplx mu(mu_re, mu_im), I(0.0, 1.0);
+  if (!finite(mu)) return KL_EINVAL;
+  const Mobius a{-I * mu, -I, -I, cplx(0.0, 0.0)};
+  const Mobius b{cplx(1.0, 0.0), cplx(2.0, 0.0), cplx(0.0, 0.0), cplx(1.0, 0.0)};
+  const Mobius all[4] = {a, b, inverse(a), inverse(b)};
+  for (int x = 0; x < 4; ++x) put(all[x], gens_out + 8 * x);
+  for (int x = 0; x < 4; x += 2) {
+    cplx z;
+    const int st = attracting_fixed_point(all[x], &z);
+    if (st != KL_OK) return st;
+    seeds_out[2 * x] = z.real();
+    seeds_out[2 * x + 1] = z.imag();
+  }
+  const Mobius k = compose(compose(a, b), compose(all[2], all[3]));
+  if (k.r == cplx(0.0, 0.0)) return KL_EDEGENERATE;
+  const cplx zk = (k.p - k.s) / (2.0 * k.r);  // the double root of a parabolic map
+  if (!finite(zk)) return KL_EDEGENERATE;
+  for (int x = 1; x < 4; x += 2) {
+    seeds_out[2 * x] = zk.real();
+    seeds_out[2 * x + 1] = zk.imag();
   }
   return KL_OK;
 }

@@ -193,3 +193,14 @@ def test_fsa_from_params_carries_the_group(kl):
     assert np.allclose(list(f.gens)[:32], list(h.gens)[:32], rtol=1e-14, atol=1e-15)
     assert np.allclose(list(f.seeds)[:8], list(h.seeds)[:8], rtol=1e-12, atol=1e-13)
     assert kl.fsa_count(f, 10) == oracle.word_count(10)
+
+
+def test_maskit_agrees_with_the_oracle(kl):
+    for mu in (-0.097 + 1.838j, 2j):
+        g_lib, s_lib = kl.maskit(mu)
+        g_or, s_or = oracle.maskit(mu)
+        # the same maps: the matrices may differ by an overall sign
+        for x in range(4):
+            u, v = g_lib[8 * x: 8 * x + 8], g_or[8 * x: 8 * x + 8]
+            assert np.allclose(u, v, atol=1e-15) or np.allclose(u, -v, atol=1e-15)
+        assert np.allclose(s_lib, s_or, rtol=1e-12, atol=1e-13)

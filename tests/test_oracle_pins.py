@@ -371,3 +371,31 @@ def test_fsa_render_of_the_torus_table_matches_the_scan_and_the_limit_set(ta, tb
     # the same words as the reduced-index render, with the same arithmetic
     ref = oracle.render(g, s, d, window, 64, 48, mode="indexed")
     assert np.array_equal(r.image, ref.image)
+
+
+# --------------------------------------------------------------------------
+# Maskit's slice (the group of the paper's example)
+
+MASKIT_MU = -0.097 + 1.838j
+
+
+@pytest.mark.parametrize("mu", [MASKIT_MU, 2j, 1.91 + 0.05j])
+def test_maskit_group(mu):
+    """a(z) = mu + 1/z and b(z) = z + 2 as det-1 matrices, tr(abAB) = -2,
+    seeds fixed by their letters (b, B: by the commutator), a's attracting."""
+    g, s = oracle.maskit(mu)
+    a, b, A, B = oracle.as_matrices(g)
+    rng = np.random.default_rng(3)
+    for z in rng.normal(size=5) + 1j * rng.normal(size=5):
+        assert np.isclose(mob(a, z), mu + 1 / z) and np.isclose(mob(b, z), z + 2)
+    for m in (a, b, A, B):
+        assert np.isclose(np.linalg.det(m), 1.0, atol=1e-14)
+    assert np.allclose(a @ A, np.eye(2)) and np.allclose(b @ B, np.eye(2))
+    K = a @ b @ A @ B
+    assert abs(np.trace(K) + 2) < 1e-12
+    pts = oracle.as_points(s)
+    assert abs(mob(a, pts[0]) - pts[0]) < 1e-12 and abs(mob(A, pts[2]) - pts[2]) < 1e-12
+    assert pts[1] == pts[3] and abs(mob(K, pts[1]) - pts[1]) < 1e-12
+    # attracting (or neutral, when a is parabolic as at mu = 2i):
+    # |a'(z)| = 1/|r z + s|^2 <= 1 at a's seed
+    assert abs(a[1, 0] * pts[0] + a[1, 1]) >= 1.0 - 1e-12
