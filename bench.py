@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-lod", action="store_true")
     ap.add_argument("--no-tiling", action="store_true")
     ap.add_argument("--no-scan", action="store_true")
+    ap.add_argument("--no-maskit", action="store_true")
     return ap.parse_args()
 
 
@@ -310,6 +311,62 @@ def scan_config(kl, dev, flush):
             "speedup_reduced_index_mixed_over_scan": scan_ms / reduced_mixed_ms}
 
 
+def maskit_config(kl, dev, flush):
+    """The paper's example: Maskit's slice at mu = -0.097 + 1.838i, depth 14,
+    tiling mode (every node of the tree, all lengths 1..14).  The paper's way:
+    scan all 4^k strings of every length k (357,913,940 in all) and filter by
+    the indexed Cayley table (kl_render_fsa, FP64); the indexed way: decode
+    only the 2 (3^14 - 1) reduced words (kl_render, tiling mode, FP64 and
+    mixed).  One period of the limit set, 4096^2."""
+    import torch
+    d, W = 14, 4096
+    window = (-1.0, 1.0, -0.08, 1.92)
+    table = [[0, 1, 2, 3, 4], [1, 1, 2, 0, 4], [2, 1, 2, 3, 0], [3, 0, 2, 3, 4], [4, 1, 0, 3, 4]]
+    gens, seeds8 = kl.maskit(-0.097 + 1.838j)
+    img = torch.empty((W, W), dtype=torch.int32, device=dev)
+    cnt = torch.zeros(kl.KL_N_COUNTERS, dtype=torch.int64, device=dev)
+
+    def timed(fn, K=5):
+        for _ in range(2):
+            fn()
+        ms = []
+        for k in range(K):
+            flush.fill_(k & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize(dev)
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    pk = [kl.params_group(gens, seeds8, k, W, W, window, kl.FP64, accumulate=int(k > 1))
+          for k in range(1, d + 1)]
+    f = kl.fsa_from_params(table, pk[0])
+
+    def scan_all_lengths():
+        for p in pk:
+            kl.render_fsa(f, p, img, cnt)
+    scan_ms = timed(scan_all_lengths)
+    scan_img = img.clone()
+    nodes = 2 * (3 ** d - 1)
+    assert int(cnt[0].item()) + int(cnt[1].item()) == nodes
+    out = {"workload": "Maskit mu = -0.097+1.838i, depth 14, tiling mode (all lengths 1..14), "
+                       "window [-1,1]x[-0.08,1.92], 4096^2",
+           "nodes": nodes, "strings_scanned": sum(4 ** k for k in range(1, d + 1)),
+           "paper_scan_fp64_ms": scan_ms}
+    for name, prec in (("fp64", kl.FP64), ("mixed", kl.MIXED)):
+        p = kl.params_group(gens, seeds8, d, W, W, window, prec, mode=kl.TILING)
+        r = kl.Renderer(p, device=dev)
+        out[f"indexed_{name}_ms"] = timed(lambda: r())
+        if name == "fp64":
+            diff = int((r.image.to(torch.int64) - scan_img.to(torch.int64)).abs().sum().item())
+            out["fp64_images_differ_in_hits"] = diff
+    out["speedup_indexed_fp64_over_scan"] = scan_ms / out["indexed_fp64_ms"]
+    out["speedup_indexed_mixed_over_scan"] = scan_ms / out["indexed_mixed_ms"]
+    return out
+
+
 def batch_sweep(kl, dev, steps: int):
     """The batched sweep: 256 seeded groups, depth 12..18, 1024^2 each, mixed,
     with launch shapes from the autotuner, captured once in a CUDA graph and
@@ -553,6 +610,8 @@ def run_ours(args):
         line["tiling"] = tiling_config(kl, dev, K, flush)
     if not args.no_scan:
         line["paper_scan"] = scan_config(kl, dev, flush)
+    if not args.no_maskit:
+        line["maskit_example"] = maskit_config(kl, dev, flush)
     if not args.no_batch:
         line["batch_sweep"] = batch_sweep(kl, dev, K)
     if not args.no_lod:
