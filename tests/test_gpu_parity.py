@@ -6,7 +6,9 @@ Tolerances (from the arithmetic and the required accuracy):
   - mixed word values: |dz| <= 2e-5 max(1, |z|);
   - FP64 images: exact for every word not within 1e-9 (in z) of a pixel edge,
     edge words only between their candidate pixels (tests/imagecheck.py);
-  - mixed images: occupancy IoU >= 0.999, hits + drops = N_d exactly.
+  - mixed images: exact for every word farther than the mixed tolerance from
+    a pixel edge (edge words among their candidate pixels), occupancy IoU >=
+    0.999, hits + drops = N_d exactly.
 """
 import numpy as np
 import pytest
@@ -166,7 +168,15 @@ def test_render_fp64_image(kl, name, d, window, W, H, fields):
 
 @pytest.mark.parametrize("name,d,window,W,H,fields", IMAGE_CASES)
 def test_render_mixed_image(kl, name, d, window, W, H, fields):
-    img, cnt, ref = render_both(kl, GROUPS[name], d, window, W, H, kl.MIXED, **fields)
+    # every word farther than the mixed tolerance, 2e-5 max(1, |z|), from a
+    # pixel edge must land in the oracle's pixel; the rest among their
+    # candidate pixels
+    zmax = max(1.0, max(abs(complex(x, y)) for x in window[:2] for y in window[2:]))
+    img, cnt, ref = render_both(kl, GROUPS[name], d, window, W, H, kl.MIXED,
+                                eta_z=TOL32 * zmax, **fields)
+    sx = max(W / (window[1] - window[0]), H / (window[3] - window[2]))
+    tol = TOL32 * zmax * sx
+    check_fp64_image(img, ref, tol, max_edge_frac=4.0 * tol + 1e-2)
     assert iou(img, ref.image) >= 0.999
     assert int(cnt[0]) == int(img.astype(np.int64).sum())
     assert abs(int(cnt[0]) - ref.in_window) <= max(10, 1e-4 * ref.in_window)
