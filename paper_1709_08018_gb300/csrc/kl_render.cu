@@ -140,6 +140,49 @@ __global__ void render_single_letter_kernel(Group G, View V, uint32_t* img,
   }
 }
 
+// Tiling mode, the short lengths 1..k0: one thread per node, its word
+// decoded from the node's index within its length and evaluated point by
+// point from the inside out (the seed of w_k, then the maps of w_k, ..., w_1),
+// in FP64 with a refined reciprocal instead of division.  These lengths hold
+// few words (2 (3^k0 - 1)), so one launch for all of them replaces a render
+// per length, whose launches would cost more than its words.
+constexpr uint32_t kShortTiling = 9;
+
+__global__ void tiling_short_kernel(Group G, View V, uint32_t k0, int mixed,
+                                    uint32_t* __restrict__ img, unsigned long long* counters) {
+  uint64_t total = 0, nk = 4;
+  for (uint32_t k = 1; k <= k0; ++k, nk *= 3) total += nk;
+  uint32_t in_window = 0, words = 0, atomics = 0;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t r = i, n = 4;
+    uint32_t k = 1;
+    while (r >= n) {
+      r -= n;
+      n *= 3;
+      ++k;
+    }
+    int w[kShortTiling];
+    decode_word(r, (int)k, w);
+    dc z = {G.seed[2 * w[k - 1]], G.seed[2 * w[k - 1] + 1]};
+    for (int j = (int)k - 1; j >= 0; --j) {
+      const double* M = G.g + 8 * w[j];
+      const dc num = {M[0] * z.re - M[1] * z.im + M[2], M[0] * z.im + M[1] * z.re + M[3]};
+      const dc den = {M[4] * z.re - M[5] * z.im + M[6], M[4] * z.im + M[5] * z.re + M[7]};
+      const double rc = rcp64(den.re * den.re + den.im * den.im);
+      z = {(num.re * den.re + num.im * den.im) * rc, (num.im * den.re - num.re * den.im) * rc};
+    }
+    const int pix = pixel64((z.re - V.x0) * V.sx, (V.y1 - z.im) * V.sy, V);
+    ++words;
+    if (pix >= 0) {
+      atomicAdd(img + pix, 1u);
+      ++in_window;
+      ++atomics;
+    }
+  }
+  publish_counts(in_window, words, mixed ? words : 0u, atomics, counters);
+}
+
 __global__ void eval_kernel(const uint64_t* __restrict__ idx, uint64_t n, uint64_t N, Group G,
                             Plan L, View V, int mixed, Tables T, double* __restrict__ out) {
   for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n;
@@ -382,15 +425,28 @@ extern "C" int kl_render(const kl_params* p, uint32_t* d_image, uint64_t* d_coun
   cudaStream_t s = (cudaStream_t)stream;
   unsigned long long* cnt = (unsigned long long*)d_counters;
   if (p->mode == KL_TILING) {
-    // the longest words first (they clear the image unless accumulating),
-    // then every shorter length added in
-    for (uint32_t k = p->depth; k >= 1; --k) {
+    // the lengths above kShortTiling as renders of their own, the longest
+    // first (it clears the image unless accumulating), each next one added
+    // in; then all the short lengths in one launch
+    const uint32_t k0 = p->depth < kShortTiling ? p->depth : kShortTiling;
+    for (uint32_t k = p->depth; k > k0; --k) {
       kl_params q = length_params(p, k);
       q.accumulate = k == p->depth ? p->accumulate : 1u;
       st = render_length(&q, d_image, cnt, d_workspace, s, k == p->depth);
       if (st != KL_OK) return st;
     }
-    return KL_OK;
+    if (p->depth <= k0 && !p->accumulate) {
+      if (cudaMemsetAsync(d_image, 0, (size_t)p->width * p->height * sizeof(uint32_t), s) !=
+          cudaSuccess)
+        return KL_ECUDA;
+      if (cnt && cudaMemsetAsync(cnt, 0, KL_N_COUNTERS * sizeof(uint64_t), s) != cudaSuccess)
+        return KL_ECUDA;
+    }
+    const int sms = sm_count();
+    if (sms <= 0) return KL_ECUDA;
+    tiling_short_kernel<<<sms * 4, 256, 0, s>>>(make_group(p), make_view(p), k0,
+                                                p->precision == KL_MIXED, d_image, cnt);
+    return check_launch();
   }
   return render_length(p, d_image, cnt, d_workspace, s, true);
 }
