@@ -299,9 +299,11 @@ KL_API size_t kl_lod_label_bytes(const kl_params* p, uint32_t lo, uint32_t hi);
 /* Exact render of *p (into d_image, d_counters as kl_render, prefix length
  * hi) and, from the same pass, the labels (uint8) and the network input
  * features (8 FP32 per node) of every node of levels lo..hi.  Features: the
- * prefix matrix divided by the principal square root of its determinant,
- * negated if needed so that Re tr > 0, then sign(v) log(1 + |v|) of the real
- * and imaginary parts of p, q, r, s. */
+ * prefix matrix (a product of generators of determinant one, so already of
+ * determinant one up to rounding: the division by the principal square root
+ * of its determinant changes no feature and is left out), negated if needed
+ * so that Re tr > 0, then sign(v) log(1 + |v|) of the real and imaginary
+ * parts of p, q, r, s. */
 KL_API int kl_lod_labels(const kl_params* p, uint32_t lo, uint32_t hi, float extent,
                          uint32_t* d_image, uint64_t* d_counters, float* d_features,
                          uint8_t* d_labels, void* d_workspace, size_t workspace_bytes,

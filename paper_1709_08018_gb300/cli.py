@@ -4,6 +4,7 @@
       [--repeat N] [--out image.npy]
   python -m paper_1709_08018_gb300.cli --batch 32 [--repeat N]
   python -m paper_1709_08018_gb300.cli --lod [--train-groups 4] [--train-steps 300] [--repeat N]
+  python -m paper_1709_08018_gb300.cli --scan [--depth 14] [--repeat N]
 
 Prints the counters and the device time of the last render.  With --repeat N
 the render runs N times (the first ones serve as warm-up for profilers).
@@ -43,11 +44,15 @@ def main(argv=None):
     ap.add_argument("--lod", action="store_true")
     ap.add_argument("--train-groups", type=int, default=4)
     ap.add_argument("--train-steps", type=int, default=300)
+    ap.add_argument("--scan", action="store_true")
+    ap.add_argument("--tiling", action="store_true")
     a = ap.parse_args(argv)
     if a.batch:
         return run_batch(a, kl, klsynth, torch)
     if a.lod:
         return run_lod(a, kl, klsynth, torch)
+    if a.scan:
+        return run_scan(a, kl, klsynth, torch)
     c = named[a.config]
     ta = a.ta if a.ta is not None else c.group.ta
     tb = a.tb if a.tb is not None else c.group.tb
@@ -55,7 +60,7 @@ def main(argv=None):
     W = H = a.size or c.width
     p = kl.params_init(ta, tb, depth, W, H, c.window,
                        kl.MIXED if a.precision == "mixed" else kl.FP64,
-                       prefix_len=a.prefix_len)
+                       prefix_len=a.prefix_len, mode=kl.TILING if a.tiling else kl.LIMIT_SET)
     r = kl.Renderer(p)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(a.repeat):
@@ -87,6 +92,28 @@ def run_batch(a, kl, klsynth, torch):
     words = sum(c.n_words for c in cfgs)
     print(f"batch of {a.batch} groups: words {words}, in-window {cnt[0]}, dropped {cnt[1]}, "
           f"fp64 words {cnt[2]}, atomics {cnt[3]}, {e0.elapsed_time(e1):.3f} ms")
+
+
+def run_scan(a, kl, klsynth, torch):
+    """The paper's scan (kl_render_fsa) of the gasket group with the torus
+    table: all 4^d strings of depth d (default 14), FP64, 4096^2."""
+    d = a.depth or 14
+    W = a.size or 4096
+    table = [[0, 1, 2, 3, 4], [1, 1, 2, 0, 4], [2, 1, 2, 3, 0], [3, 0, 2, 3, 4], [4, 1, 0, 3, 4]]
+    p = kl.params_init(klsynth.GASKET.ta, klsynth.GASKET.tb, d, W, W, (-1.5, 1.5, -1.5, 1.5),
+                       kl.FP64)
+    f = kl.fsa_from_params(table, p)
+    img = torch.empty((W, W), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(kl.KL_N_COUNTERS, dtype=torch.int64, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(a.repeat):
+        e0.record()
+        kl.render_fsa(f, p, img, cnt)
+        e1.record()
+    torch.cuda.synchronize()
+    c = cnt.cpu().tolist()
+    print(f"scan d={d}: strings {4 ** d}, kept {c[2]}, in-window {c[0]}, "
+          f"{e0.elapsed_time(e1):.3f} ms")
 
 
 def run_lod(a, kl, klsynth, torch):

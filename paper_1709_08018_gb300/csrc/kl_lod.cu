@@ -80,27 +80,18 @@ __device__ M2 node_matrix(const Group& G, int k, uint32_t slot, uint32_t nk) {
 // The 8 features: P / sqrt(det P) (principal root), negated if needed so that
 // Re tr > 0 (a zero trace takes the sign of the first nonzero entry), then
 // sign(v) log(1 + |v|) for each real part and imaginary part.
-__device__ void node_features(M2 P, float* f) {
-  // P / k with k the principal square root of d = det P: |k|^2 = |d|, so
-  // 1 / k = conj(k) / |d| (two square roots and two refined reciprocals;
-  // |d| is near 1 for these products, so no scaling against overflow)
-  const dc d = mdet(P);
-  const double r = sqrt(d.re * d.re + d.im * d.im);
-  if (r > 0.0) {
-    const double t = sqrt(0.5 * (r + fabs(d.re)));
-    const double h = 0.5 * rcp64(t);
-    const dc k = d.re >= 0.0 ? dc{t, d.im * h} : dc{fabs(d.im) * h, copysign(t, d.im)};
-    const double ir = rcp64(r);
-    const dc ik = {k.re * ir, -k.im * ir};
-    P.p = cmul(P.p, ik); P.q = cmul(P.q, ik); P.r = cmul(P.r, ik); P.s = cmul(P.s, ik);
-  }
-  double v[8];
-  from_m2(P, v);
-  double lead = v[0] + v[6];
+__device__ void node_features(const M2& P, float* f) {
+  // A node matrix is a product of generators of determinant one, so its own
+  // determinant is one up to rounding (relative 1e-15 at these depths) and
+  // dividing by its square root would change no feature at FP32 (let alone
+  // at the network's BF16): the features are taken from P as it is, and the
+  // FP64 pipe, the scarce one on this GPU, is spared that division.
+  double lead = P.p.re + P.s.re;
+  const double v[8] = {P.p.re, P.p.im, P.q.re, P.q.im, P.r.re, P.r.im, P.s.re, P.s.im};
   for (int i = 0; i < 8 && lead == 0.0; ++i) lead = v[i];
-  const double sgn = lead < 0.0 ? -1.0 : 1.0;
+  const bool neg = lead < 0.0;
   for (int i = 0; i < 8; ++i) {
-    const float a = (float)(sgn * v[i]);
+    const float a = neg ? -(float)v[i] : (float)v[i];
     f[i] = copysignf(log1pf(fabsf(a)), a);
   }
 }
@@ -348,7 +339,12 @@ __global__ void __launch_bounds__(kLodThreads) expand_kernel(
       if (prune) {
         for (int e = 0; e < kReps; ++e) {
           const double2 v = vstar[(e * 4 + x) * (hi + 1) + k];
-          const dc z = mobius(P, {v.x, v.y});
+          // P(v) with a refined reciprocal instead of a division
+          const dc num = cadd(cmul(P.p, {v.x, v.y}), P.q);
+          const dc den = cadd(cmul(P.r, {v.x, v.y}), P.s);
+          const double rc = rcp64(den.re * den.re + den.im * den.im);
+          const dc z = {(num.re * den.re + num.im * den.im) * rc,
+                        (num.im * den.re - num.re * den.im) * rc};
           const int pe = guarded_pixel((z.re - V.x0) * V.sx, (V.y1 - z.im) * V.sy, V, edge);
           if (e == 0) pix = pe;
           if (pe == kNearEdge || pe != pix) prune = false;
