@@ -328,6 +328,7 @@ __global__ void __launch_bounds__(kLodThreads) expand_kernel(
     } else {
       y = valid ? (float)labels[a.slot] : 0.0f;  // the level's true labels
     }
+    int action = 0;  // 1: expand to the three children, 2: defer to the exact render
     if (valid) {
       ++visited;
       const M2 P = to_m2(a.m);
@@ -359,21 +360,40 @@ __global__ void __launch_bounds__(kLodThreads) expand_kernel(
           drop += words_sub;
         }
       } else if (k < hi) {
-        const uint32_t base = atomicAdd(out_count, 3u);
-        const uint32_t r = a.slot % nk;
-        for (int q = 0; q < 3; ++q) {
-          const int yl = allowed_letter(q, (x + 2) & 3);
-          const int rk = x - (x > ((yl + 2) & 3) ? 1 : 0);
-          Active b;
-          from_m2(mmul(P, load_gen(G, yl)), b.m);
-          b.slot = (uint32_t)yl * 3u * nk + (uint32_t)rk * nk + r;
-          b.pad[0] = b.pad[1] = b.pad[2] = 0;
-          out[base + q] = b;
-        }
+        action = 1;
       } else {
         ++defer;
-        deferred[atomicAdd(deferred_count, 1u)] = a.slot;
+        action = 2;
       }
+    }
+    // output slots, one atomic per warp and list (all lanes take part: the
+    // tile loop is uniform over the warp)
+    const unsigned be = __ballot_sync(0xFFFFFFFFu, action == 1);
+    const unsigned bd = __ballot_sync(0xFFFFFFFFu, action == 2);
+    uint32_t base_e = 0, base_d = 0;
+    if (lane == 0) {
+      if (be) base_e = atomicAdd(out_count, 3u * (uint32_t)__popc(be));
+      if (bd) base_d = atomicAdd(deferred_count, (uint32_t)__popc(bd));
+    }
+    base_e = __shfl_sync(0xFFFFFFFFu, base_e, 0);
+    base_d = __shfl_sync(0xFFFFFFFFu, base_d, 0);
+    const unsigned lt = (1u << lane) - 1u;
+    if (action == 1) {
+      const M2 P = to_m2(a.m);
+      const int x = (int)(a.slot / nk);
+      const uint32_t base = base_e + 3u * (uint32_t)__popc(be & lt);
+      const uint32_t r = a.slot % nk;
+      for (int q = 0; q < 3; ++q) {
+        const int yl = allowed_letter(q, (x + 2) & 3);
+        const int rk = x - (x > ((yl + 2) & 3) ? 1 : 0);
+        Active b;
+        from_m2(mmul(P, load_gen(G, yl)), b.m);
+        b.slot = (uint32_t)yl * 3u * nk + (uint32_t)rk * nk + r;
+        b.pad[0] = b.pad[1] = b.pad[2] = 0;
+        out[base + q] = b;
+      }
+    } else if (action == 2) {
+      deferred[base_d + (uint32_t)__popc(bd & lt)] = a.slot;
     }
     __syncwarp();
   }
