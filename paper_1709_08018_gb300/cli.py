@@ -3,7 +3,8 @@
   python -m paper_1709_08018_gb300.cli --config gasket-d18-4096 --precision mixed \
       [--repeat N] [--out image.npy]
   python -m paper_1709_08018_gb300.cli --batch 32 [--repeat N]
-  python -m paper_1709_08018_gb300.cli --lod [--train-groups 4] [--train-steps 300] [--repeat N]
+  python -m paper_1709_08018_gb300.cli --lod [--train-groups 4] [--train-steps 300]
+      [--per-level 20000] [--held-out 1] [--repeat N]
   python -m paper_1709_08018_gb300.cli --scan [--depth 14] [--repeat N]
 
 Prints the counters and the device time of the last render.  With --repeat N
@@ -44,6 +45,8 @@ def main(argv=None):
     ap.add_argument("--lod", action="store_true")
     ap.add_argument("--train-groups", type=int, default=4)
     ap.add_argument("--train-steps", type=int, default=300)
+    ap.add_argument("--per-level", type=int, default=20_000)
+    ap.add_argument("--held-out", type=int, default=1)
     ap.add_argument("--scan", action="store_true")
     ap.add_argument("--tiling", action="store_true")
     a = ap.parse_args(argv)
@@ -117,26 +120,30 @@ def run_scan(a, kl, klsynth, torch):
 
 
 def run_lod(a, kl, klsynth, torch):
+    """Train the pruning network on --train-groups groups (--per-level nodes
+    per level, --train-steps steps; bench.py's setting is 64, 60000, 10000)
+    and run the pruned render (margin -0.8, edge 1/512 px) of the first
+    --held-out held-out groups, --repeat times each."""
     from paper_1709_08018_gb300 import lod
     d, size, lo, hi, extent = 22, 8192, 8, 15, 1.0 / 32
     W = (-2.0, 2.0, -2.0, 2.0)
     mk = lambda g: kl.params_init(g.ta, g.tb, d, size, size, W, kl.MIXED)
     tr = [mk(g) for g, _ in klsynth.draw_groups(klsynth.LOD_TRAIN_SEED, a.train_groups)]
-    x, t = lod.make_dataset(tr, lo, hi, per_level=20_000, seed=3, extent=extent)
+    x, t = lod.make_dataset(tr, lo, hi, per_level=a.per_level, seed=3, extent=extent)
     mlp, losses = lod.train(x, t, steps=a.train_steps, batch=16384, lr=2e-3, seed=5, under=32.0)
-    g = klsynth.draw_groups(klsynth.LOD_HELDOUT_SEED, 1)[0][0]
-    L = kl.LodRenderer(mk(g), lo, hi)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(a.repeat):
-        e0.record()
-        img, cnt, st = L(mlp, -0.8, 1.0 / 512)
-        e1.record()
-    torch.cuda.synchronize()
-    st, cnt = st.cpu().tolist(), cnt.cpu().tolist()
-    print(f"lod d={d} {size}^2 levels {lo}..{hi}: loss {losses[0]:.3g} -> {losses[-1]:.3g}, "
-          f"nodes {st[0]}, pruned {st[1]}, deferred {st[2]}, words {cnt[0] + cnt[1]}, "
-          f"{e0.elapsed_time(e1):.3f} ms")
-
+    for g, _ in klsynth.draw_groups(klsynth.LOD_HELDOUT_SEED, a.held_out):
+        L = kl.LodRenderer(mk(g), lo, hi)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(a.repeat):
+            e0.record()
+            img, cnt, st = L(mlp, -0.8, 1.0 / 512)
+            e1.record()
+        torch.cuda.synchronize()
+        st, cnt = st.cpu().tolist(), cnt.cpu().tolist()
+        print(f"lod d={d} {size}^2 levels {lo}..{hi}: loss {losses[0]:.3g} -> {losses[-1]:.3g}, "
+              f"nodes {st[0]}, pruned {st[1]}, deferred {st[2]}, words {cnt[0] + cnt[1]}, "
+              f"{e0.elapsed_time(e1):.3f} ms")
+        del L
 
 if __name__ == "__main__":
     main()
