@@ -18,6 +18,9 @@ Parity status per function (what pins it is in ``tests/test_oracle_pins.py``):
   fsa_count,     pinned: the paper's scan written out in Python (set and
   render_fsa     image), the closed-form counts 4 3^(d-1) (once-punctured
                  torus table) and 3 2^(d-1) (Klein four-group table)
+  cusp_seeds,    pinned: each commutator permutation has trace -2 and fixes
+  render_multiseed its point; consecutive points are images under the
+                 generators (conjugation); brute-force scan with fixed seeds
   mlp (numpy)    pinned: central finite differences, closed-form tiny nets
 """
 from .oracle import *  # noqa: F401,F403

@@ -596,3 +596,33 @@ OR_EXPORT int or_maskit(double mu_re, double mu_im, double* gens, double* seeds)
   seeds[3] = seeds[7] = zk.im;
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Seeds for multi-seed feeding (the paper's loop over a list of fixed       */
+/* points, Sec. "Implementation").  The list it cites is not in the paper;   */
+/* this oracle takes the attracting fixed points of a, b, A, B and the fixed */
+/* points of the four cyclic permutations of the commutator, abAB, bABa,     */
+/* ABab and BabA: parabolic maps of a once-punctured torus group, whose      */
+/* fixed points are the cusps of the limit set.  out: 8 points (16 doubles). */
+
+static mat2 word_matrix4(const mat2* g, const int* w) {
+  mat2 m = g[w[0]];
+  for (int k = 1; k < 4; ++k) m = mat_mul(m, g[w[k]]);
+  return m;
+}
+
+OR_EXPORT int or_cusp_seeds(const double* gens, double* out) {
+  if (or_seeds(gens, out) != 0) return -1;
+  mat2 g[4];
+  for (int x = 0; x < 4; ++x) g[x] = mat_load(gens + 8 * x);
+  /* a=0, b=1, A=2, B=3: abAB and its cyclic permutations */
+  static const int perms[4][4] = {{0, 1, 2, 3}, {1, 2, 3, 0}, {2, 3, 0, 1}, {3, 0, 1, 2}};
+  for (int c = 0; c < 4; ++c) {
+    mat2 k = word_matrix4(g, perms[c]);
+    if (k.r.re == 0.0 && k.r.im == 0.0) return -1;
+    cx z = cx_div(cx_sub(k.p, k.s), cx_scale(k.r, 2.0)); /* double root of a parabolic map */
+    out[8 + 2 * c] = z.re;
+    out[8 + 2 * c + 1] = z.im;
+  }
+  return 0;
+}

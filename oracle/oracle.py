@@ -35,6 +35,8 @@ def lib():
         L.or_render_indexed.argtypes = [P, P, I, P, I, I, U64, U64, P, P, D, P, P, U64, P]
         L.or_render_indexed.restype = I
         L.or_render_tree.argtypes = [P, P, I, P, I, I, I, I, I, P, P, D, P, P, U64, P]
+        L.or_cusp_seeds.argtypes = [P, P]
+        L.or_cusp_seeds.restype = I
         L.or_maskit.argtypes = [D, D, P, P]
         L.or_maskit.restype = I
         L.or_fsa_count.argtypes = [I, P, I, P]
@@ -240,3 +242,35 @@ def maskit(mu: complex) -> Tuple[np.ndarray, np.ndarray]:
     if lib().or_maskit(mu.real, mu.imag, _ptr(g), _ptr(s)) != 0:
         raise ValueError("degenerate Maskit group")
     return g, s
+
+
+# ---------------------------------------------------------------------------
+# multi-seed feeding (the paper's loop over a list of fixed points)
+
+def cusp_seeds(gens) -> np.ndarray:
+    """8 seed points (16 doubles): the attracting fixed points of a, b, A, B,
+    then the fixed points of abAB, bABa, ABab, BabA (see or_cusp_seeds)."""
+    g = np.ascontiguousarray(gens, dtype=np.float64)
+    out = np.zeros(16)
+    if lib().or_cusp_seeds(_ptr(g), _ptr(out)) != 0:
+        raise ValueError("degenerate group")
+    return out
+
+
+def render_multiseed(gens, points, d: int, window: Sequence[float], width: int, height: int,
+                     threads: Optional[int] = None, eta: float = 0.0,
+                     edge_cap: int = 1 << 16) -> Render:
+    """Every reduced word of length d drawn once per seed point: the word's
+    maps applied to each point of the list in turn, whatever its first
+    letter (the paper's loop over fixed points).  points: k complex."""
+    img = np.zeros((height, width), dtype=np.uint32)
+    parts = []
+    for z in points:
+        s8 = np.array([complex(z).real, complex(z).imag] * 4, dtype=np.float64)
+        r = render(gens, s8, d, window, width, height, threads=threads, eta=eta, edge_cap=edge_cap)
+        img += r.image
+        parts.append(r)
+    return Render(img, sum(r.in_window for r in parts), sum(r.dropped for r in parts),
+                  np.concatenate([r.edge_idx for r in parts]),
+                  np.concatenate([r.edge_uv for r in parts]).reshape(-1, 2),
+                  sum(r.edge_total for r in parts))

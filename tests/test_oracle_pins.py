@@ -399,3 +399,44 @@ def test_maskit_group(mu):
     # attracting (or neutral, when a is parabolic as at mu = 2i):
     # |a'(z)| = 1/|r z + s|^2 <= 1 at a's seed
     assert abs(a[1, 0] * pts[0] + a[1, 1]) >= 1.0 - 1e-12
+
+
+# --------------------------------------------------------------------------
+# multi-seed feeding
+
+@pytest.mark.parametrize("ta,tb", [GASKET, NEAR_CUSP, FUCHSIAN] + TRACE_PAIRS[3:6])
+def test_cusp_seeds(ta, tb):
+    """The commutator's cyclic permutations are parabolic and fix their
+    points; each permutation is the previous one conjugated by its first
+    letter, so each point is the previous one's image under that letter's
+    inverse: bABa = A (abAB) a fixes A(z0), ABab fixes B(z1), BabA fixes a(z2)."""
+    G, seeds, g, s = mats(ta, tb)
+    out = oracle.cusp_seeds(g)
+    pts = [complex(out[2 * i], out[2 * i + 1]) for i in range(8)]
+    assert np.allclose(pts[:4], seeds, rtol=1e-14, atol=1e-15)
+    a, b, A, B = G
+    words = [a @ b @ A @ B, b @ A @ B @ a, A @ B @ a @ b, B @ a @ b @ A]
+    for K, z in zip(words, pts[4:]):
+        assert abs(np.trace(K) + 2) < 1e-10 * max(1.0, np.abs(K).max() ** 2)
+        assert abs(mob(K, z) - z) < 1e-7 * max(1.0, abs(z))
+    for prev, nxt, inv in [(pts[4], pts[5], A), (pts[5], pts[6], B), (pts[6], pts[7], a)]:
+        assert abs(mob(inv, prev) - nxt) < 1e-7 * max(1.0, abs(nxt))
+
+
+@pytest.mark.parametrize("ta,tb,d", [(*GASKET, 5), (*NEAR_CUSP, 5)])
+def test_multiseed_render_matches_the_scan(ta, tb, d):
+    """Each reduced word drawn once per point of the list, its maps applied
+    to that point (not to its first letter's seed)."""
+    G, seeds, g, s = mats(ta, tb)
+    out = oracle.cusp_seeds(g)
+    pts = [complex(out[2 * i], out[2 * i + 1]) for i in range(8)]
+    window = (-1.37, 1.41, -1.29, 1.33)
+    img = np.zeros((48, 64), dtype=np.int64)
+    dropped = 0
+    for z in pts:
+        i, dr = brute_render(G, [z] * 4, d, window, 64, 48)
+        img += i
+        dropped += dr
+    r = oracle.render_multiseed(g, pts, d, window, 64, 48, threads=2)
+    assert np.array_equal(r.image.astype(np.int64), img)
+    assert r.dropped == dropped and r.in_window + r.dropped == 8 * oracle.word_count(d)
