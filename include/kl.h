@@ -148,6 +148,17 @@ KL_API int kl_seeds(const double* gens, double* seeds_out);
  * finite. */
 KL_API int kl_maskit(double mu_re, double mu_im, double* gens_out, double* seeds_out);
 
+/* Seed list for multi-seed feeding (Sec. "Implementation" loops the scan
+ * over a list of fixed points that the paper does not print): 8 points into
+ * seeds_out (16 doubles): the attracting fixed points of a, b, A, B (as
+ * kl_seeds), then the fixed points of the commutator a b A B and of its
+ * cyclic permutations b A B a, A B a b, B a b A, parabolic maps whose fixed
+ * points are the cusps of the limit set.  A multi-seed render draws every
+ * word once per point: kl_render with all four seeds set to that point,
+ * accumulating over the list.  Host only.  KL_EDEGENERATE if a point is not
+ * finite. */
+KL_API int kl_cusp_seeds(const double* gens, double* seeds_out);
+
 /* Fill *p: generators and seeds from the traces, the given depth, image and
  * window, and defaults for the rest (precision KL_FP64, renorm_every 8,
  * parabolic_tol 1e-6, prefix_len 0, accumulate 0).  Host only. */

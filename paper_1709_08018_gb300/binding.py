@@ -14,6 +14,7 @@ KL_CNT_IN_WINDOW, KL_CNT_DROPPED, KL_CNT_FP64_WORDS, KL_CNT_ATOMICS, KL_N_COUNTE
 
 # Every function include/kl.h declares, in declaration order.
 API = ("kl_status_string", "kl_word_count", "kl_grandma", "kl_seeds", "kl_maskit",
+       "kl_cusp_seeds",
        "kl_params_init",
        "kl_decode_words", "kl_workspace_bytes", "kl_eval_words", "kl_render",
        "kl_batch_create", "kl_batch_workspace_bytes", "kl_batch_render", "kl_batch_capture",
@@ -147,6 +148,8 @@ def lib():
         L.kl_seeds.restype = I
         L.kl_maskit.argtypes = [D, D, P, P]
         L.kl_maskit.restype = I
+        L.kl_cusp_seeds.argtypes = [P, P]
+        L.kl_cusp_seeds.restype = I
         L.kl_params_init.argtypes = [ctypes.POINTER(Params), D, D, D, D, U32, U32, U32, D, D, D, D]
         L.kl_params_init.restype = I
         L.kl_decode_words.argtypes = [U32, P, U64, P, P]
@@ -244,6 +247,32 @@ def maskit(mu: complex):
     s = np.zeros(8, dtype=np.float64)
     _check(lib().kl_maskit(mu.real, mu.imag, g.ctypes.data, s.ctypes.data), "kl_maskit")
     return g, s
+
+
+def cusp_seeds(gens) -> np.ndarray:
+    """kl_cusp_seeds: 8 seed points (16 doubles) for multi-seed feeding."""
+    g = np.ascontiguousarray(gens, dtype=np.float64)
+    out = np.zeros(16, dtype=np.float64)
+    _check(lib().kl_cusp_seeds(g.ctypes.data, out.ctypes.data), "kl_cusp_seeds")
+    return out
+
+
+def render_multiseed(p: "Params", points, image=None, counters=None, workspace=None,
+                     stream=None, device="cuda"):
+    """Multi-seed feeding: every word of p drawn once per seed point, i.e.
+    one kl_render per point with all four seeds set to it, accumulated into
+    one image and one set of counters.  points: complex seed points."""
+    q = Params.from_buffer_copy(p)
+    workspace = _workspace(q, device if image is None else image.device, workspace)
+    out = None
+    for n, z in enumerate(points):
+        for x in range(4):
+            q.seeds[2 * x] = complex(z).real
+            q.seeds[2 * x + 1] = complex(z).imag
+        q.accumulate = p.accumulate if n == 0 else 1
+        out = render(q, image, counters, workspace, stream, device)
+        image, counters = out
+    return out
 
 
 def params_group(gens, seeds8, depth: int, width: int, height: int, window: Sequence[float],

@@ -189,3 +189,26 @@ extern "C" int kl_params_init(kl_params* p, double ta_re, double ta_im, double t
   p->mode = KL_LIMIT_SET;
   return KL_OK;
 }
+
+// Seed list for multi-seed feeding: the attracting fixed points of a, b, A, B
+// (as kl_seeds), then the fixed points of the commutator a b A B and of its
+// cyclic permutations b A B a, A B a b, B a b A.  Those four are parabolic
+// (trace -2), so each fixed point is the double root (p - s) / (2 r).
+extern "C" int kl_cusp_seeds(const double* gens, double* seeds_out) {
+  if (!gens || !seeds_out) return KL_EINVAL;
+  int st = kl_seeds(gens, seeds_out);
+  if (st != KL_OK) return st;
+  Mobius m[4];
+  for (int x = 0; x < 4; ++x) m[x] = get(gens + 8 * x);
+  for (int c = 0; c < 4; ++c) {
+    // the word of letters c, c+1, c+2, c+3 (mod 4) of a b A B
+    Mobius k = m[c];
+    for (int j = 1; j < 4; ++j) k = compose(k, m[(c + j) & 3]);
+    if (k.r == cplx(0.0, 0.0)) return KL_EDEGENERATE;
+    const cplx z = (k.p - k.s) / (2.0 * k.r);
+    if (!finite(z)) return KL_EDEGENERATE;
+    seeds_out[8 + 2 * c] = z.real();
+    seeds_out[8 + 2 * c + 1] = z.imag();
+  }
+  return KL_OK;
+}

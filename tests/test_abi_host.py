@@ -204,3 +204,10 @@ def test_maskit_agrees_with_the_oracle(kl):
             u, v = g_lib[8 * x: 8 * x + 8], g_or[8 * x: 8 * x + 8]
             assert np.allclose(u, v, atol=1e-15) or np.allclose(u, -v, atol=1e-15)
         assert np.allclose(s_lib, s_or, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("ta,tb", TRACES[:6])
+def test_cusp_seeds_agree_with_the_oracle(kl, ta, tb):
+    g = kl.grandma(ta, tb)
+    assert np.allclose(kl.cusp_seeds(g), oracle.cusp_seeds(oracle.grandma(ta, tb)),
+                       rtol=1e-9, atol=1e-12)

@@ -1,0 +1,51 @@
+"""Multi-seed feeding (the paper's loop over a list of fixed points): every
+reduced word drawn once per seed point of kl_cusp_seeds, against the
+oracle's multi-seed render of the oracle's own seed list.  FP64 exact up to
+edge words; mixed exact for words farther than the mixed tolerance from a
+pixel edge; every word counted once per point."""
+import numpy as np
+import pytest
+
+import klsynth
+import oracle
+from imagecheck import check_fp64_image
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-9, "mixed": 2e-5}
+
+
+@pytest.fixture(scope="module")
+def kl():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("no CUDA device for a gpu-marked test")
+    from paper_1709_08018_gb300 import build
+    build.build()
+    import paper_1709_08018_gb300 as kl
+    return kl
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("group,d,W,window", [
+    (klsynth.GASKET, 10, 1024, (-1.5, 1.5, -1.5, 1.5)),
+    (klsynth.NEAR_CUSP, 11, 768, (-2.0, 2.0, -2.0, 2.0)),
+])
+def test_multiseed_render(kl, prec, group, d, W, window):
+    p = kl.params_init(group.ta, group.tb, d, W, W, window,
+                       kl.FP64 if prec == "fp64" else kl.MIXED)
+    s16 = kl.cusp_seeds(np.array(list(p.gens)))
+    points = [complex(s16[2 * i], s16[2 * i + 1]) for i in range(8)]
+    img, cnt = kl.render_multiseed(p, points)
+    img = img.cpu().numpy().view(np.uint32)
+    cnt = cnt.cpu().numpy()
+    assert int(cnt[0]) + int(cnt[1]) == 8 * oracle.word_count(d)
+    assert int(cnt[0]) == int(img.astype(np.int64).sum())
+    g, _ = oracle.group(group.ta, group.tb)
+    o16 = oracle.cusp_seeds(g)
+    opts = [complex(o16[2 * i], o16[2 * i + 1]) for i in range(8)]
+    sx = max(W / (window[1] - window[0]), W / (window[3] - window[2]))
+    zmax = max(1.0, max(abs(complex(x, y)) for x in window[:2] for y in window[2:]))
+    tol = TOL[prec] * zmax * sx
+    ref = oracle.render_multiseed(g, opts, d, window, W, W, eta=tol, edge_cap=1 << 22)
+    check_fp64_image(img, ref, tol, max_edge_frac=4.0 * tol + 1e-2)
