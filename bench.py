@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-tiling", action="store_true")
     ap.add_argument("--no-scan", action="store_true")
     ap.add_argument("--no-maskit", action="store_true")
+    ap.add_argument("--no-multiseed", action="store_true")
     return ap.parse_args()
 
 
@@ -367,6 +368,49 @@ def maskit_config(kl, dev, flush):
     return out
 
 
+def multiseed_config(kl, dev, flush):
+    """Multi-seed feeding: every reduced word of length 18 of the gasket drawn
+    once per point of kl_cusp_seeds (8 points: the attracting fixed points of
+    a, b, A, B and the fixed points of abAB, bABa, ABab, BabA), 4096^2, FP64
+    and mixed; against the one-seed-per-letter render of the same words."""
+    import torch
+    c = klsynth.C2
+    W = c.width
+    img = torch.empty((W, W), dtype=torch.int32, device=dev)
+    cnt = torch.zeros(kl.KL_N_COUNTERS, dtype=torch.int64, device=dev)
+
+    def timed(fn, K=5):
+        for _ in range(2):
+            fn()
+        ms = []
+        for k in range(K):
+            flush.fill_(k & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize(dev)
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    out = {"workload": "gasket ta=tb=2, length 18, 8 seed points, 4096^2, window [-1.5,1.5]^2",
+           "points": 8, "words_per_render": c.n_words, "words_per_call": 8 * c.n_words}
+    for name, prec in (("fp64", kl.FP64), ("mixed", kl.MIXED)):
+        p = kl.params_init(c.group.ta, c.group.tb, c.depth, W, W, c.window, prec)
+        s16 = kl.cusp_seeds(list(p.gens))
+        pts = [complex(s16[2 * i], s16[2 * i + 1]) for i in range(8)]
+        ws = torch.empty(kl.workspace_bytes(p), dtype=torch.uint8, device=dev)
+        ms = timed(lambda: kl.render_multiseed(p, pts, img, cnt, ws))
+        assert int(cnt[0].item()) + int(cnt[1].item()) == 8 * c.n_words
+        one = kl.Renderer(p, device=dev)
+        one_ms = timed(lambda: one())
+        out[f"{name}_ms"] = ms
+        out[f"{name}_words_per_s"] = 8 * c.n_words / (ms / 1000.0)
+        out[f"{name}_one_seed_per_letter_ms"] = one_ms
+        out[f"{name}_cost_per_point_over_one_render"] = ms / (8 * one_ms)
+    return out
+
+
 def batch_sweep(kl, dev, steps: int):
     """The batched sweep: 256 seeded groups, depth 12..18, 1024^2 each, mixed,
     with launch shapes from the autotuner, captured once in a CUDA graph and
@@ -612,6 +656,8 @@ def run_ours(args):
         line["paper_scan"] = scan_config(kl, dev, flush)
     if not args.no_maskit:
         line["maskit_example"] = maskit_config(kl, dev, flush)
+    if not args.no_multiseed:
+        line["multiseed"] = multiseed_config(kl, dev, flush)
     if not args.no_batch:
         line["batch_sweep"] = batch_sweep(kl, dev, K)
     if not args.no_lod:
