@@ -98,11 +98,25 @@ typedef struct {
                               1: it adds to them */
   uint32_t block_threads;  /* threads per block of the render kernels: 64, 128 or 256
                               (0 = 128); a tuning knob, results do not depend on it */
-  uint32_t chunk_pairs;    /* suffix-point pairs per work item (FP64: twice as many points);
-                              0 = choose; a tuning knob, results do not depend on it */
+  uint32_t chunk_pairs;    /* suffix-point pairs per work item (FP64: twice as many points;
+                              culled renders: culling blocks per item); 0 = choose; a
+                              tuning knob, results do not depend on it */
   uint32_t mode;           /* kl_mode: KL_LIMIT_SET (default) or KL_TILING; kl_render and
                               kl_render_noalloc only (the batch and level-of-detail calls
                               take KL_LIMIT_SET; kl_eval_words evaluates length-d words) */
+  uint32_t cull;           /* kl_render and kl_render_noalloc only (0 elsewhere): 0 (default)
+                              evaluates every word; 1 places whole blocks of words at once.
+                              The suffix points of one subtree (3^4 = 81 of them, fewer for
+                              short words) are bounded by a disk; a prefix map sends that
+                              disk onto a disk in closed form, and when the image disk,
+                              widened by a rounding margin, lies inside one pixel or wholly
+                              outside the window, every word of the block lands there and
+                              is tallied without being evaluated.  Other blocks are
+                              evaluated word by word.  The image and the in-window, dropped
+                              and FP64-word counters are those of the per-word render (the
+                              margin exceeds the per-word rounding error); KL_CNT_ATOMICS
+                              differs.  The prefix/suffix split differs too (the longest
+                              suffix table), so kl_workspace_bytes depends on this field. */
 } kl_params;
 
 /* Counters written by kl_render (uint64 each). */

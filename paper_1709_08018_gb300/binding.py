@@ -46,6 +46,7 @@ class Params(ctypes.Structure):
         ("block_threads", ctypes.c_uint32),
         ("chunk_pairs", ctypes.c_uint32),
         ("mode", ctypes.c_uint32),
+        ("cull", ctypes.c_uint32),
     ]
 
 

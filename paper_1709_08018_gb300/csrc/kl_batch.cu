@@ -271,7 +271,7 @@ extern "C" int kl_batch_create(const kl_params* params, uint32_t n_groups, kl_ba
   for (uint32_t g = 0; g < n_groups; ++g) {
     if (!valid_view(&params[g]) || !same_frame(p0, params[g])) return KL_EINVAL;
     if (params[g].precision != KL_FP64 && params[g].precision != KL_MIXED) return KL_EINVAL;
-    if (params[g].mode != KL_LIMIT_SET) return KL_EINVAL;
+    if (params[g].mode != KL_LIMIT_SET || params[g].cull != 0) return KL_EINVAL;
     if (!(params[g].parabolic_tol >= 0.0)) return KL_EINVAL;
     if (params[g].depth < 2) return KL_EINVAL;
   }

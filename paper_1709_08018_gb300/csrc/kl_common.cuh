@@ -53,8 +53,10 @@ struct Plan {
   uint32_t ns;   // suffix points per first letter: 3^(s-1)
   uint32_t npairs;  // FP32 point pairs per first letter: ceil(ns / 2)
   uint32_t p3_q1, p3_pq, p3_so1, p3_si, p3_si1;  // 3^(q-1), 3^(p-q), 3^(so-1), 3^si, 3^(si-1)
+  uint32_t cb;   // suffix points per culling block: 3^min(4, s-1), one subtree
+  uint32_t nb;   // culling blocks per first letter: ns / cb
   size_t off_pre64, off_pre32, off_flags, off_suf64, off_suf32, off_fb, off_fbcount;
-  size_t off_L, off_H, off_So, off_Si, total;
+  size_t off_L, off_H, off_So, off_Si, off_disk32, off_disk64, total;
 };
 
 struct View {
@@ -76,6 +78,11 @@ struct __align__(16) Pre32 {
   float gr, gi, axf, ayf, c1, c2, c3, c4;
   int axi, ayi;  // integer part of the pixel coordinates of alpha
   int kx, ky;    // 0x4B400000 - axi, 0x4B400000 - ayi (see mixed_item)
+};
+
+// Disk bounding one culling block of suffix points (FP64 points).
+struct __align__(16) Disk64 {
+  double cr, ci, rho, pad;
 };
 
 struct dc {
@@ -105,6 +112,8 @@ struct Tables {
   M2* Ht;
   PartM* Sot;
   double2* Sit;
+  float4* disk32;  // per culling block: center (x, y) and radius (z) of the FP32 points
+  Disk64* disk64;  // the same for the FP64 points
 };
 
 // Work items of the persistent render kernels: item = (q, prefix block pb,
@@ -520,6 +529,14 @@ struct Tally {
     }
     ++run;
   }
+  // n words into pixel pix (-1: outside the window)
+  __device__ __forceinline__ void add_n(int pix, uint32_t n, uint32_t* __restrict__ img) {
+    if (pix != cur) {
+      flush(img);
+      cur = pix;
+    }
+    run += n;
+  }
 };
 
 struct UnitTally {
@@ -867,6 +884,12 @@ inline int make_plan(const kl_params* p, Plan* L, bool batched) {
     pl = (int)p->prefix_len;
     sl = d - pl;
     if (pl < 1 || sl < 1 || pl > kMaxPrefix || sl > kMaxSuffix) return KL_EINVAL;
+  } else if (p->cull && !batched) {
+    // culled renders: the longest suffix table, so that blocks are large and
+    // the prefix tables small
+    sl = d - 1 < kMaxSuffix ? d - 1 : kMaxSuffix;
+    pl = d - sl;
+    if (pl > kMaxPrefix) return KL_ERANGE;
   } else if (batched) {
     sl = d - 7;
     if (sl > 8) sl = 8;
@@ -897,6 +920,8 @@ inline int make_plan(const kl_params* p, Plan* L, bool batched) {
   L->p3_so1 = L->so > 0 ? pow3u(L->so - 1) : 1;
   L->p3_si = pow3u(L->si);
   L->p3_si1 = L->si > 0 ? pow3u(L->si - 1) : 1;
+  L->cb = sl > 0 ? pow3u(sl - 1 < 4 ? sl - 1 : 4) : 1;
+  L->nb = sl > 0 ? L->ns / L->cb : 0;
   const size_t nP = 4ull * L->np, nS = 4ull * L->ns;
   size_t off = 0;
   L->off_pre64 = off; off = align256(off + nP * sizeof(Pre64));
@@ -910,6 +935,8 @@ inline int make_plan(const kl_params* p, Plan* L, bool batched) {
   L->off_H = off; off = align256(off + 4ull * L->p3_pq * sizeof(M2));
   L->off_So = off; off = align256(off + 4ull * L->p3_so1 * sizeof(PartM));
   L->off_Si = off; off = align256(off + 4ull * L->p3_si1 * sizeof(double2));
+  L->off_disk32 = off; off = align256(off + 4ull * L->nb * sizeof(float4));
+  L->off_disk64 = off; off = align256(off + 4ull * L->nb * sizeof(Disk64));
   L->total = off;
   return KL_OK;
 }
@@ -945,7 +972,8 @@ inline Tables carve(const Plan& L, void* ws) {
           (float4*)(b + L.off_suf32),          (unsigned long long*)(b + L.off_fb),
           (uint32_t*)(b + L.off_fbcount),      (PartM*)(b + L.off_L),
           (M2*)(b + L.off_H),                  (PartM*)(b + L.off_So),
-          (double2*)(b + L.off_Si)};
+          (double2*)(b + L.off_Si),            (float4*)(b + L.off_disk32),
+          (Disk64*)(b + L.off_disk64)};
 }
 
 inline int sm_count() {

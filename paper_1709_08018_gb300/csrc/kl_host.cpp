@@ -187,6 +187,7 @@ extern "C" int kl_params_init(kl_params* p, double ta_re, double ta_im, double t
   p->prefix_len = 0;
   p->accumulate = 0;
   p->mode = KL_LIMIT_SET;
+  p->cull = 0;
   return KL_OK;
 }
 

@@ -108,6 +108,374 @@ __global__ void __launch_bounds__(BT, 1536 / BT) render_mixed_kernel(
 }
 
 // ---------------------------------------------------------------------------
+// culled renders (kl_params.cull)
+//
+// The suffix points of one first letter come in aligned blocks of cb = 3^j
+// consecutive points (j <= 4): the points of one subtree, which share all but
+// their last j letters and so lie close together.  disk_kernel bounds every
+// block by a disk.  A prefix in pole form, (u, v) = M (w_re, w_im) / |w|^2 +
+// (ax, ay) with w = v + gamma, sends a disk D(c, rho) with |c + gamma| > rho
+// onto a set inside the disk of center M (c + gamma) / q + (ax, ay) and radius
+// |M| rho / q, q = |c + gamma|^2 - rho^2 (inversion maps disks that keep clear
+// of the pole onto disks; M is linear with operator norm |M|).  When that disk,
+// widened by a margin larger than the rounding error of the per-word map, lies
+// inside one pixel or wholly outside the window, every word of the block lands
+// there: the block is tallied with one add.  The other blocks are queued per
+// warp and evaluated word by word, 32 blocks at a time, one per lane.
+
+constexpr int kCullQueue = 64;  // per-warp queue of blocks left to the per-word path
+
+// Disk of each culling block, one warp per block: center = middle of the
+// points' bounding box, radius = largest distance from it, rounded up; FP64
+// over the FP64 points and, separately, over the FP32 points that the mixed
+// per-word path reads.  A block with a non-finite point gets an infinite
+// radius, which no test certifies.
+__global__ void disk_kernel(Plan L, Tables T) {
+  pdl_trigger();
+  pdl_wait();
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t blk = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (blk >= 4u * L.nb) return;
+  const uint32_t u = blk / L.nb, j0 = (blk % L.nb) * L.cb, j1 = j0 + L.cb;
+  const double2* s64 = T.suf64 + (size_t)u * L.ns;
+  const float* s32 = reinterpret_cast<const float*>(T.suf32p + (size_t)u * L.npairs);
+  const double inf = __longlong_as_double(0x7FF0000000000000ll);
+  double lo[4] = {inf, inf, inf, inf}, hi[4] = {-inf, -inf, -inf, -inf};
+  bool finite = true;
+  for (uint32_t j = j0 + lane; j < j1; j += 32) {
+    const double2 v = s64[j];
+    const double f[4] = {v.x, v.y, (double)s32[4 * (j / 2) + (j & 1)],
+                         (double)s32[4 * (j / 2) + 2 + (j & 1)]};
+    for (int i = 0; i < 4; ++i) {
+      finite = finite && isfinite(f[i]);
+      lo[i] = fmin(lo[i], f[i]);
+      hi[i] = fmax(hi[i], f[i]);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1)
+    for (int i = 0; i < 4; ++i) {
+      lo[i] = fmin(lo[i], __shfl_xor_sync(0xFFFFFFFFu, lo[i], o));
+      hi[i] = fmax(hi[i], __shfl_xor_sync(0xFFFFFFFFu, hi[i], o));
+    }
+  finite = __all_sync(0xFFFFFFFFu, finite);
+  const double cr = 0.5 * (lo[0] + hi[0]), ci = 0.5 * (lo[1] + hi[1]);
+  const float fr = (float)(0.5 * (lo[2] + hi[2])), fi = (float)(0.5 * (lo[3] + hi[3]));
+  double r64 = 0.0, r32 = 0.0;
+  for (uint32_t j = j0 + lane; j < j1; j += 32) {
+    const double2 v = s64[j];
+    r64 = fmax(r64, sqrt((v.x - cr) * (v.x - cr) + (v.y - ci) * (v.y - ci)));
+    // differences of two floats are exact in FP64
+    const double dx = (double)s32[4 * (j / 2) + (j & 1)] - (double)fr;
+    const double dy = (double)s32[4 * (j / 2) + 2 + (j & 1)] - (double)fi;
+    r32 = fmax(r32, sqrt(dx * dx + dy * dy));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    r64 = fmax(r64, __shfl_xor_sync(0xFFFFFFFFu, r64, o));
+    r32 = fmax(r32, __shfl_xor_sync(0xFFFFFFFFu, r32, o));
+  }
+  if (lane == 0) {
+    Disk64 D;
+    D.cr = cr;
+    D.ci = ci;
+    D.rho = finite ? r64 * (1.0 + 0x1p-40) : inf;
+    D.pad = 0.0;
+    T.disk64[blk] = D;
+    const float rho32 = finite ? __double2float_ru(r32 * (1.0 + 0x1p-40))
+                               : __int_as_float(0x7F800000);
+    T.disk32[blk] = make_float4(fr, fi, rho32, 0.0f);
+  }
+}
+
+// Operator norm of the 2x2 real matrix [[c1, c2], [c3, c4]] (its largest
+// singular value), slightly rounded up.
+__device__ __forceinline__ float opnorm32(float c1, float c2, float c3, float c4) {
+  const float a = sqrtf(fmaf(c1 + c4, c1 + c4, (c2 - c3) * (c2 - c3)));
+  const float b = sqrtf(fmaf(c1 - c4, c1 - c4, (c2 + c3) * (c2 + c3)));
+  return 0.5f * (a + b) * (1.0f + 0x1p-16f);
+}
+__device__ __forceinline__ double opnorm64(double c1, double c2, double c3, double c4) {
+  const double a = sqrt(fma(c1 + c4, c1 + c4, (c2 - c3) * (c2 - c3)));
+  const double b = sqrt(fma(c1 - c4, c1 - c4, (c2 + c3) * (c2 + c3)));
+  return 0.5 * (a + b) * (1.0 + 0x1p-40);
+}
+
+constexpr int kUncertified = -2;
+
+// Certified pixel of a whole block under an FP32 prefix (local frame, as the
+// mixed per-word map): the pixel id, -1 (every word outside the window), or
+// kUncertified.  The margin, 2^-11 px + 2^-20 of the offsets from alpha's
+// pixel, is far above the per-word map's rounding error; the interval ends are
+// rounded outwards before flooring, so a certified block never straddles a
+// pixel edge.
+__device__ __forceinline__ int block_pixel32(const Pre32& k, float nrm, float4 D, const View& V) {
+  const float c0r = D.x + k.gr, c0i = D.y + k.gi;
+  const float n2 = fmaf(c0r, c0r, c0i * c0i), rho2 = D.z * D.z;
+  if (!(4.0f * rho2 < n2)) return kUncertified;  // near the pole, or not finite
+  const float rq = rcp32(n2 - rho2);
+  const float X = fmaf(fmaf(k.c1, c0r, k.c2 * c0i), rq, k.axf);
+  const float Y = fmaf(fmaf(k.c3, c0r, k.c4 * c0i), rq, k.ayf);
+  const float R = nrm * D.z * rq;
+  const float m = R + fmaf(fabsf(X) + fabsf(Y) + R, 0x1p-20f, 0x1p-11f);
+  if (m < 0.5f && fabsf(X) < 0x1p21f && fabsf(Y) < 0x1p21f) {
+    const float magic = 12582912.0f;  // 1.5 * 2^23: t bits - 0x4B400000 = floor
+    const int xl = __float_as_int(__fadd_rd(__fsub_rd(X, m), magic));
+    const int xh = __float_as_int(__fadd_rd(__fadd_ru(X, m), magic));
+    const int yl = __float_as_int(__fadd_rd(__fsub_rd(Y, m), magic));
+    const int yh = __float_as_int(__fadd_rd(__fadd_ru(Y, m), magic));
+    if (xl == xh && yl == yh) {
+      const int col = xl - k.kx, row = yl - k.ky;
+      return ((uint32_t)col < V.W && (uint32_t)row < V.H) ? row * (int)V.W + col : -1;
+    }
+  }
+  // wholly outside the window (one pixel of slack covers the rounding of the
+  // absolute coordinates)
+  const float Xa = X + (float)k.axi, Ya = Y + (float)k.ayi;
+  if (Xa + m < -1.0f || Xa - m > (float)V.W + 1.0f || Ya + m < -1.0f ||
+      Ya - m > (float)V.H + 1.0f)
+    return -1;
+  return kUncertified;
+}
+
+// The same in FP64 (pole-form prefixes; absolute pixel coordinates).  Margin
+// 2^-30 px + 2^-44 of the offsets from alpha.
+__device__ __forceinline__ int block_pixel64(const Pre64& k, double nrm, const Disk64& D,
+                                             const View& V) {
+  const double c0r = D.cr + k.gr, c0i = D.ci + k.gi;
+  const double n2 = fma(c0r, c0r, c0i * c0i), rho2 = D.rho * D.rho;
+  if (!(4.0 * rho2 < n2)) return kUncertified;
+  const double rq = rcp64(n2 - rho2);
+  const double ox = fma(k.c1, c0r, k.c2 * c0i) * rq, oy = fma(k.c3, c0r, k.c4 * c0i) * rq;
+  const double R = nrm * D.rho * rq;
+  const double m = R + fma(fabs(ox) + fabs(oy) + R, 0x1p-44, 0x1p-30);
+  const double X = ox + k.ax, Y = oy + k.ay;
+  if (m < 0.5 && fabs(X) < 0x1p40 && fabs(Y) < 0x1p40) {
+    const double xl = floor(__dsub_rd(X, m)), xh = floor(__dadd_ru(X, m));
+    const double yl = floor(__dsub_rd(Y, m)), yh = floor(__dadd_ru(Y, m));
+    if (xl == xh && yl == yh)
+      return (xl >= 0.0 && xl < (double)V.W && yl >= 0.0 && yl < (double)V.H)
+                 ? (int)yl * (int)V.W + (int)xl
+                 : -1;
+  }
+  if (X + m < -1.0 || X - m > (double)V.W + 1.0 || Y + m < -1.0 || Y - m > (double)V.H + 1.0)
+    return -1;
+  return kUncertified;
+}
+
+// One FP32 word of prefix constants k: suffix point j of the letter's pair
+// table (the operations of the packed per-word loop, on one half).
+__device__ __forceinline__ void mixed_single_word(const Pre32& k, const float4* src, uint32_t j,
+                                                  const View& V, Tally& t,
+                                                  uint32_t* __restrict__ img) {
+  const float4 s = __ldg(src + j / 2u);
+  const bool odd = j & 1u;
+  float uf, vf;
+  uv_pole32(k, odd ? s.y : s.x, odd ? s.w : s.z, uf, vf);
+  const int col = __float_as_int(__fadd_rd(uf, 12582912.0f)) - k.kx;
+  const int row = __float_as_int(__fadd_rd(vf, 12582912.0f)) - k.ky;
+  t.add(((uint32_t)col < V.W && (uint32_t)row < V.H) ? row * (int)V.W + col : -1, img);
+}
+
+// Words of FP32 prefix slot `slot` on suffix points [j0, j0 + n) of letter u:
+// the odd ends one at a time, the rest as packed pairs.
+__device__ __forceinline__ void mixed_block_words(uint32_t slot, int u, uint32_t j0, uint32_t n,
+                                                  const Plan& L, const View& V, const Tables& T,
+                                                  Tally& t, uint32_t& words,
+                                                  uint32_t* __restrict__ img) {
+  const float4* src = T.suf32p + (size_t)u * L.npairs;
+  uint32_t j1 = j0 + n;
+  if (j0 & 1u) {
+    mixed_single_word(T.pre32[slot], src, j0, V, t, img);
+    ++j0;
+    ++words;
+  }
+  if (j1 > j0 && (j1 & 1u)) {
+    --j1;
+    mixed_single_word(T.pre32[slot], src, j1, V, t, img);
+    ++words;
+  }
+  if (j1 > j0) mixed_slot_words(slot, u, j0 / 2u, j1 / 2u, L, V, T, t, words, img);
+}
+
+// One FP64 culling unit: block b of suffix letter u under prefix slot.
+// Returns the unit's words, in-window words and atomics.
+__device__ __noinline__ UnitTally cull_unit64(const Pre64* __restrict__ pre,
+                                              const uint32_t* __restrict__ flags,
+                                              const double2* __restrict__ suf,
+                                              const Disk64* __restrict__ disks, uint32_t slot,
+                                              int u, uint32_t b, uint32_t ns, uint32_t nb,
+                                              uint32_t cb, View V, uint32_t* __restrict__ img) {
+  const Pre64 c = pre[slot];
+  const bool direct = flags[slot] & kDirect;
+  Tally t;
+  int pix = kUncertified;
+  if (!direct)
+    pix = block_pixel64(c, opnorm64(c.c1, c.c2, c.c3, c.c4), disks[(size_t)u * nb + b], V);
+  if (pix != kUncertified) {
+    t.add_n(pix, cb, img);
+    t.flush(img);
+  } else {
+    words64(c, direct, suf + (size_t)u * ns, b * cb, b * cb + cb, V, t, img);
+  }
+  return {cb, t.in_window, t.atomics};
+}
+
+__device__ __forceinline__ unsigned long long cull_entry(uint32_t slot, int u, uint32_t b) {
+  return (unsigned long long)slot | ((unsigned long long)u << 32) |
+         ((unsigned long long)b << 34);
+}
+
+// Mixed culled render.  Items: the FP64 units of the fallback prefixes
+// (fallback entry, suffix letter, block), 32 per warp item, then FP32 items of
+// 32 prefixes x a chunk of blocks, one prefix per lane.  Uncertified FP32
+// blocks wait in the warp's queue until 32 are there.
+template <int BT>
+__global__ void __launch_bounds__(BT, 1536 / BT) cull_mixed_kernel(
+    Tables T, Plan L, View V, Work Wk, uint32_t* __restrict__ img,
+    unsigned long long* counters) {
+  __shared__ unsigned long long s_queue[BT / 32][kCullQueue];
+  pdl_wait();
+  const uint32_t fb_units = 3u * L.nb * (*T.fbcount);
+  const uint32_t n64 = (fb_units + 31) / 32;
+  const uint32_t total = n64 + Wk.n_items;
+  const uint32_t lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned long long* q = s_queue[threadIdx.x >> 5];
+  uint32_t qlen = 0;
+  Tally t;
+  uint32_t words = 0, fp64_words = 0;
+  auto drain = [&](uint32_t n) {  // queue entries [0, n), one per lane
+    if (lane < n) {
+      const unsigned long long e = q[lane];
+      mixed_block_words((uint32_t)(e & 0xFFFFFFFFull), (int)((e >> 32) & 3ull),
+                        (uint32_t)(e >> 34) * L.cb, L.cb, L, V, T, t, words, img);
+    }
+    __syncwarp();
+  };
+  for (;;) {
+    const uint32_t item = next_item_warp(T.fbcount + 1);
+    if (item >= total) break;
+    if (item < n64) {
+      const uint32_t unit = item * 32 + lane;
+      if (unit < fb_units) {
+        const uint32_t e = unit / (3u * L.nb), rem = unit % (3u * L.nb);
+        const uint32_t slot = (uint32_t)(T.fb[e] & 0xFFFFFFFFull);
+        const int u = allowed_letter((int)(rem / L.nb), ((int)(slot / L.np) + 2) & 3);
+        const UnitTally r = cull_unit64(T.pre64, T.flags, T.suf64, T.disk64, slot, u,
+                                        rem % L.nb, L.ns, L.nb, L.cb, V, img);
+        words += r.words;
+        fp64_words += r.words;
+        t.in_window += r.in_window;
+        t.atomics += r.atomics;
+      }
+      continue;
+    }
+    int x, u;
+    uint32_t pb, c;
+    item_of(item - n64, Wk, x, u, pb, c);
+    const uint32_t r = pb * 32 + lane;
+    const uint32_t slot = (uint32_t)x * L.np + r;
+    const bool live = r < L.np && !(T.flags[slot] & kFallback);
+    Pre32 k{};
+    float nrm = 0.0f;
+    if (live) {
+      k = T.pre32[slot];
+      nrm = opnorm32(k.c1, k.c2, k.c3, k.c4);
+    }
+    const float4* disks = T.disk32 + (size_t)u * L.nb;
+    const uint32_t b0 = c * Wk.chunk, b1 = min(L.nb, b0 + Wk.chunk);
+    for (uint32_t b = b0; b < b1; ++b) {
+      const float4 D = disks[b];
+      const int pix = live ? block_pixel32(k, nrm, D, V) : kUncertified;
+      if (pix != kUncertified) {
+        t.add_n(pix, L.cb, img);
+        words += L.cb;
+      }
+      const bool miss = live && pix == kUncertified;
+      const unsigned bal = __ballot_sync(0xFFFFFFFFu, miss);
+      if (miss) q[qlen + __popc(bal & lt)] = cull_entry(slot, u, b);
+      qlen += __popc(bal);
+      __syncwarp();
+      if (qlen >= 32) {
+        drain(32);
+        qlen -= 32;
+        if (lane < qlen) q[lane] = q[32 + lane];
+        __syncwarp();
+      }
+    }
+  }
+  drain(qlen);
+  t.flush(img);
+  publish_counts(t.in_window, words, fp64_words, t.atomics, counters);
+}
+
+// FP64 culled render: items of 32 prefixes x a chunk of blocks, FP64 tests;
+// uncertified blocks (and every block of a direct-form prefix) go through the
+// warp's queue to the FP64 per-word path.
+template <int BT>
+__global__ void __launch_bounds__(BT) cull64_kernel(Tables T, Plan L, View V, Work Wk,
+                                                    uint32_t* __restrict__ img,
+                                                    unsigned long long* counters) {
+  __shared__ unsigned long long s_queue[BT / 32][kCullQueue];
+  pdl_wait();
+  const uint32_t lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned long long* q = s_queue[threadIdx.x >> 5];
+  uint32_t qlen = 0;
+  Tally t;
+  uint32_t words = 0;
+  auto drain = [&](uint32_t n) {
+    if (lane < n) {
+      const unsigned long long e = q[lane];
+      const uint32_t slot = (uint32_t)(e & 0xFFFFFFFFull), j0 = (uint32_t)(e >> 34) * L.cb;
+      words64(T.pre64[slot], T.flags[slot] & kDirect,
+              T.suf64 + (size_t)((e >> 32) & 3ull) * L.ns, j0, j0 + L.cb, V, t, img);
+      words += L.cb;
+    }
+    __syncwarp();
+  };
+  for (;;) {
+    const uint32_t item = next_item_warp(T.fbcount + 1);
+    if (item >= Wk.n_items) break;
+    int x, u;
+    uint32_t pb, c;
+    item_of(item, Wk, x, u, pb, c);
+    const uint32_t r = pb * 32 + lane;
+    const uint32_t slot = (uint32_t)x * L.np + r;
+    const bool live = r < L.np;
+    const bool direct = live && (T.flags[slot] & kDirect);
+    Pre64 k{};
+    double nrm = 0.0;
+    if (live && !direct) {
+      k = T.pre64[slot];
+      nrm = opnorm64(k.c1, k.c2, k.c3, k.c4);
+    }
+    const Disk64* disks = T.disk64 + (size_t)u * L.nb;
+    const uint32_t b0 = c * Wk.chunk, b1 = min(L.nb, b0 + Wk.chunk);
+    for (uint32_t b = b0; b < b1; ++b) {
+      const int pix = live && !direct ? block_pixel64(k, nrm, disks[b], V) : kUncertified;
+      if (pix != kUncertified) {
+        t.add_n(pix, L.cb, img);
+        words += L.cb;
+      }
+      const bool miss = live && pix == kUncertified;
+      const unsigned bal = __ballot_sync(0xFFFFFFFFu, miss);
+      if (miss) q[qlen + __popc(bal & lt)] = cull_entry(slot, u, b);
+      qlen += __popc(bal);
+      __syncwarp();
+      if (qlen >= 32) {
+        drain(32);
+        qlen -= 32;
+        if (lane < qlen) q[lane] = q[32 + lane];
+        __syncwarp();
+      }
+    }
+  }
+  drain(qlen);
+  t.flush(img);
+  publish_counts(t.in_window, words, 0, t.atomics, counters);
+}
+
+// ---------------------------------------------------------------------------
 // decode, sequential words (d = 1) and evaluation
 
 __global__ void decode_kernel(const uint64_t* __restrict__ idx, uint64_t n, int d, uint64_t N,
@@ -296,6 +664,7 @@ int validate(const kl_params* p, size_t ws_bytes, void* ws, Plan* L) {
   if (!p || !valid_view(p)) return KL_EINVAL;
   if (p->precision != KL_FP64 && p->precision != KL_MIXED) return KL_EINVAL;
   if (p->mode != KL_LIMIT_SET && p->mode != KL_TILING) return KL_EINVAL;
+  if (p->cull > 1) return KL_EINVAL;
   if (!(p->parabolic_tol >= 0.0)) return KL_EINVAL;
   const int st = make_plan(p, L, false);
   if (st != KL_OK) return st;
@@ -314,6 +683,23 @@ int launch_render(const kl_params* p, const Plan& L, const View& V, const Tables
                   uint32_t* img, unsigned long long* cnt, cudaStream_t s, bool profile) {
   const cudaEvent_t ev0 = profile ? g_prof_start : nullptr, ev1 = profile ? g_prof_stop : nullptr;
   int sms = 0, occ = 0;
+  if (p->cull) {
+    // block disks (a programmatic dependent of combine), then the culled render
+    if (launch_dependent(disk_kernel, dim3((4u * L.nb + 3u) / 4u), dim3(128), s, L, T) != KL_OK)
+      return KL_ECUDA;
+    const bool mixed = p->precision == KL_MIXED;
+    const void* k = mixed ? (const void*)cull_mixed_kernel<BT> : (const void*)cull64_kernel<BT>;
+    if (device_slots(k, BT, &sms, &occ) != KL_OK) return KL_ECUDA;
+    // warp-sized items (32 prefixes x a chunk of blocks), about 12 per resident warp
+    const Work Wk = make_work(L, 32, L.nb, sms * occ * (BT / 32), p->chunk_pairs);
+    if (prof_mark(ev0, s) != KL_OK) return KL_ECUDA;
+    const int st = mixed ? launch_dependent(cull_mixed_kernel<BT>, dim3(sms * occ), dim3(BT), s,
+                                            T, L, V, Wk, img, cnt)
+                         : launch_dependent(cull64_kernel<BT>, dim3(sms * occ), dim3(BT), s, T,
+                                            L, V, Wk, img, cnt);
+    if (st != KL_OK) return KL_ECUDA;
+    return prof_mark(ev1, s);
+  }
   if (p->precision == KL_FP64) {
     if (device_slots((const void*)render64_kernel<BT>, BT, &sms, &occ) != KL_OK) return KL_ECUDA;
     const Work Wk = make_work(L, BT, L.ns, sms * occ, 2u * p->chunk_pairs);
