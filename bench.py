@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-scan", action="store_true")
     ap.add_argument("--no-maskit", action="store_true")
     ap.add_argument("--no-multiseed", action="store_true")
+    ap.add_argument("--no-cull", action="store_true")
     return ap.parse_args()
 
 
@@ -411,6 +412,57 @@ def multiseed_config(kl, dev, flush):
     return out
 
 
+def cull_config(kl, dev, flush):
+    """Culled renders (kl_params.cull = 1): the same images with whole blocks
+    of words placed at once where a closed-form disk bound certifies their
+    pixel.  Gasket length 18 at 4096^2 (mixed and FP64) and the near-cusp
+    group at length 20, 8192^2 (mixed).  Each culled image is compared bit for
+    bit with the per-word render on the same prefix/suffix split, and timed
+    against the per-word render on its default split.  Throughput is in
+    word-equivalents/s: the words whose pixels the render fixes, not words
+    evaluated one by one."""
+    import torch
+
+    def timed(r, K=7):
+        for _ in range(2):
+            r()
+        ms = []
+        for k in range(K):
+            flush.fill_(k & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            r()
+            b.record()
+            torch.cuda.synchronize(dev)
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    out = {}
+    for tag, cfg, prec in (("gasket_d18_mixed", klsynth.C2, kl.MIXED),
+                           ("gasket_d18_fp64", klsynth.C2, kl.FP64),
+                           ("nearcusp_d20_mixed", klsynth.C3, kl.MIXED)):
+        mk = lambda **f: kl.params_init(cfg.group.ta, cfg.group.tb, cfg.depth, cfg.width,
+                                        cfg.height, cfg.window, prec, **f)
+        rc = kl.Renderer(mk(cull=1), device=dev)
+        cull_ms = timed(rc)
+        sl = cfg.depth - 1 if cfg.depth - 1 <= 9 else min(12, max(9, cfg.depth // 2 + 1))
+        rs = kl.Renderer(mk(prefix_len=cfg.depth - sl), device=dev)
+        rs()
+        same = bool(torch.equal(rc.image, rs.image) and
+                    torch.equal(rc.counters[:3], rs.counters[:3]))
+        del rs
+        rw = kl.Renderer(mk(), device=dev)
+        word_ms = timed(rw)
+        del rw
+        out[tag] = {"words": cfg.n_words, "culled_ms": cull_ms, "per_word_ms": word_ms,
+                    "word_equivalents_per_s": cfg.n_words / (cull_ms / 1000.0),
+                    "speedup_over_per_word": word_ms / cull_ms,
+                    "identical_to_per_word_same_split": same,
+                    "fp64_words": int(rc.counters[2].item())}
+        del rc
+    return out
+
+
 def batch_sweep(kl, dev, steps: int):
     """The batched sweep: 256 seeded groups, depth 12..18, 1024^2 each, mixed,
     with launch shapes from the autotuner, captured once in a CUDA graph and
@@ -476,6 +528,22 @@ def lod_config(kl, n_train: int = 64, n_test: int = 16, n_valid: int = 8):
     margin, edge = tuned["margin"], tuned["edge"]
     evals = [lod.evaluate(p, mlp, lo, hi, margin, edge, repeats=3) for p in te]
     s = lod.summarize(evals)
+    # the exact culled render of the same groups (no network; every word placed)
+    cul_ms, cul_iou, cul_diff = 0.0, 1.0, 0
+    for p in te:
+        q = kl.Params.from_buffer_copy(p)
+        q.cull = 1
+        rc, rw = kl.Renderer(q), kl.Renderer(p)
+        rw()
+        cul_ms += lod.time_ms(lambda: rc(), 3)
+        a, b = rw.image != 0, rc.image != 0
+        union = int((a | b).sum())
+        cul_iou = min(cul_iou, int((a & b).sum()) / union if union else 1.0)
+        cul_diff += int((rw.image != rc.image).sum())
+        del rc, rw
+    s["culled"] = {"ms": cul_ms, "speedup_over_exact": s["exact_ms"] / cul_ms,
+                   "iou_min_vs_exact": cul_iou, "pixels_differing_from_exact": cul_diff,
+                   "pruned_speedup_over_culled": cul_ms / s["pruned_ms"]}
     s.update({"workload": f"{n_test} held-out groups (seed 1711), depth 22 "
                           f"({kl.word_count(d)} words each), 8192^2 over [-2,2]^2; network "
                           f"trained on {n_train} groups (seed 1710); pruning setting chosen "
@@ -681,6 +749,8 @@ def run_ours(args):
         line["maskit_example"] = maskit_config(kl, dev, flush)
     if not args.no_multiseed:
         line["multiseed"] = multiseed_config(kl, dev, flush)
+    if not args.no_cull:
+        line["culled"] = cull_config(kl, dev, flush)
     if not args.no_batch:
         line["batch_sweep"] = batch_sweep(kl, dev, K)
     if not args.no_lod:

@@ -93,7 +93,8 @@ typedef struct {
   double parabolic_tol;    /* KL_MIXED: a prefix matrix P with
                               |tr(P)^2 - 4 det P| < tol * max(1, |tr P|^2) is near-parabolic
                               and its words are evaluated in FP64; default 1e-6 */
-  uint32_t prefix_len;     /* letters per cached prefix matrix (0 = choose) */
+  uint32_t prefix_len;     /* letters per cached prefix matrix, 1 .. 15 leaving 1 .. 12
+                              suffix letters (0 = choose) */
   uint32_t accumulate;     /* 0: kl_render zeroes the image and counters first;
                               1: it adds to them */
   uint32_t block_threads;  /* threads per block of the render kernels: 64, 128 or 256

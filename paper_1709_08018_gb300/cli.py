@@ -49,6 +49,7 @@ def main(argv=None):
     ap.add_argument("--held-out", type=int, default=1)
     ap.add_argument("--scan", action="store_true")
     ap.add_argument("--tiling", action="store_true")
+    ap.add_argument("--cull", action="store_true", help="place certified blocks of words at once")
     a = ap.parse_args(argv)
     if a.batch:
         return run_batch(a, kl, klsynth, torch)
@@ -63,7 +64,8 @@ def main(argv=None):
     W = H = a.size or c.width
     p = kl.params_init(ta, tb, depth, W, H, c.window,
                        kl.MIXED if a.precision == "mixed" else kl.FP64,
-                       prefix_len=a.prefix_len, mode=kl.TILING if a.tiling else kl.LIMIT_SET)
+                       prefix_len=a.prefix_len, mode=kl.TILING if a.tiling else kl.LIMIT_SET,
+                       cull=int(a.cull))
     r = kl.Renderer(p)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(a.repeat):

@@ -32,9 +32,11 @@
 namespace {
 
 constexpr int kMaxPrefix = 15;
-constexpr int kMaxSuffix = 9;
-constexpr int kMaxRenderDepth = kMaxPrefix + kMaxSuffix;
+constexpr int kMaxPlainSuffix = 9;  // suffix letters of the default per-word plans
+constexpr int kMaxSuffix = 12;      // of culled plans and of a caller's prefix_len
+constexpr int kMaxRenderDepth = kMaxPrefix + kMaxPlainSuffix;
 constexpr int kDefaultThreads = 128;
+constexpr int kMaxCullLevels = 8;
 
 // Prefix flags.
 constexpr uint32_t kDirect = 1u;     // P10 ~ 0: pole form invalid, use the direct map
@@ -53,10 +55,13 @@ struct Plan {
   uint32_t ns;   // suffix points per first letter: 3^(s-1)
   uint32_t npairs;  // FP32 point pairs per first letter: ceil(ns / 2)
   uint32_t p3_q1, p3_pq, p3_so1, p3_si, p3_si1;  // 3^(q-1), 3^(p-q), 3^(so-1), 3^si, 3^(si-1)
-  uint32_t cb;   // suffix points per culling block: 3^min(4, s-1), one subtree
-  uint32_t nb;   // culling blocks per first letter: ns / cb
+  // culling blocks (kl_params.cull): level l = 0 .. clev-1 holds aligned blocks
+  // of csz[l] = 3^(cj0 + l) suffix points (one subtree each), cnb[l] = ns /
+  // csz[l] of them per first letter, their disks from index cdisk[l] on
+  uint32_t cj0, clev, ndisks;
+  uint32_t csz[kMaxCullLevels], cnb[kMaxCullLevels], cdisk[kMaxCullLevels];
   size_t off_pre64, off_pre32, off_flags, off_suf64, off_suf32, off_fb, off_fbcount;
-  size_t off_L, off_H, off_So, off_Si, off_disk32, off_disk64, total;
+  size_t off_L, off_H, off_So, off_Si, off_disk32, off_disk64, off_nrm32, off_nrm64, total;
 };
 
 struct View {
@@ -114,6 +119,8 @@ struct Tables {
   double2* Sit;
   float4* disk32;  // per culling block: center (x, y) and radius (z) of the FP32 points
   Disk64* disk64;  // the same for the FP64 points
+  float* nrm32;    // per prefix slot: operator norm of the FP32 pole-form matrix
+  double* nrm64;   // the same in FP64
 };
 
 // Work items of the persistent render kernels: item = (q, prefix block pb,
@@ -885,9 +892,16 @@ inline int make_plan(const kl_params* p, Plan* L, bool batched) {
     sl = d - pl;
     if (pl < 1 || sl < 1 || pl > kMaxPrefix || sl > kMaxSuffix) return KL_EINVAL;
   } else if (p->cull && !batched) {
-    // culled renders: the longest suffix table, so that blocks are large and
-    // the prefix tables small
-    sl = d - 1 < kMaxSuffix ? d - 1 : kMaxSuffix;
+    // culled renders: long suffix tables (large blocks, and a prefix table
+    // whose FP64 products are the bulk of the table cost kept small): all but
+    // one letter up to 9, then about half the word plus one, at most 12
+    if (d - 1 <= kMaxPlainSuffix) {
+      sl = d - 1;
+    } else {
+      sl = d / 2 + 1;
+      if (sl < kMaxPlainSuffix) sl = kMaxPlainSuffix;
+      if (sl > kMaxSuffix) sl = kMaxSuffix;
+    }
     pl = d - sl;
     if (pl > kMaxPrefix) return KL_ERANGE;
   } else if (batched) {
@@ -920,8 +934,21 @@ inline int make_plan(const kl_params* p, Plan* L, bool batched) {
   L->p3_so1 = L->so > 0 ? pow3u(L->so - 1) : 1;
   L->p3_si = pow3u(L->si);
   L->p3_si1 = L->si > 0 ? pow3u(L->si - 1) : 1;
-  L->cb = sl > 0 ? pow3u(sl - 1 < 4 ? sl - 1 : 4) : 1;
-  L->nb = sl > 0 ? L->ns / L->cb : 0;
+  // culling levels: blocks of 9 .. 729 points (fewer levels for short suffixes)
+  {
+    const int top = sl > 0 ? (sl - 1 < 6 ? sl - 1 : 6) : 0;
+    const int j0 = top < 2 ? top : 2;
+    L->cj0 = (uint32_t)j0;
+    L->clev = sl > 0 ? (uint32_t)(top - j0 + 1) : 0;
+    L->ndisks = 0;
+    for (uint32_t l = 0; l < (uint32_t)kMaxCullLevels; ++l) {
+      const bool on = l < L->clev;
+      L->csz[l] = on ? pow3u(j0 + (int)l) : 0;
+      L->cnb[l] = on ? L->ns / L->csz[l] : 0;
+      L->cdisk[l] = L->ndisks;
+      L->ndisks += 4u * L->cnb[l];
+    }
+  }
   const size_t nP = 4ull * L->np, nS = 4ull * L->ns;
   size_t off = 0;
   L->off_pre64 = off; off = align256(off + nP * sizeof(Pre64));
@@ -935,8 +962,10 @@ inline int make_plan(const kl_params* p, Plan* L, bool batched) {
   L->off_H = off; off = align256(off + 4ull * L->p3_pq * sizeof(M2));
   L->off_So = off; off = align256(off + 4ull * L->p3_so1 * sizeof(PartM));
   L->off_Si = off; off = align256(off + 4ull * L->p3_si1 * sizeof(double2));
-  L->off_disk32 = off; off = align256(off + 4ull * L->nb * sizeof(float4));
-  L->off_disk64 = off; off = align256(off + 4ull * L->nb * sizeof(Disk64));
+  L->off_disk32 = off; off = align256(off + (size_t)L->ndisks * sizeof(float4));
+  L->off_disk64 = off; off = align256(off + (size_t)L->ndisks * sizeof(Disk64));
+  L->off_nrm32 = off; off = align256(off + nP * sizeof(float));
+  L->off_nrm64 = off; off = align256(off + nP * sizeof(double));
   L->total = off;
   return KL_OK;
 }
@@ -973,7 +1002,8 @@ inline Tables carve(const Plan& L, void* ws) {
           (uint32_t*)(b + L.off_fbcount),      (PartM*)(b + L.off_L),
           (M2*)(b + L.off_H),                  (PartM*)(b + L.off_So),
           (double2*)(b + L.off_Si),            (float4*)(b + L.off_disk32),
-          (Disk64*)(b + L.off_disk64)};
+          (Disk64*)(b + L.off_disk64),         (float*)(b + L.off_nrm32),
+          (double*)(b + L.off_nrm64)};
 }
 
 inline int sm_count() {

@@ -457,7 +457,7 @@ int lod_plan(const kl_params* p, uint32_t lo, uint32_t hi, LodPlan* P, Plan* L) 
   if (p->mode != KL_LIMIT_SET || p->cull != 0) return KL_EINVAL;
   const int D = (int)p->depth;
   if (lo < 1 || lo > hi || (int)hi >= D || hi > (uint32_t)kMaxPrefix ||
-      D - (int)hi > kMaxSuffix)
+      D - (int)hi > kMaxPlainSuffix)
     return KL_ERANGE;
   kl_params q = *p;
   q.prefix_len = hi;

@@ -110,81 +110,26 @@ __global__ void __launch_bounds__(BT, 1536 / BT) render_mixed_kernel(
 // ---------------------------------------------------------------------------
 // culled renders (kl_params.cull)
 //
-// The suffix points of one first letter come in aligned blocks of cb = 3^j
-// consecutive points (j <= 4): the points of one subtree, which share all but
-// their last j letters and so lie close together.  disk_kernel bounds every
-// block by a disk.  A prefix in pole form, (u, v) = M (w_re, w_im) / |w|^2 +
-// (ax, ay) with w = v + gamma, sends a disk D(c, rho) with |c + gamma| > rho
-// onto a set inside the disk of center M (c + gamma) / q + (ax, ay) and radius
-// |M| rho / q, q = |c + gamma|^2 - rho^2 (inversion maps disks that keep clear
-// of the pole onto disks; M is linear with operator norm |M|).  When that disk,
-// widened by a margin larger than the rounding error of the per-word map, lies
-// inside one pixel or wholly outside the window, every word of the block lands
-// there: the block is tallied with one add.  The other blocks are queued per
-// warp and evaluated word by word, 32 blocks at a time, one per lane.
+// The suffix points of one first letter come in aligned blocks of 3^j
+// consecutive points: the points of one subtree, which share all but their
+// last j letters and so lie close together.  Blocks of 9 .. 729 points form a
+// tree (a block's children are the three blocks of a third its size inside
+// it), and disk_kernel bounds every block by a disk.  A prefix in pole form,
+// (u, v) = M (w_re, w_im) / |w|^2 + (ax, ay) with w = v + gamma, sends a disk
+// D(c, rho) with |c + gamma| > rho onto a set inside the disk of center
+// M (c + gamma) / q + (ax, ay) and radius |M| rho / q, q = |c + gamma|^2 - rho^2
+// (inversion maps a disk clear of the pole onto a disk; M is linear with
+// operator norm |M|).  When that disk, widened by a margin larger than the
+// rounding error of the per-word map, lies inside one pixel or wholly outside
+// the window, every word of the block lands there and the block is tallied
+// with one add; otherwise its three children are tested, and a failing block
+// of the smallest size is evaluated word by word.  Tests run 32 to a warp, one
+// per lane, from a per-warp stack of (prefix, level, block) entries in shared
+// memory; word-by-word blocks wait in a second per-warp queue until 32 are
+// there.
 
-constexpr int kCullQueue = 64;  // per-warp queue of blocks left to the per-word path
-
-// Disk of each culling block, one warp per block: center = middle of the
-// points' bounding box, radius = largest distance from it, rounded up; FP64
-// over the FP64 points and, separately, over the FP32 points that the mixed
-// per-word path reads.  A block with a non-finite point gets an infinite
-// radius, which no test certifies.
-__global__ void disk_kernel(Plan L, Tables T) {
-  pdl_trigger();
-  pdl_wait();
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t blk = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (blk >= 4u * L.nb) return;
-  const uint32_t u = blk / L.nb, j0 = (blk % L.nb) * L.cb, j1 = j0 + L.cb;
-  const double2* s64 = T.suf64 + (size_t)u * L.ns;
-  const float* s32 = reinterpret_cast<const float*>(T.suf32p + (size_t)u * L.npairs);
-  const double inf = __longlong_as_double(0x7FF0000000000000ll);
-  double lo[4] = {inf, inf, inf, inf}, hi[4] = {-inf, -inf, -inf, -inf};
-  bool finite = true;
-  for (uint32_t j = j0 + lane; j < j1; j += 32) {
-    const double2 v = s64[j];
-    const double f[4] = {v.x, v.y, (double)s32[4 * (j / 2) + (j & 1)],
-                         (double)s32[4 * (j / 2) + 2 + (j & 1)]};
-    for (int i = 0; i < 4; ++i) {
-      finite = finite && isfinite(f[i]);
-      lo[i] = fmin(lo[i], f[i]);
-      hi[i] = fmax(hi[i], f[i]);
-    }
-  }
-  for (int o = 16; o > 0; o >>= 1)
-    for (int i = 0; i < 4; ++i) {
-      lo[i] = fmin(lo[i], __shfl_xor_sync(0xFFFFFFFFu, lo[i], o));
-      hi[i] = fmax(hi[i], __shfl_xor_sync(0xFFFFFFFFu, hi[i], o));
-    }
-  finite = __all_sync(0xFFFFFFFFu, finite);
-  const double cr = 0.5 * (lo[0] + hi[0]), ci = 0.5 * (lo[1] + hi[1]);
-  const float fr = (float)(0.5 * (lo[2] + hi[2])), fi = (float)(0.5 * (lo[3] + hi[3]));
-  double r64 = 0.0, r32 = 0.0;
-  for (uint32_t j = j0 + lane; j < j1; j += 32) {
-    const double2 v = s64[j];
-    r64 = fmax(r64, sqrt((v.x - cr) * (v.x - cr) + (v.y - ci) * (v.y - ci)));
-    // differences of two floats are exact in FP64
-    const double dx = (double)s32[4 * (j / 2) + (j & 1)] - (double)fr;
-    const double dy = (double)s32[4 * (j / 2) + 2 + (j & 1)] - (double)fi;
-    r32 = fmax(r32, sqrt(dx * dx + dy * dy));
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    r64 = fmax(r64, __shfl_xor_sync(0xFFFFFFFFu, r64, o));
-    r32 = fmax(r32, __shfl_xor_sync(0xFFFFFFFFu, r32, o));
-  }
-  if (lane == 0) {
-    Disk64 D;
-    D.cr = cr;
-    D.ci = ci;
-    D.rho = finite ? r64 * (1.0 + 0x1p-40) : inf;
-    D.pad = 0.0;
-    T.disk64[blk] = D;
-    const float rho32 = finite ? __double2float_ru(r32 * (1.0 + 0x1p-40))
-                               : __int_as_float(0x7F800000);
-    T.disk32[blk] = make_float4(fr, fi, rho32, 0.0f);
-  }
-}
+constexpr int kCullStack = 384;  // per-warp test stack (entries)
+constexpr int kLeafQueue = 64;   // per-warp queue of blocks left to the per-word path
 
 // Operator norm of the 2x2 real matrix [[c1, c2], [c3, c4]] (its largest
 // singular value), slightly rounded up.
@@ -296,143 +241,203 @@ __device__ __forceinline__ void mixed_block_words(uint32_t slot, int u, uint32_t
   if (j1 > j0) mixed_slot_words(slot, u, j0 / 2u, j1 / 2u, L, V, T, t, words, img);
 }
 
-// One FP64 culling unit: block b of suffix letter u under prefix slot.
-// Returns the unit's words, in-window words and atomics.
-__device__ __noinline__ UnitTally cull_unit64(const Pre64* __restrict__ pre,
-                                              const uint32_t* __restrict__ flags,
-                                              const double2* __restrict__ suf,
-                                              const Disk64* __restrict__ disks, uint32_t slot,
-                                              int u, uint32_t b, uint32_t ns, uint32_t nb,
-                                              uint32_t cb, View V, uint32_t* __restrict__ img) {
-  const Pre64 c = pre[slot];
-  const bool direct = flags[slot] & kDirect;
-  Tally t;
-  int pix = kUncertified;
-  if (!direct)
-    pix = block_pixel64(c, opnorm64(c.c1, c.c2, c.c3, c.c4), disks[(size_t)u * nb + b], V);
-  if (pix != kUncertified) {
-    t.add_n(pix, cb, img);
-    t.flush(img);
-  } else {
-    words64(c, direct, suf + (size_t)u * ns, b * cb, b * cb + cb, V, t, img);
+// Disks of all culling blocks, one warp per block, from the FP32 points that
+// the mixed per-word path reads: center = middle of their bounding box,
+// radius = largest distance from it, with a relative allowance for the FP32
+// rounding of that distance.  The FP64 disk has the same center and a radius
+// larger by 2^-23 of the largest coordinate, which covers the distance from
+// an FP64 point to its FP32 rounding.  A block with a non-finite point gets
+// an infinite radius, which no test certifies.  The warps after those compute
+// the operator norm of every prefix's pole-form matrix (one thread per slot;
+// the FP64 norm from the FP32 one where that is finite and nonzero, since the
+// FP32 entries are the FP64 ones rounded).
+__global__ void __launch_bounds__(128) disk_kernel(Plan L, Tables T) {
+  pdl_trigger();
+  pdl_wait();
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (warp >= L.ndisks) {
+    const uint32_t slot = (warp - L.ndisks) * 32u + lane;
+    if (slot < 4u * L.np) {
+      const Pre32 k = T.pre32[slot];
+      const float n32 = opnorm32(k.c1, k.c2, k.c3, k.c4);
+      T.nrm32[slot] = n32;
+      if (isfinite(n32) && n32 > 0.0f) {
+        T.nrm64[slot] = (double)n32 * (1.0 + 0x1p-20);
+      } else {
+        const Pre64 c = T.pre64[slot];
+        T.nrm64[slot] = opnorm64(c.c1, c.c2, c.c3, c.c4);
+      }
+    }
+    return;
   }
-  return {cb, t.in_window, t.atomics};
+  uint32_t l = 0;
+  while (l + 1 < L.clev && L.cdisk[l + 1] <= warp) ++l;
+  const uint32_t rem = warp - L.cdisk[l];
+  const uint32_t u = rem / L.cnb[l], j0 = (rem % L.cnb[l]) * L.csz[l], j1 = j0 + L.csz[l];
+  const float* s32 = reinterpret_cast<const float*>(T.suf32p + (size_t)u * L.npairs);
+  const float inf = __int_as_float(0x7F800000);
+  float x0 = inf, y0 = inf, x1 = -inf, y1 = -inf, amax = 0.0f;
+  bool finite = true;
+  for (uint32_t j = j0 + lane; j < j1; j += 32) {
+    const float x = s32[4 * (j / 2) + (j & 1)], y = s32[4 * (j / 2) + 2 + (j & 1)];
+    finite = finite && isfinite(x) && isfinite(y);
+    x0 = fminf(x0, x);
+    x1 = fmaxf(x1, x);
+    y0 = fminf(y0, y);
+    y1 = fmaxf(y1, y);
+    amax = fmaxf(amax, fmaxf(fabsf(x), fabsf(y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    x0 = fminf(x0, __shfl_xor_sync(0xFFFFFFFFu, x0, o));
+    x1 = fmaxf(x1, __shfl_xor_sync(0xFFFFFFFFu, x1, o));
+    y0 = fminf(y0, __shfl_xor_sync(0xFFFFFFFFu, y0, o));
+    y1 = fmaxf(y1, __shfl_xor_sync(0xFFFFFFFFu, y1, o));
+    amax = fmaxf(amax, __shfl_xor_sync(0xFFFFFFFFu, amax, o));
+  }
+  finite = __all_sync(0xFFFFFFFFu, finite);
+  const float cx = 0.5f * x0 + 0.5f * x1, cy = 0.5f * y0 + 0.5f * y1;  // any center serves
+  float d2 = 0.0f;
+  for (uint32_t j = j0 + lane; j < j1; j += 32) {
+    const float dx = s32[4 * (j / 2) + (j & 1)] - cx, dy = s32[4 * (j / 2) + 2 + (j & 1)] - cy;
+    d2 = fmaxf(d2, fmaf(dx, dx, dy * dy));
+  }
+  for (int o = 16; o > 0; o >>= 1) d2 = fmaxf(d2, __shfl_xor_sync(0xFFFFFFFFu, d2, o));
+  if (lane == 0) {
+    // six roundings at most, each within 2^-24 relative; 1e-30 covers underflow
+    const float r32 = finite ? __fmaf_ru(sqrtf(d2), 1.0f + 0x1p-20f, 1e-30f) : inf;
+    T.disk32[warp] = make_float4(cx, cy, r32, 0.0f);
+    Disk64 D;
+    D.cr = cx;
+    D.ci = cy;
+    D.rho = finite ? ((double)r32 + (double)amax * 0x1p-23) * (1.0 + 0x1p-40)
+                   : __longlong_as_double(0x7FF0000000000000ll);
+    D.pad = 0.0;
+    T.disk64[warp] = D;
+  }
 }
 
-__device__ __forceinline__ unsigned long long cull_entry(uint32_t slot, int u, uint32_t b) {
+// Culling levels of a plan in shared memory (the kernels index them by a
+// run-time level).
+struct CullLevels {
+  uint32_t sz[kMaxCullLevels], nb[kMaxCullLevels], disk[kMaxCullLevels];
+};
+
+__device__ __forceinline__ void load_levels(const Plan& L, CullLevels* C) {
+  if (threadIdx.x < (unsigned)kMaxCullLevels) {
+    C->sz[threadIdx.x] = L.csz[threadIdx.x];
+    C->nb[threadIdx.x] = L.cnb[threadIdx.x];
+    C->disk[threadIdx.x] = L.cdisk[threadIdx.x];
+  }
+  __syncthreads();
+}
+
+// Stack entry: prefix slot (bits 0-31), suffix letter (32-33), level (34-36),
+// FP64 flag (37: a mixed render's fallback prefix), block (38-63).
+__device__ __forceinline__ unsigned long long cull_entry(uint32_t slot, uint32_t u, uint32_t l,
+                                                         bool f64, uint32_t b) {
   return (unsigned long long)slot | ((unsigned long long)u << 32) |
-         ((unsigned long long)b << 34);
+         ((unsigned long long)l << 34) | ((unsigned long long)f64 << 37) |
+         ((unsigned long long)b << 38);
 }
 
-// Mixed culled render.  Items: the FP64 units of the fallback prefixes
-// (fallback entry, suffix letter, block), 32 per warp item, then FP32 items of
-// 32 prefixes x a chunk of blocks, one prefix per lane.  Uncertified FP32
-// blocks wait in the warp's queue until 32 are there.
-template <int BT>
-__global__ void __launch_bounds__(BT, 1536 / BT) cull_mixed_kernel(
+// Culled render, both precisions.  Items of 32 prefixes x a chunk of top
+// blocks, one prefix per lane, each block tested and its failing children
+// pushed; whenever the warp's stack holds 32 entries they are tested, one per
+// lane.  In a mixed render the fallback prefixes (near-parabolic, direct-form
+// and far) take the FP64 tests and FP64 words, as in the per-word render.
+template <int BT, bool MIXED>
+__global__ void __launch_bounds__(BT, 1024 / BT) cull_kernel(
     Tables T, Plan L, View V, Work Wk, uint32_t* __restrict__ img,
     unsigned long long* counters) {
-  __shared__ unsigned long long s_queue[BT / 32][kCullQueue];
+  __shared__ unsigned long long s_stack[BT / 32][kCullStack];
+  __shared__ unsigned long long s_leaf[BT / 32][kLeafQueue];
+  __shared__ CullLevels C;
+  load_levels(L, &C);
   pdl_wait();
-  const uint32_t fb_units = 3u * L.nb * (*T.fbcount);
-  const uint32_t n64 = (fb_units + 31) / 32;
-  const uint32_t total = n64 + Wk.n_items;
+  const uint32_t top = L.clev - 1;
   const uint32_t lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
-  unsigned long long* q = s_queue[threadIdx.x >> 5];
-  uint32_t qlen = 0;
+  unsigned long long* stack = s_stack[threadIdx.x >> 5];
+  unsigned long long* leafq = s_leaf[threadIdx.x >> 5];
+  uint32_t len = 0, lq = 0;
   Tally t;
   uint32_t words = 0, fp64_words = 0;
-  auto drain = [&](uint32_t n) {  // queue entries [0, n), one per lane
-    if (lane < n) {
-      const unsigned long long e = q[lane];
-      mixed_block_words((uint32_t)(e & 0xFFFFFFFFull), (int)((e >> 32) & 3ull),
-                        (uint32_t)(e >> 34) * L.cb, L.cb, L, V, T, t, words, img);
-    }
-    __syncwarp();
-  };
-  for (;;) {
-    const uint32_t item = next_item_warp(T.fbcount + 1);
-    if (item >= total) break;
-    if (item < n64) {
-      const uint32_t unit = item * 32 + lane;
-      if (unit < fb_units) {
-        const uint32_t e = unit / (3u * L.nb), rem = unit % (3u * L.nb);
-        const uint32_t slot = (uint32_t)(T.fb[e] & 0xFFFFFFFFull);
-        const int u = allowed_letter((int)(rem / L.nb), ((int)(slot / L.np) + 2) & 3);
-        const UnitTally r = cull_unit64(T.pre64, T.flags, T.suf64, T.disk64, slot, u,
-                                        rem % L.nb, L.ns, L.nb, L.cb, V, img);
-        words += r.words;
-        fp64_words += r.words;
-        t.in_window += r.in_window;
-        t.atomics += r.atomics;
-      }
-      continue;
-    }
-    int x, u;
-    uint32_t pb, c;
-    item_of(item - n64, Wk, x, u, pb, c);
-    const uint32_t r = pb * 32 + lane;
-    const uint32_t slot = (uint32_t)x * L.np + r;
-    const bool live = r < L.np && !(T.flags[slot] & kFallback);
-    Pre32 k{};
-    float nrm = 0.0f;
-    if (live) {
-      k = T.pre32[slot];
-      nrm = opnorm32(k.c1, k.c2, k.c3, k.c4);
-    }
-    const float4* disks = T.disk32 + (size_t)u * L.nb;
-    const uint32_t b0 = c * Wk.chunk, b1 = min(L.nb, b0 + Wk.chunk);
-    for (uint32_t b = b0; b < b1; ++b) {
-      const float4 D = disks[b];
-      const int pix = live ? block_pixel32(k, nrm, D, V) : kUncertified;
-      if (pix != kUncertified) {
-        t.add_n(pix, L.cb, img);
-        words += L.cb;
-      }
-      const bool miss = live && pix == kUncertified;
-      const unsigned bal = __ballot_sync(0xFFFFFFFFu, miss);
-      if (miss) q[qlen + __popc(bal & lt)] = cull_entry(slot, u, b);
-      qlen += __popc(bal);
-      __syncwarp();
-      if (qlen >= 32) {
-        drain(32);
-        qlen -= 32;
-        if (lane < qlen) q[lane] = q[32 + lane];
-        __syncwarp();
-      }
-    }
-  }
-  drain(qlen);
-  t.flush(img);
-  publish_counts(t.in_window, words, fp64_words, t.atomics, counters);
-}
 
-// FP64 culled render: items of 32 prefixes x a chunk of blocks, FP64 tests;
-// uncertified blocks (and every block of a direct-form prefix) go through the
-// warp's queue to the FP64 per-word path.
-template <int BT>
-__global__ void __launch_bounds__(BT) cull64_kernel(Tables T, Plan L, View V, Work Wk,
-                                                    uint32_t* __restrict__ img,
-                                                    unsigned long long* counters) {
-  __shared__ unsigned long long s_queue[BT / 32][kCullQueue];
-  pdl_wait();
-  const uint32_t lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  unsigned long long* q = s_queue[threadIdx.x >> 5];
-  uint32_t qlen = 0;
-  Tally t;
-  uint32_t words = 0;
-  auto drain = [&](uint32_t n) {
+  // all words of block b (level l) of letter u under slot, one by one
+  auto block_words = [&](uint32_t slot, uint32_t u, uint32_t l, bool f64, uint32_t b) {
+    const uint32_t j0 = b * C.sz[l];
+    if (MIXED && !f64) {
+      mixed_block_words(slot, (int)u, j0, C.sz[l], L, V, T, t, words, img);
+    } else {
+      words64(T.pre64[slot], T.flags[slot] & kDirect, T.suf64 + (size_t)u * L.ns, j0,
+              j0 + C.sz[l], V, t, img);
+      words += C.sz[l];
+      if (MIXED) fp64_words += C.sz[l];
+    }
+  };
+  auto drain_leaves = [&](uint32_t n) {  // leaf queue entries [0, n), one per lane
     if (lane < n) {
-      const unsigned long long e = q[lane];
-      const uint32_t slot = (uint32_t)(e & 0xFFFFFFFFull), j0 = (uint32_t)(e >> 34) * L.cb;
-      words64(T.pre64[slot], T.flags[slot] & kDirect,
-              T.suf64 + (size_t)((e >> 32) & 3ull) * L.ns, j0, j0 + L.cb, V, t, img);
-      words += L.cb;
+      const unsigned long long e = leafq[lane];
+      block_words((uint32_t)e, (uint32_t)(e >> 32) & 3u, 0u, (e >> 37) & 1ull,
+                  (uint32_t)(e >> 38));
     }
     __syncwarp();
   };
+  // certified pixel of (slot, u, l, b), or kUncertified
+  auto test = [&](uint32_t slot, uint32_t u, uint32_t l, bool f64, uint32_t b) -> int {
+    const uint32_t di = C.disk[l] + u * C.nb[l] + b;
+    if (MIXED && !f64) return block_pixel32(T.pre32[slot], T.nrm32[slot], T.disk32[di], V);
+    if (T.flags[slot] & kDirect) return kUncertified;
+    return block_pixel64(T.pre64[slot], T.nrm64[slot], T.disk64[di], V);
+  };
+  // the outcome of one test per lane (act: this lane tested an entry)
+  auto settle = [&](bool act, uint32_t slot, uint32_t u, uint32_t l, bool f64, uint32_t b,
+                    int pix) {
+    if (act && pix != kUncertified) {
+      t.add_n(pix, C.sz[l], img);
+      words += C.sz[l];
+      if (MIXED && f64) fp64_words += C.sz[l];
+    }
+    const bool miss = act && pix == kUncertified;
+    const bool direct = miss && f64 && (T.flags[slot] & kDirect);
+    const bool kids = miss && l > 0 && !direct;
+    const bool leaf = miss && l == 0 && !direct;
+    // children onto the stack while there is room; a block that finds none
+    // (never with the stack's size) and a direct-form prefix (no pole form to
+    // test) are evaluated word by word at once
+    const unsigned bk = __ballot_sync(0xFFFFFFFFu, kids);
+    const uint32_t room = (uint32_t)(kCullStack - len) / 3u, rank = __popc(bk & lt);
+    const bool pushed = kids && rank < room;
+    if (pushed)
+      for (uint32_t i = 0; i < 3; ++i)
+        stack[len + 3 * rank + i] = cull_entry(slot, u, l - 1, f64, 3 * b + 2 - i);
+    len += 3u * min((uint32_t)__popc(bk), room);
+    if ((kids && !pushed) || direct) block_words(slot, u, l, f64, b);
+    const unsigned bl = __ballot_sync(0xFFFFFFFFu, leaf);
+    if (leaf) leafq[lq + __popc(bl & lt)] = cull_entry(slot, u, 0, f64, b);
+    lq += __popc(bl);
+    __syncwarp();
+    if (lq >= 32) {
+      drain_leaves(32);
+      lq -= 32;
+      if (lane < lq) leafq[lane] = leafq[32 + lane];
+      __syncwarp();
+    }
+  };
+  // one round: the top n (<= 32) stack entries, one per lane
+  auto round = [&](uint32_t n) {
+    unsigned long long e = 0;
+    if (lane < n) e = stack[len - n + lane];
+    __syncwarp();
+    len -= n;
+    const bool act = lane < n;
+    const uint32_t slot = (uint32_t)e, u = (uint32_t)(e >> 32) & 3u;
+    const uint32_t l = (uint32_t)(e >> 34) & 7u, b = (uint32_t)(e >> 38);
+    const bool f64 = (e >> 37) & 1ull;
+    settle(act, slot, u, l, f64, b, act ? test(slot, u, l, f64, b) : kUncertified);
+  };
+
   for (;;) {
     const uint32_t item = next_item_warp(T.fbcount + 1);
     if (item >= Wk.n_items) break;
@@ -442,37 +447,18 @@ __global__ void __launch_bounds__(BT) cull64_kernel(Tables T, Plan L, View V, Wo
     const uint32_t r = pb * 32 + lane;
     const uint32_t slot = (uint32_t)x * L.np + r;
     const bool live = r < L.np;
-    const bool direct = live && (T.flags[slot] & kDirect);
-    Pre64 k{};
-    double nrm = 0.0;
-    if (live && !direct) {
-      k = T.pre64[slot];
-      nrm = opnorm64(k.c1, k.c2, k.c3, k.c4);
-    }
-    const Disk64* disks = T.disk64 + (size_t)u * L.nb;
-    const uint32_t b0 = c * Wk.chunk, b1 = min(L.nb, b0 + Wk.chunk);
+    const bool f64 = !MIXED || (live && (T.flags[slot] & kFallback));
+    const uint32_t b0 = c * Wk.chunk, b1 = min(C.nb[top], b0 + Wk.chunk);
     for (uint32_t b = b0; b < b1; ++b) {
-      const int pix = live && !direct ? block_pixel64(k, nrm, disks[b], V) : kUncertified;
-      if (pix != kUncertified) {
-        t.add_n(pix, L.cb, img);
-        words += L.cb;
-      }
-      const bool miss = live && pix == kUncertified;
-      const unsigned bal = __ballot_sync(0xFFFFFFFFu, miss);
-      if (miss) q[qlen + __popc(bal & lt)] = cull_entry(slot, u, b);
-      qlen += __popc(bal);
-      __syncwarp();
-      if (qlen >= 32) {
-        drain(32);
-        qlen -= 32;
-        if (lane < qlen) q[lane] = q[32 + lane];
-        __syncwarp();
-      }
+      settle(live, slot, (uint32_t)u, top, f64, b,
+             live ? test(slot, (uint32_t)u, top, f64, b) : kUncertified);
+      while (len >= 32) round(32);
     }
   }
-  drain(qlen);
+  while (len > 0) round(min(len, 32u));
+  drain_leaves(lq);
   t.flush(img);
-  publish_counts(t.in_window, words, 0, t.atomics, counters);
+  publish_counts(t.in_window, words, fp64_words, t.atomics, counters);
 }
 
 // ---------------------------------------------------------------------------
@@ -685,18 +671,20 @@ int launch_render(const kl_params* p, const Plan& L, const View& V, const Tables
   int sms = 0, occ = 0;
   if (p->cull) {
     // block disks (a programmatic dependent of combine), then the culled render
-    if (launch_dependent(disk_kernel, dim3((4u * L.nb + 3u) / 4u), dim3(128), s, L, T) != KL_OK)
+    const uint32_t warps = L.ndisks + (4u * L.np + 31u) / 32u;
+    if (launch_dependent(disk_kernel, dim3((warps + 3u) / 4u), dim3(128), s, L, T) != KL_OK)
       return KL_ECUDA;
     const bool mixed = p->precision == KL_MIXED;
-    const void* k = mixed ? (const void*)cull_mixed_kernel<BT> : (const void*)cull64_kernel<BT>;
+    const void* k = mixed ? (const void*)cull_kernel<BT, true> : (const void*)cull_kernel<BT, false>;
     if (device_slots(k, BT, &sms, &occ) != KL_OK) return KL_ECUDA;
-    // warp-sized items (32 prefixes x a chunk of blocks), about 12 per resident warp
-    const Work Wk = make_work(L, 32, L.nb, sms * occ * (BT / 32), p->chunk_pairs);
+    // warp-sized items: 32 prefixes x a chunk of top-level blocks (one by default)
+    const Work Wk = make_work(L, 32, L.cnb[L.clev - 1], sms * occ * (BT / 32),
+                              p->chunk_pairs ? p->chunk_pairs : 1u);
     if (prof_mark(ev0, s) != KL_OK) return KL_ECUDA;
-    const int st = mixed ? launch_dependent(cull_mixed_kernel<BT>, dim3(sms * occ), dim3(BT), s,
+    const int st = mixed ? launch_dependent(cull_kernel<BT, true>, dim3(sms * occ), dim3(BT), s,
                                             T, L, V, Wk, img, cnt)
-                         : launch_dependent(cull64_kernel<BT>, dim3(sms * occ), dim3(BT), s, T,
-                                            L, V, Wk, img, cnt);
+                         : launch_dependent(cull_kernel<BT, false>, dim3(sms * occ), dim3(BT),
+                                            s, T, L, V, Wk, img, cnt);
     if (st != KL_OK) return KL_ECUDA;
     return prof_mark(ev1, s);
   }

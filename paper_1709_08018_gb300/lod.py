@@ -103,7 +103,7 @@ class Eval:
     words: int
 
 
-def _time(fn, repeats: int = 3) -> float:
+def time_ms(fn, repeats: int = 3) -> float:
     import torch
     fn()
     torch.cuda.synchronize()
@@ -132,10 +132,10 @@ def evaluate(p: kb.Params, mlp, lo: int, hi: int, margin: float, edge: float = 0
              repeats: int = 3) -> Eval:
     """Pruned against exact render of one group (both timed with CUDA events)."""
     r = kb.Renderer(p)
-    exact_ms = _time(lambda: r(), repeats)
+    exact_ms = time_ms(lambda: r(), repeats)
     exact = r.image.clone()
     lod = kb.LodRenderer(p, lo, hi)
-    pruned_ms = _time(lambda: lod(mlp, margin, edge), repeats)
+    pruned_ms = time_ms(lambda: lod(mlp, margin, edge), repeats)
     img, cnt, st = lod(mlp, margin, edge)
     return _compare(exact, img, cnt, st, exact_ms, pruned_ms)
 
@@ -144,11 +144,11 @@ def evaluate_labels(p: kb.Params, lo: int, hi: int, extent: float = 1.0) -> Eval
     """Pruning by the true labels (edge guard = the label extent) against the
     exact render: what the splat loses when every prune decision is right."""
     r = kb.Renderer(p)
-    exact_ms = _time(lambda: r(), 1)
+    exact_ms = time_ms(lambda: r(), 1)
     exact = r.image.clone()
     _, _, _, labels = kb.lod_labels(p, lo, hi, extent=extent)
     lod = kb.LodRenderer(p, lo, hi)
-    pruned_ms = _time(lambda: lod.with_labels(labels, extent), 1)
+    pruned_ms = time_ms(lambda: lod.with_labels(labels, extent), 1)
     img, cnt, st = lod.with_labels(labels, extent)
     return _compare(exact, img, cnt, st, exact_ms, pruned_ms)
 
@@ -179,7 +179,7 @@ def tune_prune(params: Sequence[kb.Params], mlp, lo: int, hi: int, target: float
         for edge in edges:
             worst, ms = 1.0, 0.0
             for occ, L in zip(exact, lods):
-                ms += _time(lambda: L(mlp, margin, edge), 1)
+                ms += time_ms(lambda: L(mlp, margin, edge), 1)
                 img, _, _ = L(mlp, margin, edge)
                 b = img != 0
                 union = int((occ | b).sum())

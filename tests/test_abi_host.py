@@ -74,6 +74,7 @@ def test_params_init_defaults(kl):
     assert (p.x0, p.x1, p.y0, p.y1) == (-1.5, 1.5, -1.0, 1.0)
     assert p.precision == kl.FP64 and p.renorm_every == 8 and p.parabolic_tol == 1e-6
     assert p.prefix_len == 0 and p.accumulate == 0
+    assert p.mode == kl.LIMIT_SET and p.cull == 0
     assert np.allclose(list(p.gens), oracle.grandma(2, 2), atol=1e-15)
 
 
@@ -134,6 +135,34 @@ def test_tiling_workspace_and_rejections(kl):
     assert kl.workspace_bytes(p) == 0
     L = kl.binding.lib()
     p = kl.params_init(2 + 0j, 2 + 0j, 12, 64, 64, (-1.5, 1.5, -1.5, 1.5), mode=kl.TILING)
+    h = ctypes.c_void_p()
+    assert L.kl_batch_create(ctypes.byref(p), 1, ctypes.byref(h)) == 1
+    assert L.kl_lod_label_bytes(ctypes.byref(p), 3, 8) == 0
+
+
+def test_cull_workspace_and_rejections(kl):
+    """Culled renders take their own split (long suffix tables: d - 1 letters
+    up to 9, then about half the word plus one, at most 12), so their
+    workspace differs; a caller's prefix length may leave up to 12 suffix
+    letters; cull values above 1, and culled batch or level-of-detail calls,
+    are refused before any device call."""
+    import ctypes
+    win = (-1.5, 1.5, -1.5, 1.5)
+    for d in (2, 9, 10, 11, 18, 20, 22, 24):
+        sl = d - 1 if d - 1 <= 9 else min(12, max(9, d // 2 + 1))
+        c = kl.params_init(2 + 0j, 2 + 0j, d, 512, 512, win, cull=1)
+        w = kl.params_init(2 + 0j, 2 + 0j, d, 512, 512, win, cull=1, prefix_len=d - sl)
+        assert kl.workspace_bytes(c) == kl.workspace_bytes(w) > 0
+    for d, plen, ok in ((20, 8, True), (20, 7, False), (24, 12, True), (24, 11, False)):
+        p = kl.params_init(2 + 0j, 2 + 0j, d, 512, 512, win, prefix_len=plen)
+        assert (kl.workspace_bytes(p) > 0) == ok
+    p = kl.params_init(2 + 0j, 2 + 0j, 25, 512, 512, win, cull=1)
+    assert kl.workspace_bytes(p) == 0
+    L = kl.binding.lib()
+    p = kl.params_init(2 + 0j, 2 + 0j, 12, 64, 64, win, kl.MIXED, cull=2)
+    assert L.kl_render(ctypes.byref(p), ctypes.c_void_p(16), None, ctypes.c_void_p(256),
+                       ctypes.c_size_t(1 << 30), None) == 1
+    p.cull = 1
     h = ctypes.c_void_p()
     assert L.kl_batch_create(ctypes.byref(p), 1, ctypes.byref(h)) == 1
     assert L.kl_lod_label_bytes(ctypes.byref(p), 3, 8) == 0

@@ -19,7 +19,12 @@ pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-9
 TOL32 = 2e-5
-MAX_SUFFIX = 9  # the culled split: the longest suffix table, d - 1 letters at most
+
+def cull_suffix(d):
+    """Suffix letters of the culled render's own split: d - 1 up to 9, then
+    about half the word plus one, 9 .. 12."""
+    return d - 1 if d - 1 <= 9 else min(12, max(9, d // 2 + 1))
+
 
 GROUPS = {
     "gasket": klsynth.GASKET,
@@ -52,7 +57,7 @@ def culled_and_per_word(kl, group, d, window, W, H, precision, **fields):
     pc = kl.params_init(group.ta, group.tb, d, W, H, window, precision, cull=1,
                         prefix_len=plen, **fields)
     pw = kl.params_init(group.ta, group.tb, d, W, H, window, precision,
-                        prefix_len=plen or d - min(MAX_SUFFIX, d - 1), **fields)
+                        prefix_len=plen or d - cull_suffix(d), **fields)
     ic, cc = kl.render(pc)
     iw, cw = kl.render(pw)
     return (as_u32(ic), cc.cpu().numpy()), (as_u32(iw), cw.cpu().numpy())
