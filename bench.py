@@ -736,7 +736,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": cfg.width * cfg.height * 4 + kl.KL_N_COUNTERS * 8,
                     "overlap": "the copy of step k's image overlaps the render of step k+1 "
                                "(two image buffers, two streams)"},
-            "gpu_launches": 4 * K,
+            "gpu_launches": 3 * K,  # per step: parts, combine and render
             "counters": {"in_window": int(cnt[0]), "dropped": int(cnt[1]),
                          "fp64_words": fp64_words, "atomics": int(cnt[3])},
             "plain_fp64": plain,
