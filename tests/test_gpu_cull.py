@@ -178,3 +178,19 @@ def test_cull_rejections(kl):
     p = kl.params_init(g.ta, g.tb, 12, 64, 64, (-1.5, 1.5, -1.5, 1.5), kl.MIXED, cull=2)
     with pytest.raises(RuntimeError):
         kl.render(p)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_cull_through_noalloc(kl, prec):
+    """The culled render through kl_render_noalloc (the library's static
+    scratch array) gives the culled image of kl_render."""
+    import torch
+    P = kl.FP64 if prec == "fp64" else kl.MIXED
+    g = GROUPS["gasket"]
+    p = kl.params_init(g.ta, g.tb, 16, 2048, 2048, (-1.5, 1.5, -1.5, 1.5), P, cull=1)
+    assert kl.workspace_bytes(p) <= kl.KL_STATIC_SCRATCH_BYTES
+    a, ca = kl.render(p)
+    b = torch.empty_like(a)
+    cb = torch.zeros_like(ca)
+    kl.render_noalloc(p, b, cb)
+    assert torch.equal(a, b) and torch.equal(ca[:3], cb[:3])
