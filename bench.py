@@ -141,12 +141,39 @@ RENDER_SOURCES = ("paper_1709_08018_gb300/csrc/kl_common.cuh",
                   "paper_1709_08018_gb300/csrc/kl_render.cu", "include/kl.h")
 
 
+def code_text(src: str) -> str:
+    """C/C++/CUDA source with comments removed and whitespace runs collapsed
+    (string and character literals kept), so that documentation edits leave
+    the hash of the code unchanged."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def source_hash():
-    """Hash of the sources the single-render kernels are built from."""
+    """Hash of the code (comments and layout aside) of the sources the
+    single-render kernels are built from."""
     h = hashlib.sha256()
     for f in RENDER_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            h.update(code_text(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

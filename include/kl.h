@@ -107,17 +107,21 @@ typedef struct {
                               take KL_LIMIT_SET; kl_eval_words evaluates length-d words) */
   uint32_t cull;           /* kl_render and kl_render_noalloc only (0 elsewhere): 0 (default)
                               evaluates every word; 1 places whole blocks of words at once.
-                              The suffix points of one subtree (3^4 = 81 of them, fewer for
-                              short words) are bounded by a disk; a prefix map sends that
-                              disk onto a disk in closed form, and when the image disk,
-                              widened by a rounding margin, lies inside one pixel or wholly
-                              outside the window, every word of the block lands there and
-                              is tallied without being evaluated.  Other blocks are
+                              The suffix points of one subtree (blocks of 9 .. 729 points,
+                              fewer for short words, each block's children being the three
+                              blocks of a third its size inside it) are bounded by a disk; a
+                              prefix map sends that disk onto a disk in closed form, and when
+                              the image disk, widened by a rounding margin, lies inside one
+                              pixel or wholly outside the window, every word of the block
+                              lands there and is tallied without being evaluated.  Otherwise
+                              the block's children are tested, and a failing 9-point block is
                               evaluated word by word.  The image and the in-window, dropped
-                              and FP64-word counters are those of the per-word render (the
-                              margin exceeds the per-word rounding error); KL_CNT_ATOMICS
-                              differs.  The prefix/suffix split differs too (the longest
-                              suffix table), so kl_workspace_bytes depends on this field. */
+                              and FP64-word counters are those of the per-word render on the
+                              same prefix/suffix split (the margin exceeds the per-word
+                              rounding error); KL_CNT_ATOMICS differs.  The split differs from
+                              the per-word default (suffixes of d-1 letters up to 9, then
+                              d/2+1, at most 12), so kl_workspace_bytes depends on this
+                              field. */
 } kl_params;
 
 /* Counters written by kl_render (uint64 each). */
