@@ -962,10 +962,12 @@ inline int make_plan(const kl_params* p, Plan* L, bool batched) {
   L->off_H = off; off = align256(off + 4ull * L->p3_pq * sizeof(M2));
   L->off_So = off; off = align256(off + 4ull * L->p3_so1 * sizeof(PartM));
   L->off_Si = off; off = align256(off + 4ull * L->p3_si1 * sizeof(double2));
-  L->off_disk32 = off; off = align256(off + (size_t)L->ndisks * sizeof(float4));
-  L->off_disk64 = off; off = align256(off + (size_t)L->ndisks * sizeof(Disk64));
-  L->off_nrm32 = off; off = align256(off + nP * sizeof(float));
-  L->off_nrm64 = off; off = align256(off + nP * sizeof(double));
+  // disks and prefix norms exist in culled plans only
+  const size_t nD = p->cull && !batched ? L->ndisks : 0, nN = p->cull && !batched ? nP : 0;
+  L->off_disk32 = off; off = align256(off + nD * sizeof(float4));
+  L->off_disk64 = off; off = align256(off + nD * sizeof(Disk64));
+  L->off_nrm32 = off; off = align256(off + nN * sizeof(float));
+  L->off_nrm64 = off; off = align256(off + nN * sizeof(double));
   L->total = off;
   return KL_OK;
 }
