@@ -526,7 +526,33 @@ def batch_sweep(kl, dev, steps: int):
            "words_per_s": words / (statistics.mean(ms) / 1000.0),
            "tuned": tuned["best"], "tune_seconds": tune_s, "candidates": len(tuned["tried"]),
            "fp64_words": int(cnt[:, 2].sum()), "replays": K}
-    del b
+    # the same sweep culled (kl_params.cull = 1): every word placed, each
+    # group's image equal to its culled single render (tests/test_gpu_cull.py)
+    pc = [kl.params_init(c.group.ta, c.group.tb, c.depth, c.width, c.height, c.window,
+                         kl.MIXED, cull=1) for c in cfgs]
+    bc = kl.Batch(pc, device=dev)
+    bc.capture()
+    for _ in range(2):
+        bc.replay()
+    torch.cuda.synchronize(dev)
+    evc = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(K)]
+    for a, e in evc:
+        a.record()
+        bc.replay()
+        e.record()
+    torch.cuda.synchronize(dev)
+    msc = statistics.mean(a.elapsed_time(e) for a, e in evc)
+    cntc = bc.counters.cpu()
+    assert int(cntc[:, 0].sum() + cntc[:, 1].sum()) == words
+    occ_w, occ_c = b.images != 0, bc.images != 0
+    inter = (occ_w & occ_c).flatten(1).sum(1).double()
+    union = (occ_w | occ_c).flatten(1).sum(1).double().clamp(min=1)
+    out["culled"] = {"ms_per_replay": msc, "word_equivalents_per_s": words / (msc / 1000.0),
+                     "speedup_over_per_word": statistics.mean(ms) / msc,
+                     "iou_min_vs_per_word": float((inter / union).min()),
+                     "fp64_words": int(cntc[:, 2].sum())}
+    del b, bc
     torch.cuda.synchronize(dev)
     return out
 

@@ -126,22 +126,85 @@ __global__ void __launch_bounds__(BT, 1280 / BT) batch_render_kernel(
   if (gcur >= 0) publish_counts(t.in_window, words, 0, t.atomics, D[gcur].cnt);
 }
 
+// Culling disks and prefix norms of every group (culled batches): unit =
+// one warp, bases over the groups' units (ndisks + ceil(4 np / 32) each).
+__global__ void __launch_bounds__(128) batch_disk_kernel(const GroupDesc* __restrict__ D,
+                                                         const uint32_t* __restrict__ bases,
+                                                         uint32_t n, uint32_t total) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t nw = gridDim.x * (blockDim.x / 32);
+  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
+    const uint32_t g = find_group(bases, n, w), local = w - bases[g];
+    const Plan& L = D[g].L;
+    if (local < L.ndisks) {
+      cull_disk(L, D[g].T, local, lane);
+    } else {
+      const uint32_t slot = (local - L.ndisks) * 32u + lane;
+      if (slot < 4u * L.np) cull_norm(D[g].T, slot);
+    }
+  }
+}
+
+// Culled batch in one persistent launch: warps take items (32 prefixes x one
+// top-level block of one group) in group order.  A warp that moves to another
+// group first finishes the culling of the one it leaves and publishes that
+// group's counts, so its stack never mixes groups.
+template <int BT, bool MIXED>
+__global__ void __launch_bounds__(BT, 1024 / BT) batch_cull_kernel(
+    const GroupDesc* __restrict__ D, const uint32_t* __restrict__ item_bases, uint32_t n,
+    uint32_t n_items, uint32_t* queue) {
+  __shared__ unsigned long long s_stack[BT / 32][kCullStack];
+  __shared__ unsigned long long s_leaf[BT / 32][kLeafQueue];
+  __shared__ CullLevels s_lev[BT / 32];
+  const uint32_t wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  CullWarp<MIXED> w(s_stack[wi], s_leaf[wi], &s_lev[wi]);
+  int gcur = -1;
+  auto leave = [&]() {  // finish and publish the current group
+    const GroupDesc& d = D[gcur];
+    w.finish(d.L, d.V, d.T, d.img);
+    w.t.flush(d.img);
+    publish_counts(w.t.in_window, w.words, w.fp64_words, w.t.atomics, d.cnt);
+    w.t = Tally();
+    w.words = 0;
+    w.fp64_words = 0;
+  };
+  for (;;) {
+    const uint32_t item = next_item_warp(queue);
+    if (item >= n_items) break;
+    const int g = (int)find_group(item_bases, n, item);
+    if (g != gcur) {
+      if (gcur >= 0) leave();
+      if (lane < (uint32_t)kMaxCullLevels) {
+        s_lev[wi].sz[lane] = D[g].L.csz[lane];
+        s_lev[wi].nb[lane] = D[g].L.cnb[lane];
+        s_lev[wi].disk[lane] = D[g].L.cdisk[lane];
+      }
+      __syncwarp();
+      gcur = g;
+    }
+    const GroupDesc& d = D[g];
+    cull_item(w, item - item_bases[g], d.Wk, d.L, d.V, d.T, d.img, d.L.cnb[d.L.clev - 1]);
+  }
+  if (gcur >= 0) leave();
+}
+
 }  // namespace
 
 // Host handle.
 struct kl_batch {
   uint32_t n = 0;
   int mixed = 0;
+  int cull = 0;
   int bt = kDefaultThreads;
   uint32_t W = 0, H = 0;
   std::vector<kl_params> params;
   std::vector<Plan> plans;
   std::vector<Work> works;
   std::vector<size_t> table_off;
-  std::vector<uint32_t> bases;  // parts [n+1], combine [n+1], items [n+1]
+  std::vector<uint32_t> bases;  // parts [n+1], combine [n+1], items [n+1], disk units [n+1]
   std::vector<GroupDesc> desc;
   size_t off_desc = 0, off_bases = 0, off_fb = 0, off_cnt = 0, total = 0;
-  uint32_t n_parts = 0, n_comb = 0, n_items = 0, cmax = 1;
+  uint32_t n_parts = 0, n_comb = 0, n_items = 0, n_disk = 0, cmax = 1;
   int sms = 0, occ = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -149,7 +212,17 @@ struct kl_batch {
 
 namespace {
 
-const void* render_fn(int bt, bool mixed) {
+const void* render_fn(int bt, bool mixed, bool cull) {
+  if (cull) {
+    switch (bt) {
+      case 64: return mixed ? (const void*)batch_cull_kernel<64, true>
+                            : (const void*)batch_cull_kernel<64, false>;
+      case 256: return mixed ? (const void*)batch_cull_kernel<256, true>
+                             : (const void*)batch_cull_kernel<256, false>;
+      default: return mixed ? (const void*)batch_cull_kernel<128, true>
+                            : (const void*)batch_cull_kernel<128, false>;
+    }
+  }
   if (mixed) {
     switch (bt) {
       case 64: return (const void*)batch_render_kernel<64, true>;
@@ -165,10 +238,14 @@ const void* render_fn(int bt, bool mixed) {
 }
 
 template <int BT>
-void launch_batch(int grid, cudaStream_t s, bool mixed, const GroupDesc* D,
+void launch_batch(int grid, cudaStream_t s, bool mixed, bool cull, const GroupDesc* D,
                   const uint32_t* item_bases, uint32_t n, uint32_t n_items,
                   const unsigned long long* fb, uint32_t* cnt2, uint32_t cmax) {
-  if (mixed)
+  if (cull && mixed)
+    batch_cull_kernel<BT, true><<<grid, BT, 0, s>>>(D, item_bases, n, n_items, cnt2 + 1);
+  else if (cull)
+    batch_cull_kernel<BT, false><<<grid, BT, 0, s>>>(D, item_bases, n, n_items, cnt2 + 1);
+  else if (mixed)
     batch_render_kernel<BT, true><<<grid, BT, 0, s>>>(D, item_bases, n, n_items, fb, cnt2, cmax,
                                                       cnt2 + 1);
   else
@@ -177,7 +254,8 @@ void launch_batch(int grid, cudaStream_t s, bool mixed, const GroupDesc* D,
 }
 
 bool same_frame(const kl_params& a, const kl_params& b) {
-  return a.precision == b.precision && a.width == b.width && a.height == b.height &&
+  return a.precision == b.precision && a.cull == b.cull && a.width == b.width &&
+         a.height == b.height &&
          a.x0 == b.x0 && a.x1 == b.x1 && a.y0 == b.y0 && a.y1 == b.y1 &&
          a.renorm_every == b.renorm_every && a.parabolic_tol == b.parabolic_tol;
 }
@@ -240,17 +318,26 @@ int enqueue(kl_batch* b, uint32_t* images, uint64_t* counters, void* ws, cudaStr
   batch_combine_kernel<<<gc < 1048576u ? gc : 1048576u, 128, 0, s>>>(
       D, bases + (n + 1), n, b->n_comb, b->mixed, fb, cnt2);
   if (check_launch() != KL_OK) return KL_ECUDA;
+  if (b->cull) {
+    const uint32_t gd = (b->n_disk + 3) / 4;  // four warps per block
+    batch_disk_kernel<<<gd < 65535u ? gd : 65535u, 128, 0, s>>>(D, bases + 3 * (n + 1), n,
+                                                                b->n_disk);
+    if (check_launch() != KL_OK) return KL_ECUDA;
+  }
   const uint32_t* item_bases = bases + 2 * (n + 1);
   const int grid = b->sms * b->occ;
+  const bool cull = b->cull != 0;
   switch (b->bt) {
     case 64:
-      launch_batch<64>(grid, s, b->mixed, D, item_bases, n, b->n_items, fb, cnt2, b->cmax);
+      launch_batch<64>(grid, s, b->mixed, cull, D, item_bases, n, b->n_items, fb, cnt2, b->cmax);
       break;
     case 256:
-      launch_batch<256>(grid, s, b->mixed, D, item_bases, n, b->n_items, fb, cnt2, b->cmax);
+      launch_batch<256>(grid, s, b->mixed, cull, D, item_bases, n, b->n_items, fb, cnt2,
+                        b->cmax);
       break;
     default:
-      launch_batch<128>(grid, s, b->mixed, D, item_bases, n, b->n_items, fb, cnt2, b->cmax);
+      launch_batch<128>(grid, s, b->mixed, cull, D, item_bases, n, b->n_items, fb, cnt2,
+                        b->cmax);
   }
   return check_launch();
 }
@@ -271,7 +358,7 @@ extern "C" int kl_batch_create(const kl_params* params, uint32_t n_groups, kl_ba
   for (uint32_t g = 0; g < n_groups; ++g) {
     if (!valid_view(&params[g]) || !same_frame(p0, params[g])) return KL_EINVAL;
     if (params[g].precision != KL_FP64 && params[g].precision != KL_MIXED) return KL_EINVAL;
-    if (params[g].mode != KL_LIMIT_SET || params[g].cull != 0) return KL_EINVAL;
+    if (params[g].mode != KL_LIMIT_SET || params[g].cull > 1) return KL_EINVAL;
     if (!(params[g].parabolic_tol >= 0.0)) return KL_EINVAL;
     if (params[g].depth < 2) return KL_EINVAL;
   }
@@ -279,6 +366,7 @@ extern "C" int kl_batch_create(const kl_params* params, uint32_t n_groups, kl_ba
   if (!b) return KL_ERANGE;
   b->n = n_groups;
   b->mixed = p0.precision == KL_MIXED;
+  b->cull = p0.cull ? 1 : 0;
   b->bt = p0.block_threads ? (int)p0.block_threads : kDefaultThreads;
   b->W = p0.width;
   b->H = p0.height;
@@ -287,13 +375,13 @@ extern "C" int kl_batch_create(const kl_params* params, uint32_t n_groups, kl_ba
   b->works.resize(n_groups);
   b->table_off.resize(n_groups);
   b->desc.resize(n_groups);
-  b->bases.assign(3 * (n_groups + 1), 0u);
-  if (device_slots(render_fn(b->bt, b->mixed), b->bt, &b->sms, &b->occ) != KL_OK) {
+  b->bases.assign(4 * (n_groups + 1), 0u);
+  if (device_slots(render_fn(b->bt, b->mixed, b->cull), b->bt, &b->sms, &b->occ) != KL_OK) {
     delete b;
     return KL_ECUDA;
   }
   const uint32_t chunk = p0.chunk_pairs ? p0.chunk_pairs : 64u;
-  uint64_t parts = 0, comb = 0, items = 0, fb = 0;
+  uint64_t parts = 0, comb = 0, items = 0, fb = 0, disk = 0;
   size_t off = 0;
   b->off_desc = off; off = align256(off + n_groups * sizeof(GroupDesc));
   b->off_bases = off; off = align256(off + b->bases.size() * sizeof(uint32_t));
@@ -304,26 +392,32 @@ extern "C" int kl_batch_create(const kl_params* params, uint32_t n_groups, kl_ba
       delete b;
       return st;
     }
-    b->works[g] = b->mixed ? make_work(L, b->bt, L.npairs, 1, chunk)
-                           : make_work(L, b->bt, L.ns, 1, 2u * chunk);
+    // culled: warp items of 32 prefixes x one top-level block
+    b->works[g] = b->cull    ? make_work(L, 32, L.cnb[L.clev - 1], 1, 1u)
+                  : b->mixed ? make_work(L, b->bt, L.npairs, 1, chunk)
+                             : make_work(L, b->bt, L.ns, 1, 2u * chunk);
     b->bases[g] = (uint32_t)parts;
     b->bases[(n_groups + 1) + g] = (uint32_t)comb;
     b->bases[2 * (n_groups + 1) + g] = (uint32_t)items;
+    b->bases[3 * (n_groups + 1) + g] = (uint32_t)disk;
     parts += parts_count(L);
     comb += combine_count(L);
     items += b->works[g].n_items;
+    if (b->cull) disk += L.ndisks + (4ull * L.np + 31) / 32;
     fb += 4ull * L.np;
     const uint32_t cg = (L.ns + kFbChunk - 1) / kFbChunk;
     if (cg > b->cmax) b->cmax = cg;
   }
   if (parts >= (1ull << 32) || comb >= (1ull << 32) || items >= (1ull << 31) ||
-      3ull * b->cmax * fb >= (1ull << 32)) {
+      disk >= (1ull << 31) || 3ull * b->cmax * fb >= (1ull << 32)) {
     delete b;
     return KL_ERANGE;
   }
   b->bases[n_groups] = (uint32_t)parts;
   b->bases[(n_groups + 1) + n_groups] = (uint32_t)comb;
   b->bases[2 * (n_groups + 1) + n_groups] = (uint32_t)items;
+  b->bases[3 * (n_groups + 1) + n_groups] = (uint32_t)disk;
+  b->n_disk = (uint32_t)disk;
   b->n_parts = (uint32_t)parts;
   b->n_comb = (uint32_t)comb;
   b->n_items = (uint32_t)items;

@@ -144,8 +144,8 @@ def test_cull_workspace_and_rejections(kl):
     """Culled renders take their own split (long suffix tables: d - 1 letters
     up to 9, then about half the word plus one, at most 12), so their
     workspace differs; a caller's prefix length may leave up to 12 suffix
-    letters; cull values above 1, and culled batch or level-of-detail calls,
-    are refused before any device call."""
+    letters; cull values above 1, and culled level-of-detail calls, are
+    refused before any device call."""
     import ctypes
     win = (-1.5, 1.5, -1.5, 1.5)
     for d in (2, 9, 10, 11, 18, 20, 22, 24):
@@ -162,9 +162,9 @@ def test_cull_workspace_and_rejections(kl):
     p = kl.params_init(2 + 0j, 2 + 0j, 12, 64, 64, win, kl.MIXED, cull=2)
     assert L.kl_render(ctypes.byref(p), ctypes.c_void_p(16), None, ctypes.c_void_p(256),
                        ctypes.c_size_t(1 << 30), None) == 1
-    p.cull = 1
     h = ctypes.c_void_p()
-    assert L.kl_batch_create(ctypes.byref(p), 1, ctypes.byref(h)) == 1
+    assert L.kl_batch_create(ctypes.byref(p), 1, ctypes.byref(h)) == 1  # cull = 2
+    p.cull = 1
     assert L.kl_lod_label_bytes(ctypes.byref(p), 3, 8) == 0
 
 

@@ -194,3 +194,31 @@ def test_cull_through_noalloc(kl, prec):
     cb = torch.zeros_like(ca)
     kl.render_noalloc(p, b, cb)
     assert torch.equal(a, b) and torch.equal(ca[:3], cb[:3])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("bt", [64, 128, 256])
+def test_culled_batch_equals_culled_single_renders(kl, prec, bt):
+    """A culled batch (one persistent launch over groups of uneven depth)
+    gives each group's culled single render, image and counts, eagerly and
+    from a captured graph."""
+    import torch
+    P = kl.FP64 if prec == "fp64" else kl.MIXED
+    drawn = klsynth.draw_groups(klsynth.BATCH_SEED, 7)
+    groups = [g for g, _ in drawn] + [GROUPS["gasket"], GROUPS["nearcusp"]]
+    depths = [8, 14, 9, 12, 2, 11, 10, 15, 13]
+    ps = [kl.params_init(g.ta, g.tb, d, 384, 384, (-1.5, 1.5, -1.5, 1.5), P, cull=1,
+                         block_threads=bt) for g, d in zip(groups, depths)]
+    b = kl.Batch(ps)
+    imgs, cnts = b.render()
+    eager_imgs, eager_cnts = imgs.clone(), cnts.clone()
+    for k, p in enumerate(ps):
+        img, cnt = kl.render(p)
+        assert torch.equal(imgs[k], img), k
+        assert torch.equal(cnts[k][:3], cnt[:3]), (k, cnts[k], cnt)
+        assert int(cnt[0]) + int(cnt[1]) == oracle.word_count(depths[k])
+    b.capture()
+    b.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(b.images, eager_imgs)
+    assert torch.equal(b.counters[:, :3], eager_cnts[:, :3])
