@@ -413,39 +413,60 @@ __global__ void __launch_bounds__(kLodThreads) expand_kernel(
   }
 }
 
-// Exact render of the deferred level-hi nodes: item = (block of BT deferred
-// nodes, one of the three compatible suffix letters, a chunk of point pairs).
-template <int BT>
-__global__ void __launch_bounds__(BT, 1536 / BT) deferred_render_kernel(
-    Tables T, Plan L, View V, uint32_t chunk, const uint32_t* __restrict__ deferred,
-    const uint32_t* deferred_count, uint32_t* __restrict__ img, unsigned long long* counters) {
-  const uint32_t n = *deferred_count;
-  const uint32_t n_chunks = (L.npairs + chunk - 1) / chunk;
-  const uint32_t n_items = ((n + BT - 1) / BT) * 3u * n_chunks;
-  Tally t;
-  uint32_t words = 0, fp64_words = 0;
-  for (;;) {
-    const uint32_t item = next_item(T.fbcount + 1);
-    if (item >= n_items) break;
-    const uint32_t cidx = item % n_chunks, rest = item / n_chunks;
-    const uint32_t kq = rest % 3u, blk = rest / 3u;
-    const uint32_t e = blk * BT + threadIdx.x;
-    if (e >= n) continue;
-    const uint32_t slot = deferred[e];
-    const int x = (int)(slot / L.np);
-    const int u = allowed_letter((int)kq, (x + 2) & 3);
-    const uint32_t k0 = cidx * chunk, k1 = min(L.npairs, k0 + chunk);
-    if (T.flags[slot] & kFallback) {
-      const uint32_t j0 = 2u * k0, j1 = min(L.ns, 2u * k1);
-      words64(T.pre64[slot], T.flags[slot] & kDirect, T.suf64 + (size_t)u * L.ns, j0, j1, V, t,
-              img);
-      words += j1 - j0;
-      fp64_words += j1 - j0;
-    } else {
-      mixed_slot_words(slot, u, k0, k1, L, V, T, t, words, img);
-    }
+// Culled exact render of the deferred level-hi nodes (the culling of
+// kl_params.cull, kl_common.cuh): the same image as the per-word render of
+// those nodes on this split, with whole blocks of a node's words placed at
+// once where certified.
+// lod_disk_kernel first bounds the suffix blocks (warps [0, ndisks)) and
+// computes the operator norms of the listed nodes' prefixes (the other
+// threads, striding over the list).
+__global__ void __launch_bounds__(128) lod_disk_kernel(Plan L, Tables T,
+                                                       const uint32_t* __restrict__ slots,
+                                                       const uint32_t* n_slots) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (warp < L.ndisks) {
+    cull_disk(L, T, warp, lane);
+    return;
   }
-  publish_counts(t.in_window, words, fp64_words, t.atomics, counters);
+  const uint32_t n = *n_slots;
+  const uint32_t stride = gridDim.x * blockDim.x - 32u * L.ndisks;
+  for (uint32_t e = (warp - L.ndisks) * 32u + lane; e < n; e += stride) cull_norm(T, slots[e]);
+}
+
+// Items: (block of 32 listed nodes, one of the three compatible suffix
+// letters, one top-level block); each lane's letter follows its node's last
+// letter.
+template <int BT, bool MIXED>
+__global__ void __launch_bounds__(BT, 1024 / BT) lod_cull_kernel(
+    Tables T, Plan L, View V, const uint32_t* __restrict__ deferred,
+    const uint32_t* deferred_count, uint32_t* __restrict__ img, unsigned long long* counters) {
+  __shared__ unsigned long long s_stack[BT / 32][kCullStack];
+  __shared__ unsigned long long s_leaf[BT / 32][kLeafQueue];
+  __shared__ CullLevels C;
+  if (threadIdx.x < (unsigned)kMaxCullLevels) {
+    C.sz[threadIdx.x] = L.csz[threadIdx.x];
+    C.nb[threadIdx.x] = L.cnb[threadIdx.x];
+    C.disk[threadIdx.x] = L.cdisk[threadIdx.x];
+  }
+  __syncthreads();
+  CullWarp<MIXED> w(s_stack[threadIdx.x >> 5], s_leaf[threadIdx.x >> 5], &C);
+  const uint32_t n = *deferred_count, nbt = L.cnb[L.clev - 1];
+  const uint32_t n_items = ((n + 31) / 32) * 3u * nbt;
+  for (;;) {
+    const uint32_t item = next_item_warp(T.fbcount + 1);
+    if (item >= n_items) break;
+    const uint32_t bt = item % nbt, rest = item / nbt;
+    const uint32_t kq = rest % 3u, e = (rest / 3u) * 32u + w.lane;
+    const bool live = e < n;
+    const uint32_t slot = live ? deferred[e] : 0u;
+    const int u = allowed_letter((int)kq, ((int)(slot / L.np) + 2) & 3);
+    const bool f64 = !MIXED || (live && (T.flags[slot] & kFallback));
+    w.item(L, V, T, img, live, slot, (uint32_t)u, f64, bt, bt + 1);
+  }
+  w.finish(L, V, T, img);
+  w.t.flush(img);
+  publish_counts(w.t.in_window, w.words, w.fp64_words, w.t.atomics, counters);
 }
 
 // ---------------------------------------------------------------------------
@@ -476,6 +497,17 @@ int lod_plan(const kl_params* p, uint32_t lo, uint32_t hi, LodPlan* P, Plan* L) 
   P->base[hi + 1] = acc;
   P->total = acc;
   return KL_OK;
+}
+
+// The pruned render's plan: the same split, with the culling disks and the
+// prefix norms that its exact render of the deferred nodes uses.
+int lod_render_plan(const kl_params* p, uint32_t lo, uint32_t hi, LodPlan* P, Plan* L) {
+  const int st = lod_plan(p, lo, hi, P, L);
+  if (st != KL_OK) return st;
+  kl_params q = *p;
+  q.prefix_len = hi;
+  q.cull = 1;
+  return make_plan(&q, L, false);
 }
 
 // Workspace of kl_lod_labels: render tables | boxes of level hi | per-level int4 boxes
@@ -666,7 +698,7 @@ extern "C" int kl_lod_labels(const kl_params* p, uint32_t lo, uint32_t hi, float
 extern "C" size_t kl_lod_render_bytes(const kl_params* p, uint32_t lo, uint32_t hi) {
   LodPlan P;
   Plan L;
-  if (lod_plan(p, lo, hi, &P, &L) != KL_OK) return 0;
+  if (lod_render_plan(p, lo, hi, &P, &L) != KL_OK) return 0;
   return render_layout(P, L).total;
 }
 
@@ -678,7 +710,7 @@ int render_lod_impl(const kl_params* p, uint32_t lo, uint32_t hi, const float* d
                     size_t workspace_bytes, void* stream) {
   LodPlan P;
   Plan L;
-  int st = lod_plan(p, lo, hi, &P, &L);
+  int st = lod_render_plan(p, lo, hi, &P, &L);
   if (st != KL_OK) return st;
   if (p->precision != KL_MIXED) return KL_EINVAL;
   if (!(edge >= 0.0f && edge < 0.5f)) return KL_EINVAL;
@@ -722,10 +754,14 @@ int render_lod_impl(const kl_params* p, uint32_t lo, uint32_t hi, const float* d
   st = build_tables_forced(&q, L, V, G, T, s, deferred, counts + 32);
   if (st != KL_OK) return st;
   int sms = 0, occ = 0;
-  if (device_slots((const void*)deferred_render_kernel<128>, 128, &sms, &occ) != KL_OK)
+  if (device_slots((const void*)lod_cull_kernel<128, true>, 128, &sms, &occ) != KL_OK)
     return KL_ECUDA;
-  deferred_render_kernel<128><<<sms * occ, 128, 0, s>>>(T, L, V, 64u, deferred, counts + 32,
-                                                        d_image, cnt);
+  // block disks (four warps per block), then the deferred prefixes' norms
+  lod_disk_kernel<<<(L.ndisks + 3) / 4 + 2u * (uint32_t)sms, 128, 0, s>>>(L, T, deferred,
+                                                                           counts + 32);
+  if (check_launch() != KL_OK) return KL_ECUDA;
+  lod_cull_kernel<128, true><<<sms * occ, 128, 0, s>>>(T, L, V, deferred, counts + 32, d_image,
+                                                       cnt);
   return check_launch();
 }
 
