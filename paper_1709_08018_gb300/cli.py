@@ -83,8 +83,8 @@ def main(argv=None):
 
 def run_batch(a, kl, klsynth, torch):
     cfgs = klsynth.batch_configs(256)[:a.batch]
-    ps = [kl.params_init(c.group.ta, c.group.tb, c.depth, c.width, c.height, c.window, kl.MIXED)
-          for c in cfgs]
+    ps = [kl.params_init(c.group.ta, c.group.tb, c.depth, c.width, c.height, c.window, kl.MIXED,
+                         cull=int(a.cull)) for c in cfgs]
     b = kl.Batch(ps)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(a.repeat):
