@@ -127,21 +127,15 @@ __global__ void __launch_bounds__(BT, 1280 / BT) batch_render_kernel(
 }
 
 // Culling disks and prefix norms of every group (culled batches): unit =
-// one warp, bases over the groups' units (ndisks + ceil(4 np / 32) each).
+// one warp, bases over the groups' units (cull_disk_units each).
 __global__ void __launch_bounds__(128) batch_disk_kernel(const GroupDesc* __restrict__ D,
                                                          const uint32_t* __restrict__ bases,
                                                          uint32_t n, uint32_t total) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nw = gridDim.x * (blockDim.x / 32);
   for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
-    const uint32_t g = find_group(bases, n, w), local = w - bases[g];
-    const Plan& L = D[g].L;
-    if (local < L.ndisks) {
-      cull_disk(L, D[g].T, local, lane);
-    } else {
-      const uint32_t slot = (local - L.ndisks) * 32u + lane;
-      if (slot < 4u * L.np) cull_norm(D[g].T, slot);
-    }
+    const uint32_t g = find_group(bases, n, w);
+    cull_disk_unit(D[g].L, D[g].T, w - bases[g], lane);
   }
 }
 
@@ -403,7 +397,7 @@ extern "C" int kl_batch_create(const kl_params* params, uint32_t n_groups, kl_ba
     parts += parts_count(L);
     comb += combine_count(L);
     items += b->works[g].n_items;
-    if (b->cull) disk += L.ndisks + (4ull * L.np + 31) / 32;
+    if (b->cull) disk += cull_disk_units(L);
     fb += 4ull * L.np;
     const uint32_t cg = (L.ns + kFbChunk - 1) / kFbChunk;
     if (cg > b->cmax) b->cmax = cg;

@@ -1031,6 +1031,72 @@ __device__ __forceinline__ void cull_norm(const Tables& T, uint32_t slot) {
   }
 }
 
+// The same for a small block, by one thread.
+__device__ __forceinline__ void cull_disk_thread(const Plan& L, const Tables& T, uint32_t disk) {
+  uint32_t l = 0;
+  while (l + 1 < L.clev && L.cdisk[l + 1] <= disk) ++l;
+  const uint32_t rem = disk - L.cdisk[l];
+  const uint32_t u = rem / L.cnb[l], j0 = (rem % L.cnb[l]) * L.csz[l], j1 = j0 + L.csz[l];
+  const float* s32 = reinterpret_cast<const float*>(T.suf32p + (size_t)u * L.npairs);
+  const float inf = __int_as_float(0x7F800000);
+  float x0 = inf, y0 = inf, x1 = -inf, y1 = -inf, amax = 0.0f;
+  bool finite = true;
+  for (uint32_t j = j0; j < j1; ++j) {
+    const float x = s32[4 * (j / 2) + (j & 1)], y = s32[4 * (j / 2) + 2 + (j & 1)];
+    finite = finite && isfinite(x) && isfinite(y);
+    x0 = fminf(x0, x);
+    x1 = fmaxf(x1, x);
+    y0 = fminf(y0, y);
+    y1 = fmaxf(y1, y);
+    amax = fmaxf(amax, fmaxf(fabsf(x), fabsf(y)));
+  }
+  const float cx = 0.5f * x0 + 0.5f * x1, cy = 0.5f * y0 + 0.5f * y1;
+  float d2 = 0.0f;
+  for (uint32_t j = j0; j < j1; ++j) {
+    const float dx = s32[4 * (j / 2) + (j & 1)] - cx, dy = s32[4 * (j / 2) + 2 + (j & 1)] - cy;
+    d2 = fmaxf(d2, fmaf(dx, dx, dy * dy));
+  }
+  const float r32 = finite ? __fmaf_ru(sqrtf(d2), 1.0f + 0x1p-20f, 1e-30f) : inf;
+  T.disk32[disk] = make_float4(cx, cy, r32, 0.0f);
+  Disk64 D;
+  D.cr = cx;
+  D.ci = cy;
+  D.rho = finite ? ((double)r32 + (double)amax * 0x1p-23) * (1.0 + 0x1p-40)
+                 : __longlong_as_double(0x7FF0000000000000ll);
+  D.pad = 0.0;
+  T.disk64[disk] = D;
+}
+
+// Work units of a plan's disk-and-norm pass, in warps: the disks of blocks of
+// up to kThreadDiskPoints points one per thread (the smallest levels come
+// first in the disk table), then one warp per larger disk, then one thread
+// per prefix norm.
+constexpr uint32_t kThreadDiskPoints = 81;
+
+__device__ __host__ __forceinline__ uint32_t cull_small_disks(const Plan& L) {
+  uint32_t l = 0;
+  while (l < L.clev && L.csz[l] <= kThreadDiskPoints) ++l;
+  return l < L.clev ? L.cdisk[l] : L.ndisks;
+}
+__device__ __host__ __forceinline__ uint32_t cull_disk_units(const Plan& L) {
+  const uint32_t small = cull_small_disks(L);
+  return (small + 31) / 32 + (L.ndisks - small) + (4u * L.np + 31) / 32;
+}
+// One warp's share (all lanes call): unit w of cull_disk_units(L).
+__device__ __forceinline__ void cull_disk_unit(const Plan& L, const Tables& T, uint32_t w,
+                                               uint32_t lane) {
+  const uint32_t small = cull_small_disks(L), ws = (small + 31) / 32;
+  if (w < ws) {
+    const uint32_t disk = w * 32 + lane;
+    if (disk < small) cull_disk_thread(L, T, disk);
+  } else if (w < ws + (L.ndisks - small)) {
+    cull_disk(L, T, small + (w - ws), lane);
+  } else {
+    const uint32_t slot = (w - ws - (L.ndisks - small)) * 32 + lane;
+    if (slot < 4u * L.np) cull_norm(T, slot);
+  }
+}
+
 // Culling levels of one plan in shared memory (the kernels index them by a
 // run-time level).
 struct CullLevels {

@@ -425,13 +425,15 @@ __global__ void __launch_bounds__(128) lod_disk_kernel(Plan L, Tables T,
                                                        const uint32_t* n_slots) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (warp < L.ndisks) {
-    cull_disk(L, T, warp, lane);
+  const uint32_t small = cull_small_disks(L), ws = (small + 31) / 32;
+  const uint32_t nd = ws + (L.ndisks - small);  // disk warps (cull_disk_unit)
+  if (warp < nd) {
+    cull_disk_unit(L, T, warp, lane);
     return;
   }
   const uint32_t n = *n_slots;
-  const uint32_t stride = gridDim.x * blockDim.x - 32u * L.ndisks;
-  for (uint32_t e = (warp - L.ndisks) * 32u + lane; e < n; e += stride) cull_norm(T, slots[e]);
+  const uint32_t stride = gridDim.x * blockDim.x - 32u * nd;
+  for (uint32_t e = (warp - nd) * 32u + lane; e < n; e += stride) cull_norm(T, slots[e]);
 }
 
 // Items: (block of 32 listed nodes, one of the three compatible suffix
@@ -757,8 +759,10 @@ int render_lod_impl(const kl_params* p, uint32_t lo, uint32_t hi, const float* d
   if (device_slots((const void*)lod_cull_kernel<128, true>, 128, &sms, &occ) != KL_OK)
     return KL_ECUDA;
   // block disks (four warps per block), then the deferred prefixes' norms
-  lod_disk_kernel<<<(L.ndisks + 3) / 4 + 2u * (uint32_t)sms, 128, 0, s>>>(L, T, deferred,
-                                                                           counts + 32);
+  const uint32_t small = cull_small_disks(L);
+  const uint32_t disk_warps = (small + 31) / 32 + (L.ndisks - small);
+  lod_disk_kernel<<<(disk_warps + 3) / 4 + 2u * (uint32_t)sms, 128, 0, s>>>(L, T, deferred,
+                                                                              counts + 32);
   if (check_launch() != KL_OK) return KL_ECUDA;
   lod_cull_kernel<128, true><<<sms * occ, 128, 0, s>>>(T, L, V, deferred, counts + 32, d_image,
                                                        cnt);

@@ -110,19 +110,12 @@ __global__ void __launch_bounds__(BT, 1536 / BT) render_mixed_kernel(
 // ---------------------------------------------------------------------------
 // culled renders (kl_params.cull; the culling itself is in kl_common.cuh)
 
-// Disks of all culling blocks (one warp per block), then the prefix norms
-// (one thread per slot).
+// Disks of all culling blocks, then the prefix norms (cull_disk_unit).
 __global__ void __launch_bounds__(128) disk_kernel(Plan L, Tables T) {
   pdl_trigger();
   pdl_wait();
-  const uint32_t lane = threadIdx.x & 31;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (warp < L.ndisks) {
-    cull_disk(L, T, warp, lane);
-  } else {
-    const uint32_t slot = (warp - L.ndisks) * 32u + lane;
-    if (slot < 4u * L.np) cull_norm(T, slot);
-  }
+  if (warp < cull_disk_units(L)) cull_disk_unit(L, T, warp, threadIdx.x & 31);
 }
 
 // Culled render of one group: persistent warps take items of 32 prefixes x
@@ -363,7 +356,7 @@ int launch_render(const kl_params* p, const Plan& L, const View& V, const Tables
   int sms = 0, occ = 0;
   if (p->cull) {
     // block disks (a programmatic dependent of combine), then the culled render
-    const uint32_t warps = L.ndisks + (4u * L.np + 31u) / 32u;
+    const uint32_t warps = cull_disk_units(L);
     if (launch_dependent(disk_kernel, dim3((warps + 3u) / 4u), dim3(128), s, L, T) != KL_OK)
       return KL_ECUDA;
     const bool mixed = p->precision == KL_MIXED;
