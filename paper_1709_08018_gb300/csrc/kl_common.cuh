@@ -834,8 +834,9 @@ __device__ __forceinline__ void mixed_item(uint32_t item, const Work& Wk, const 
 // consecutive points: the points of one subtree, which share all but their
 // last j letters and so lie close together.  Blocks of 9 .. 729 points form a
 // tree (a block's children are the three blocks of a third its size inside
-// it), and cull_disk bounds every block by a disk.  A prefix in pole form,
-// (u, v) = M (w_re, w_im) / |w|^2 + (ax, ay) with w = v + gamma, sends a disk
+// it), and the disk pass (cull_disk_unit) bounds every block by a disk.  A
+// prefix in pole form, (u, v) = M (w_re, w_im) / |w|^2 + (ax, ay) with
+// w = v + gamma, sends a disk
 // D(c, rho) with |c + gamma| > rho onto a set inside the disk of center
 // M (c + gamma) / q + (ax, ay) and radius |M| rho / q, q = |c + gamma|^2 - rho^2
 // (inversion maps a disk clear of the pole onto a disk; M is linear with
