@@ -836,9 +836,9 @@ __device__ __forceinline__ void mixed_item(uint32_t item, const Work& Wk, const 
 // tree (a block's children are the three blocks of a third its size inside
 // it), and the disk pass (cull_disk_unit) bounds every block by a disk.  A
 // prefix in pole form, (u, v) = M (w_re, w_im) / |w|^2 + (ax, ay) with
-// w = v + gamma, sends a disk
-// D(c, rho) with |c + gamma| > rho onto a set inside the disk of center
-// M (c + gamma) / q + (ax, ay) and radius |M| rho / q, q = |c + gamma|^2 - rho^2
+// w = v + gamma, sends a disk D(c, rho) with |c + gamma| > rho onto a set
+// inside the disk of center M (c + gamma) / q + (ax, ay) and radius
+// |M| rho / q, q = |c + gamma|^2 - rho^2
 // (inversion maps a disk clear of the pole onto a disk; M is linear with
 // operator norm |M|).  When that disk, widened by a margin larger than the
 // rounding error of the per-word map, lies inside one pixel or wholly outside
