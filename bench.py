@@ -32,7 +32,8 @@ if ROOT not in sys.path:
 import klsynth  # noqa: E402
 
 METRIC = "words/sec evaluated+splatted at depth d"
-FP32_OPS_PER_WORD = 12    # FP32 FMA-pipe operations of the mixed per-word map
+FP32_OPS_PER_WORD = 12    # FP32 operations of the mixed per-word map: w = v + gamma (2),
+                          # |w|^2 (2), M w (4), M w / |w|^2 + alpha (2), the two floors (2)
 FP64_OPS_PER_WORD = 13    # FP64 operations of the plain per-word map
 SMS = 152
 FP32_LANES_PER_SM = 128
@@ -561,7 +562,7 @@ def lod_config(kl, n_train: int = 64, n_test: int = 16, n_valid: int = 8):
     """Learned level-of-detail pruning: the network trained by the library's
     kernels on exact depth-22 renders of n_train groups (seed 1710), its
     pruning setting chosen on n_valid validation groups (seed 1712, target
-    IoU 0.9995), judged on n_test held-out groups (seed 1711) at 8192^2
+    IoU 0.9995), evaluated on n_test held-out groups (seed 1711) at 8192^2
     against the exact render."""
     import torch
     from paper_1709_08018_gb300 import lod

@@ -1,6 +1,6 @@
 """Learned level-of-detail pruning, end to end: training data from the exact
 renderer, training with the library's tensor-core MLP kernels, and the
-pruned render judged against the exact one.
+pruned render compared with the exact one.
 
 All arithmetic runs in the library (kl_lod_labels, kl_mlp_grad, kl_mlp_adam,
 kl_render_lod, kl_render); this module only selects samples and batches,
