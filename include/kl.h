@@ -105,7 +105,9 @@ typedef struct {
   uint32_t mode;           /* kl_mode: KL_LIMIT_SET (default) or KL_TILING; kl_render and
                               kl_render_noalloc only (the batch and level-of-detail calls
                               take KL_LIMIT_SET; kl_eval_words evaluates length-d words) */
-  uint32_t cull;           /* kl_render and kl_render_noalloc only (0 elsewhere): 0 (default)
+  uint32_t cull;           /* kl_render, kl_render_noalloc and batches (the level-of-detail
+                              calls take 0; their exact render of deferred nodes culls
+                              anyway, with the same image): 0 (default)
                               evaluates every word; 1 places whole blocks of words at once.
                               The suffix points of one subtree (blocks of 9 .. 729 points,
                               fewer for short words, each block's children being the three
@@ -225,9 +227,11 @@ KL_API int kl_render(const kl_params* p, uint32_t* d_image, uint64_t* d_counters
  * Batched render: a sweep over many groups in one persistent launch.
  *
  * n_groups parameter sets with their own traces/generators, seeds, depth and
- * prefix_len, sharing precision, image size, window, renorm_every,
+ * prefix_len, sharing precision, cull, image size, window, renorm_every,
  * parabolic_tol and the tuning knobs of params[0].  Every group's words are
- * rendered exactly as kl_render would render them, into its own image:
+ * rendered exactly as kl_render would render them, into its own image (with
+ * cull = 1, a culled batch: one persistent launch of the culling over all
+ * groups, each image that of the group's culled kl_render):
  * d_images holds n_groups images of width*height uint32, group k at offset
  * k*width*height; d_counters holds n_groups * KL_N_COUNTERS uint64.  All
  * groups' work items share one device queue (FP64 fallback items first), so
@@ -242,7 +246,8 @@ typedef struct kl_batch kl_batch;
 
 /* Validate the parameter sets and plan the batch on the current device.
  * *out receives a handle to free with kl_batch_destroy.  KL_EINVAL if the sets
- * do not share precision, image size and window; other codes as kl_render. */
+ * do not share precision, cull, image size and window, or a set has cull > 1;
+ * other codes as kl_render. */
 KL_API int kl_batch_create(const kl_params* params, uint32_t n_groups, kl_batch** out);
 
 /* Device workspace bytes the batch needs (256-byte aligned), 0 on a null handle. */
