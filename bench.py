@@ -1,19 +1,23 @@
 #!/usr/bin/env python
-"""Benchmark: words/s evaluated and splatted at depth d, on GB300.
+"""Benchmark: words/s evaluated and splatted at depth d, with the image IoU
+and the largest word-value error against the FP64 oracle.
 
-Workload (default): the gasket group ta = tb = 2, all 516,560,652 reduced
-words of length 18, 4096 x 4096 uint32 hit image over [-1.5, 1.5]^2, mixed
-precision (FP32 per-word map with FP64 prefix matrices, FP64 near-parabolic
-prefixes), which is the configuration the words/s metric is quoted on; the
-plain FP64 render of the same job is timed beside it.  One step = one full
-kl_render call: image and counter zeroing, prefix table, suffix table, the
-per-word render kernel and the FP64 fallback kernel.
+Workload (the headline): the near-cusp quasi-Fuchsian group ta = tb =
+1.91 + 0.05i (Grandma's recipe), all 4,649,045,868 reduced words of length 20,
+8192 x 8192 uint32 hit image over [-2, 2]^2, in FP64, the precision of the
+paper's renderer.  One step = one full kl_render call: image and counter
+clearing, the prefix and suffix tables and the per-word render kernel.  The
+same line carries the mixed-precision renders of this job and of the gasket
+at length 18 (4096^2) as secondary keys, each with its own IoU and error.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Rank 0 prints one JSON line.  With N > 1 (torchrun) every rank renders the
-whole job on its own GPU (independent replicas: weak scaling); value is the
-words of all ranks divided by the slowest rank's time.
+Rank 0 prints one JSON line.  With N > 1 (torchrun, one process per GPU) the
+job is sharded: rank k renders shard k of N (kl_params.shard_index /
+shard_count, a partition of the words by prefix slot) into its own image, and
+one reduce sums the uint32 images and the counters onto rank 0 inside the
+timed region (strong scaling: value = the job's words / the slowest rank's
+time).  The oracle legs (CPU baseline and accuracy) run at N = 1 only.
 """
 import argparse
 import hashlib
@@ -31,19 +35,21 @@ if ROOT not in sys.path:
 
 import klsynth  # noqa: E402
 
-METRIC = "words/sec evaluated+splatted at depth d"
+METRIC = "words/sec evaluated+splatted at depth d; image IoU and max |\u0394z| vs FP64 oracle"
 FP32_OPS_PER_WORD = 12    # FP32 operations of the mixed per-word map: w = v + gamma (2),
                           # |w|^2 (2), M w (4), M w / |w|^2 + alpha (2), the two floors (2)
-FP64_OPS_PER_WORD = 13    # FP64 operations of the plain per-word map
+FP64_OPS_PER_WORD = 13    # FP64 operations of the plain per-word map: w = v + gamma (2),
+                          # |w|^2 (2), reciprocal refinement (3), M w (4), final FMAs (2)
 SMS = 152
 FP32_LANES_PER_SM = 128
 FP64_LANES_PER_SM = 2
+SAMPLE_N = 1_000_000      # seeded index sample for the word-value errors
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -57,12 +63,23 @@ def parse():
     return ap.parse_args()
 
 
-def workload():
-    c = klsynth.C2
-    return c, {"workload": "gasket ta=tb=2, all reduced words of length 18, 4096x4096 uint32, "
-                           "window [-1.5,1.5]^2, mixed FP32/FP64",
-               "group": "grandma ta=tb=2+0i", "depth": c.depth, "words_per_step": c.n_words,
-               "image": [c.width, c.height], "window": list(c.window),
+def describe(c, precision: str) -> str:
+    tr = f"{c.group.ta.real:g}" + (f"{c.group.ta.imag:+g}i" if c.group.ta.imag else "")
+    x0, x1, y0, y1 = c.window
+    return (f"grandma ta=tb={tr}, all {c.n_words:,} reduced words of length {c.depth}, "
+            f"{c.width}x{c.height} uint32 hit image over [{x0:g},{x1:g}]x[{y0:g},{y1:g}], "
+            f"{precision}")
+
+
+def workload(world: int = 1):
+    """The headline job: the near-cusp group at length 20, 8192^2, FP64."""
+    c = klsynth.C3
+    return c, {"workload": describe(c, "FP64"),
+               "group": "grandma ta=tb=1.91+0.05i (near-cusp, quasi-Fuchsian)",
+               "depth": c.depth, "words_per_step": c.n_words, "image": [c.width, c.height],
+               "window": list(c.window), "precision": "fp64",
+               "parallelism": ("1 GPU" if world == 1 else
+                               f"{world} shards by prefix slot, uint32 image sum (NCCL reduce)"),
                "l2": "flushed between timed steps (256 MiB write)"}
 
 
@@ -178,51 +195,87 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources; else None."""
+def traffic_for(kernel: str, workload_name: str):
+    """DRAM bytes per launch of `kernel` on `workload_name` from the committed
+    ncu summary, if it was taken on the current kernel sources; else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    k = rec.get(kernel)
+    k = rec.get(f"{kernel}@{workload_name}")
     if not k or k.get("source_hash") != source_hash():
         return None
     return k.get("dram_bytes_per_launch")
 
 
-def cpu_baseline(cfg, budget_s=15.0):
-    """The oracle's tree walk on all host cores over the first jobs of the same
-    render (equal-size jobs), sized to about budget_s seconds."""
+# ---------------------------------------------------------------------------
+# oracle legs (CPU): the baseline and the accuracy figures
+
+def oracle_render(cfg, threads=None):
+    """The oracle's tree-walk render of a whole workload on the host cores,
+    edge words logged at the FP64 tolerance band (1e-9 in z); returns
+    (render, seconds, threads)."""
     import oracle
+    threads = threads or os.cpu_count() or 1
     g, s = oracle.group(cfg.group.ta, cfg.group.tb)
-    jobs = oracle.tree_jobs(cfg.depth)
-    threads = os.cpu_count() or 1
-    per_job = cfg.n_words // jobs
+    sx = cfg.width / (cfg.window[1] - cfg.window[0])
     t0 = time.perf_counter()
-    oracle.render(g, s, cfg.depth, cfg.window, cfg.width, cfg.height, threads=threads,
-                  jobs=(0, min(jobs, threads)))
-    dt = time.perf_counter() - t0
-    done, words, elapsed = min(jobs, threads), per_job * min(jobs, threads), dt
-    if elapsed < budget_s and done < jobs:
-        more = int(min(jobs - done, max(1, (budget_s - elapsed) / max(dt, 1e-9) * done)))
-        t0 = time.perf_counter()
-        oracle.render(g, s, cfg.depth, cfg.window, cfg.width, cfg.height, threads=threads,
-                      jobs=(done, done + more))
-        elapsed += time.perf_counter() - t0
-        done += more
-        words += per_job * more
-    return {"value": words / elapsed, "unit": "words/s", "cores": threads, "kind": "oracle",
-            "sample": f"tree-walk jobs 0..{done - 1} of {jobs} (words with fixed innermost 5 "
-                      f"letters; {words} of {cfg.n_words} words), FP64, {threads} threads",
-            "seconds": elapsed}
+    r = oracle.render(g, s, cfg.depth, cfg.window, cfg.width, cfg.height, threads=threads,
+                      eta=1e-9 * sx, edge_cap=1 << 22)
+    return r, time.perf_counter() - t0, threads
+
+
+def oracle_sample(cfg):
+    """The seeded index sample and its word values by the oracle's per-word
+    definition (one orbit of d maps per word)."""
+    import oracle
+    idx = klsynth.index_sample(klsynth.SAMPLE_SEED, SAMPLE_N, cfg.depth)
+    g, s = oracle.group(cfg.group.ta, cfg.group.tb)
+    return idx, oracle.evaluate(g, s, cfg.depth, idx)
+
+
+def cpu_baseline(cfg, rend, secs, threads):
+    return {"value": cfg.n_words / secs, "unit": "words/s", "cores": threads, "kind": "oracle",
+            "sample": f"the whole workload: all {cfg.n_words} words of length {cfg.depth} "
+                      f"(FP64 tree walk, {threads} threads, edge words logged)",
+            "seconds": secs}
+
+
+def occupancy_iou(a, b) -> float:
+    oa, ob = a > 0, b > 0
+    union = int((oa | ob).sum())
+    return 1.0 if union == 0 else int((oa & ob).sum()) / union
+
+
+def image_agreement(got, ref):
+    """Agreement of a GPU image (H, W uint32) with an oracle render."""
+    import numpy as np
+    d = got.astype(np.int64) - ref.image.astype(np.int64)
+    return {"iou_vs_oracle": occupancy_iou(got, ref.image),
+            "pixels_differing": int((d != 0).sum()), "l1_hit_difference": int(np.abs(d).sum()),
+            "oracle_edge_words": int(ref.edge_total)}
+
+
+def sample_dz(cfg, uv, z):
+    """Largest |dz| / max(1, |z|) and |dz| over the sample: uv are the GPU's
+    pixel coordinates (kl_eval_words), z the oracle's word values."""
+    import numpy as np
+    x0, x1, y0, y1 = cfg.window
+    sx, sy = cfg.width / (x1 - x0), cfg.height / (y1 - y0)
+    zg = (x0 + uv[:, 0] / sx) + 1j * (y1 - uv[:, 1] / sy)
+    fin = np.isfinite(z) & (np.abs(z) < 1e12)
+    dz = np.abs(zg[fin] - z[fin])
+    return {"max_dz_rel": float((dz / np.maximum(1.0, np.abs(z[fin]))).max()),
+            "max_dz_abs": float(dz.max()), "sample": f"{SAMPLE_N} indices, SplitMix64(1709)"}
 
 
 def run_reference(args):
-    """The CPU oracle as the reference arm (rank 0 only)."""
+    """The CPU oracle as the reference arm (rank 0 only), on the headline
+    workload: each step renders a bounded sample of it (equal-size tree-walk
+    jobs), sized so that warmup + steps end in about two minutes."""
     world, rank, _ = dist_env()
-    cfg, config = workload()
+    cfg, config = workload(world)
     if rank != 0:
         return
     import oracle
@@ -230,8 +283,6 @@ def run_reference(args):
     jobs = oracle.tree_jobs(cfg.depth)
     threads = os.cpu_count() or 1
     per_job = cfg.n_words // jobs
-    # each step renders `chunk` equal-size jobs, sized so that warmup + steps
-    # end in about two minutes
     t0 = time.perf_counter()
     oracle.render(g, s, cfg.depth, cfg.window, cfg.width, cfg.height, threads=threads,
                   jobs=(0, threads))
@@ -256,7 +307,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "words/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * secs / len(times), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config,
             "cpu_baseline": {"value": value, "unit": "words/s", "cores": threads,
                              "kind": "oracle", "sample": sample},
@@ -636,15 +687,132 @@ def make_max_over_ranks(world: int, device):
     return max_over_ranks
 
 
-def job_rate(world: int, words_per_step: int, steps: int, local_ms: float, max_over_ranks):
-    """Whole-job throughput of `world` replicas: every rank renders
-    words_per_step words per step; the job's time is the slowest rank's.
-    Returns (words/s over all ranks, job milliseconds)."""
+def make_image_sum(world: int):
+    """(image, counters) -> both summed element-wise over the ranks into rank
+    0's tensors (one reduce each).  The uint32 hit counts travel as int32:
+    two's-complement addition wraps exactly as uint32 addition does."""
+    def image_sum(image, counters):
+        if world == 1:
+            return
+        import torch.distributed as dist
+        dist.reduce(image, dst=0, op=dist.ReduceOp.SUM)
+        dist.reduce(counters, dst=0, op=dist.ReduceOp.SUM)
+    return image_sum
+
+
+def shard_fields(world: int, rank: int) -> dict:
+    """kl_params fields of rank `rank`'s shard of a job split over `world`
+    processes (none for one process)."""
+    return {"shard_index": rank, "shard_count": world} if world > 1 else {}
+
+
+def job_rate(job_words: int, steps: int, local_ms: float, max_over_ranks):
+    """Whole-job throughput: `steps` steps of a job of job_words words (all
+    ranks together); the job's time is the slowest rank's.  Returns (words/s,
+    job milliseconds)."""
     total_ms = max_over_ranks(local_ms)
-    return world * words_per_step * steps / (total_ms / 1000.0), total_ms
+    return job_words * steps / (total_ms / 1000.0), total_ms
+
+
+def events(stream, n):
+    import torch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+    for e in ev:
+        e.record(stream)   # create the underlying CUDA events
+    return ev
+
+
+def timed_render(kl, r, flush, stream, K, dev, image_sum=None):
+    """K renders, each after an L2 flush, timed with CUDA events on `stream`
+    (step = the kl_render call, plus the image sum when given) and with the
+    library's events around its per-word kernel.  Returns (step ms list,
+    kernel ms list)."""
+    import torch
+    st0, st1, kn0, kn1 = events(stream, K), events(stream, K), events(stream, K), events(stream, K)
+    torch.cuda.synchronize(dev)
+    for k in range(K):
+        flush.fill_(k & 0xFF)                   # L2 flush, outside the timed events
+        kl.set_profile_events(kn0[k], kn1[k])
+        st0[k].record(stream)
+        r()
+        if image_sum is not None:
+            image_sum(r.image, r.counters)
+        st1[k].record(stream)
+    kl.set_profile_events()
+    torch.cuda.synchronize(dev)
+    return ([st0[k].elapsed_time(st1[k]) for k in range(K)],
+            [kn0[k].elapsed_time(kn1[k]) for k in range(K)])
+
+
+def fp_peaks():
+    pk = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    return (SMS * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12,
+            SMS * FP64_LANES_PER_SM * sm_max * 1e6 / 1e12)
+
+
+def roofline64(words, kern_ms, wl):
+    fp64_peak = fp_peaks()[1]
+    ach = words * FP64_OPS_PER_WORD / (kern_ms / 1000.0) / 1e12
+    return {"bound": "alu", "kernel": "render64_kernel", "achieved": ach, "peak": fp64_peak,
+            "unit": "T FP64-op/s", "frac": ach / fp64_peak,
+            "peak_kind": "derived: 152 SMs x 2 FP64 lanes x max SM clock (DFMA probe: "
+                         "1.99/clk/SM)",
+            "ops_per_word": FP64_OPS_PER_WORD, "traffic": traffic_for("render64_kernel", wl),
+            "kernel_ms": kern_ms}
+
+
+def roofline32(words_fp32, kern_ms, wl):
+    fp32_peak = fp_peaks()[0]
+    ach = words_fp32 * FP32_OPS_PER_WORD / (kern_ms / 1000.0) / 1e12
+    return {"bound": "alu", "kernel": "render_mixed_kernel", "achieved": ach, "peak": fp32_peak,
+            "unit": "T FP32-op/s", "frac": ach / fp32_peak,
+            "peak_kind": "derived: 152 SMs x 128 FP32 lanes x max SM clock",
+            "ops_per_word": FP32_OPS_PER_WORD,
+            "traffic": traffic_for("render_mixed_kernel", wl), "kernel_ms": kern_ms}
+
+
+def secondary(kl, cfg, prec, flush, stream, dev, K):
+    """One more whole-job render timed like the headline (N = 1): its rates,
+    the roofline of its per-word kernel, its atomics and its image (host copy)
+    for the accuracy figures."""
+    import numpy as np
+    p = kl.params_init(cfg.group.ta, cfg.group.tb, cfg.depth, cfg.width, cfg.height,
+                       cfg.window, prec)
+    r = kl.Renderer(p, device=dev)
+    for _ in range(3):
+        r()
+    step_ms, kern_ms = timed_render(kl, r, flush, stream, K, dev)
+    ms, kms = statistics.median(step_ms), statistics.median(kern_ms)
+    cnt = [int(x) for x in r.counters.cpu().tolist()]
+    assert cnt[0] + cnt[1] == cfg.n_words
+    out = {"workload": describe(cfg, "FP64" if prec == kl.FP64 else
+                                "mixed (FP32 per-word map, FP64 prefixes and fallback words)"),
+           "words_per_step": cfg.n_words, "ms_per_step": ms,
+           "words_per_s": cfg.n_words / (ms / 1000.0), "steps": K,
+           "roofline": (roofline64(cfg.n_words, kms, cfg.name) if prec == kl.FP64 else
+                        roofline32(cfg.n_words - cnt[2], kms, cfg.name)),
+           "counters": {"in_window": cnt[0], "dropped": cnt[1], "fp64_words": cnt[2],
+                        "atomics": cnt[3]},
+           "atomics_per_s": cnt[3] / (kms / 1000.0)}
+    img = r.image.cpu().numpy().view(np.uint32).copy()
+    del r
+    return out, img
+
+
+def eval_sample(kl, cfg, prec, dev):
+    """GPU pixel coordinates (kl_eval_words) of the seeded index sample."""
+    import numpy as np
+    import torch
+    idx = klsynth.index_sample(klsynth.SAMPLE_SEED, SAMPLE_N, cfg.depth)
+    p = kl.params_init(cfg.group.ta, cfg.group.tb, cfg.depth, cfg.width, cfg.height,
+                       cfg.window, prec)
+    t = torch.from_numpy(np.ascontiguousarray(idx).view(np.int64)).to(dev)
+    return kl.eval_words(p, t).cpu().numpy()
 
 
 def run_ours(args):
+    import numpy as np
     import torch
     import paper_1709_08018_gb300 as kl
 
@@ -654,76 +822,45 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    cfg, config = workload()
+    cfg, config = workload(world)
     N = cfg.n_words
 
     barrier = make_barrier(world)
     max_over_ranks = make_max_over_ranks(world, dev)
+    image_sum = make_image_sum(world)
 
     p = kl.params_init(cfg.group.ta, cfg.group.tb, cfg.depth, cfg.width, cfg.height,
-                       cfg.window, kl.MIXED)
+                       cfg.window, kl.FP64, **shard_fields(world, rank))
     r = kl.Renderer(p, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def events(n):
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
-        for e in ev:
-            e.record(stream)   # create the underlying CUDA events
-        return ev
-
     for _ in range(args.warmup):
         r()
+        image_sum(r.image, r.counters)
     torch.cuda.synchronize(dev)
 
     K = args.steps
-    st0, st1, kn0, kn1 = events(K), events(K), events(K), events(K)
-    torch.cuda.synchronize(dev)
     sampler = ClockSampler(local)
     with sampler:
         barrier()
-        torch.cuda.synchronize(dev)
-        for k in range(K):
-            flush.fill_(k & 0xFF)                   # L2 flush, outside the timed events
-            kl.set_profile_events(kn0[k], kn1[k])
-            st0[k].record(stream)
-            r()
-            st1[k].record(stream)
-        kl.set_profile_events()
-        torch.cuda.synchronize(dev)
+        step_ms, kern_ms = timed_render(kl, r, flush, stream, K, dev, image_sum)
         barrier()
     clocks = sampler.summary()
-    step_ms = [st0[k].elapsed_time(st1[k]) for k in range(K)]
-    kern_ms = [kn0[k].elapsed_time(kn1[k]) for k in range(K)]
-    value, total_ms = job_rate(world, N, K, sum(step_ms), max_over_ranks)
-    cnt = r.counters.cpu().tolist()
-    fp64_words = int(cnt[2])
+    value, total_ms = job_rate(N, K, sum(step_ms), max_over_ranks)
+    # one more render whose image and counters are summed: rank 0 holds the job's
+    r()
+    image_sum(r.image, r.counters)
+    cnt = [int(x) for x in r.counters.cpu().tolist()]
+    if rank == 0:
+        assert cnt[0] + cnt[1] == N, cnt
+    kern_s = statistics.mean(kern_ms) / 1000.0
 
-    # plain FP64 render of the same job, timed the same way
-    p64 = kl.params_init(cfg.group.ta, cfg.group.tb, cfg.depth, cfg.width, cfg.height,
-                         cfg.window, kl.FP64)
-    r64 = kl.Renderer(p64, device=dev)
-    r64()
-    K64 = max(3, min(10, K // 5))
-    a0, a1, b0, b1 = events(K64), events(K64), events(K64), events(K64)
-    torch.cuda.synchronize(dev)
-    for k in range(K64):
-        flush.fill_(k & 0xFF)
-        kl.set_profile_events(b0[k], b1[k])
-        a0[k].record(stream)
-        r64()
-        a1[k].record(stream)
-    kl.set_profile_events()
-    torch.cuda.synchronize(dev)
-    fp64_step_ms = statistics.median(a0[k].elapsed_time(a1[k]) for k in range(K64))
-    fp64_kern_ms = statistics.median(b0[k].elapsed_time(b1[k]) for k in range(K64))
-    del r64
-
-    # end to end through the public API: host parameters in, image and
-    # counters copied back to pinned host memory every step.  Two image
-    # buffers: step k+1 renders while step k's image is copied out on a second
-    # stream; the time is the span of all KE steps (CUDA events), L2 flushes
-    # included.
+    # end to end through the public API: host parameters in, the job's image
+    # and counters copied back to pinned host memory every step (rank 0).  Two
+    # image buffers: step k+1 renders while step k's image is copied out on a
+    # second stream; the time is the span of all KE steps (CUDA events), L2
+    # flushes included.
     rb = [r, kl.Renderer(p, device=dev)]
     host_img = [torch.empty((cfg.height, cfg.width), dtype=torch.int32, pin_memory=True)
                 for _ in range(2)]
@@ -732,8 +869,8 @@ def run_ours(args):
     copy_stream = torch.cuda.Stream(dev)
     rendered = [torch.cuda.Event() for _ in range(2)]
     copied = [torch.cuda.Event() for _ in range(2)]
-    KE = max(4, min(K, 20))
-    e0, e1 = events(1)[0], events(1)[0]
+    KE = max(4, min(K, 10))
+    e0, e1 = events(stream, 1)[0], events(stream, 1)[0]
     rb[1]()
     torch.cuda.synchronize(dev)
     barrier()
@@ -744,75 +881,101 @@ def run_ours(args):
         if k >= 2:
             stream.wait_event(copied[b])          # buffer b's previous image is out
         kl.render(rb[b].p, rb[b].image, rb[b].counters, rb[b].workspace, stream)
+        image_sum(rb[b].image, rb[b].counters)
         rendered[b].record(stream)
-        copy_stream.wait_event(rendered[b])
-        with torch.cuda.stream(copy_stream):
-            host_img[b].copy_(rb[b].image, non_blocking=True)
-            host_cnt[b].copy_(rb[b].counters, non_blocking=True)
+        if rank == 0:
+            copy_stream.wait_event(rendered[b])
+            with torch.cuda.stream(copy_stream):
+                host_img[b].copy_(rb[b].image, non_blocking=True)
+                host_cnt[b].copy_(rb[b].counters, non_blocking=True)
         copied[b].record(copy_stream)
     stream.wait_event(copied[0])
     stream.wait_event(copied[1])
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    for b in range(2):
-        assert int(host_cnt[b][0]) + int(host_cnt[b][1]) == N
-        assert int(host_img[b].sum(dtype=torch.int64)) == int(host_cnt[b][0])
-    e2e_value, e2e_ms = job_rate(world, N, KE, e0.elapsed_time(e1), max_over_ranks)
+    if rank == 0:
+        for b in range(2):
+            assert int(host_cnt[b][0]) + int(host_cnt[b][1]) == N
+            hits = int(host_img[b].numpy().view(np.uint32).sum(dtype=np.uint64))
+            assert hits == int(host_cnt[b][0]) % (1 << 64), (hits, int(host_cnt[b][0]))
+    e2e_value, e2e_ms = job_rate(N, KE, e0.elapsed_time(e1), max_over_ranks)
+    del rb, host_img
 
-    pk = peaks()
-    sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    fp32_peak = SMS * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12     # T lane-ops/s
-    fp64_peak = SMS * FP64_LANES_PER_SM * sm_max * 1e6 / 1e12
-    kern_s = statistics.mean(kern_ms) / 1000.0
-    words_fp32 = N - fp64_words
-    achieved = words_fp32 * FP32_OPS_PER_WORD / kern_s / 1e12
-    roofline = {"bound": "alu", "kernel": "render_mixed_kernel", "achieved": achieved,
-                "peak": fp32_peak, "unit": "T FP32-op/s", "frac": achieved / fp32_peak,
-                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x max SM clock",
-                "ops_per_word": FP32_OPS_PER_WORD,
-                "traffic": traffic_for("render_mixed_kernel"),
-                "kernel_ms": statistics.mean(kern_ms),
-                "kernel_share_of_step": statistics.mean(kern_ms) / statistics.mean(step_ms)}
-    fp64_ach = N * FP64_OPS_PER_WORD / (fp64_kern_ms / 1000.0) / 1e12
-    plain = {"words_per_s": N / (fp64_step_ms / 1000.0), "ms_per_step": fp64_step_ms,
-             "kernel_ms": fp64_kern_ms,
-             "roofline": {"bound": "alu", "kernel": "render64_kernel", "achieved": fp64_ach,
-                          "peak": fp64_peak, "unit": "T FP64-op/s", "frac": fp64_ach / fp64_peak,
-                          "peak_kind": "derived: 152 SMs x 2 FP64 lanes x max SM clock",
-                          "ops_per_word": FP64_OPS_PER_WORD,
-                          "traffic": traffic_for("render64_kernel")}}
     line = {"metric": METRIC, "value": value, "unit": "words/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": config, "clocks": clocks, "roofline": roofline,
+            "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config, "clocks": clocks,
+            "roofline": dict(roofline64(N if world == 1 else N / world,
+                                        statistics.mean(kern_ms), cfg.name),
+                             kernel_share_of_step=statistics.mean(kern_ms) /
+                             statistics.mean(step_ms)),
             "e2e": {"value": e2e_value, "unit": "words/s",
                     "h2d_bytes_per_step": __import__("ctypes").sizeof(r.p),
                     "d2h_bytes_per_step": cfg.width * cfg.height * 4 + kl.KL_N_COUNTERS * 8,
                     "overlap": "the copy of step k's image overlaps the render of step k+1 "
                                "(two image buffers, two streams)"},
-            "gpu_launches": 3 * K,  # per step: parts, combine and render
-            "counters": {"in_window": int(cnt[0]), "dropped": int(cnt[1]),
-                         "fp64_words": fp64_words, "atomics": int(cnt[3])},
-            "plain_fp64": plain,
-            "speedup_mixed_over_fp64": fp64_step_ms / (total_ms / K)}
-    if not args.no_tiling:
-        line["tiling"] = tiling_config(kl, dev, K, flush)
-    if not args.no_scan:
-        line["paper_scan"] = scan_config(kl, dev, flush)
-    if not args.no_maskit:
-        line["maskit_example"] = maskit_config(kl, dev, flush)
-    if not args.no_multiseed:
-        line["multiseed"] = multiseed_config(kl, dev, flush)
-    if not args.no_cull:
-        line["culled"] = cull_config(kl, dev, flush)
-    if not args.no_batch:
-        line["batch_sweep"] = batch_sweep(kl, dev, K)
-    if not args.no_lod:
-        line["lod"] = lod_config(kl)
-        line["lod"]["speedup_over_plain_fp64"] = (
-            line["lod"]["words_per_s_pruned"] / plain["words_per_s"])
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cfg)
+            "gpu_launches": 3 * K,  # per step: parts, combine and the render kernel
+            "counters": {"in_window": cnt[0], "dropped": cnt[1], "fp64_words": cnt[2],
+                         "atomics": cnt[3]},
+            "atomics_per_s": cnt[3] / world / kern_s}
+    if world == 1:
+        fp64_img = r.image.cpu().numpy().view(np.uint32).copy()
+    del r
+    torch.cuda.synchronize(dev)
+
+    if world == 1:
+        KS = max(5, min(K, 20))
+        mixed3, mixed3_img = secondary(kl, klsynth.C3, kl.MIXED, flush, stream, dev, KS)
+        mixed3["speedup_over_fp64"] = (total_ms / K) / mixed3["ms_per_step"]
+        mixed2, mixed2_img = secondary(kl, klsynth.C2, kl.MIXED, flush, stream, dev, KS)
+        fp64_2, fp64_2_img = secondary(kl, klsynth.C2, kl.FP64, flush, stream, dev,
+                                       max(3, KS // 4))
+        mixed2["speedup_over_fp64"] = fp64_2["ms_per_step"] / mixed2["ms_per_step"]
+        uv = {(c.name, prec): eval_sample(kl, c, prec, dev)
+              for c in (klsynth.C3, klsynth.C2) for prec in (kl.FP64, kl.MIXED)}
+        if not args.no_cpu_baseline:
+            # the oracle legs: the whole headline workload (the CPU baseline and
+            # the reference image), the gasket render and the two samples
+            ref3, secs3, threads = oracle_render(klsynth.C3)
+            line["cpu_baseline"] = cpu_baseline(klsynth.C3, ref3, secs3, threads)
+            idx3, z3 = oracle_sample(klsynth.C3)
+            line["accuracy"] = dict(image_agreement(fp64_img, ref3),
+                                    **sample_dz(klsynth.C3, uv[(klsynth.C3.name, kl.FP64)], z3))
+            mixed3["accuracy"] = dict(image_agreement(mixed3_img, ref3),
+                                      **sample_dz(klsynth.C3, uv[(klsynth.C3.name, kl.MIXED)],
+                                                  z3))
+            del ref3
+            ref2, _, _ = oracle_render(klsynth.C2)
+            idx2, z2 = oracle_sample(klsynth.C2)
+            mixed2["accuracy"] = dict(image_agreement(mixed2_img, ref2),
+                                      **sample_dz(klsynth.C2, uv[(klsynth.C2.name, kl.MIXED)],
+                                                  z2))
+            fp64_2["accuracy"] = dict(image_agreement(fp64_2_img, ref2),
+                                      **sample_dz(klsynth.C2, uv[(klsynth.C2.name, kl.FP64)],
+                                                  z2))
+            line["iou_vs_oracle"] = line["accuracy"]["iou_vs_oracle"]
+            line["max_dz_rel"] = line["accuracy"]["max_dz_rel"]
+            del ref2
+        del fp64_img, mixed3_img, mixed2_img, fp64_2_img
+        line["mixed_nearcusp_d20"] = mixed3
+        line["mixed_gasket_d18"] = mixed2
+        line["fp64_gasket_d18"] = fp64_2
+        if not args.no_tiling:
+            line["tiling"] = tiling_config(kl, dev, K, flush)
+        if not args.no_scan:
+            line["paper_scan"] = scan_config(kl, dev, flush)
+        if not args.no_maskit:
+            line["maskit_example"] = maskit_config(kl, dev, flush)
+        if not args.no_multiseed:
+            line["multiseed"] = multiseed_config(kl, dev, flush)
+        if not args.no_cull:
+            line["culled"] = cull_config(kl, dev, flush)
+        if not args.no_batch:
+            line["batch_sweep"] = batch_sweep(kl, dev, K)
+        if not args.no_lod:
+            line["lod"] = lod_config(kl)
+            line["lod"]["speedup_over_plain_fp64"] = (
+                line["lod"]["words_per_s_pruned"] / fp64_2["words_per_s"])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

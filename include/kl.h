@@ -124,6 +124,29 @@ typedef struct {
                               the per-word default (suffixes of d-1 letters up to 9, then
                               d/2+1, at most 12), so kl_workspace_bytes depends on this
                               field. */
+  uint32_t shard_index;    /* Sharded render, one process per GPU: kl_render (and
+                              kl_render_noalloc) with shard_count = n > 1 draws only the
+                              words of shard shard_index (0 .. n-1): those whose prefix
+                              slot r lies in [floor(k np / n), floor((k+1) np / n)), k =
+                              shard_index, np = 3^(p-1), p = the render's prefix length
+                              (prefix_len, or the length the render chooses for 0).  The
+                              prefix slot of a word w_1 .. w_d is r = the base-3 ranks of
+                              w_{p-1}, ..., w_1, most significant first, each among the
+                              three letters other than the inverse of its right
+                              neighbour.  Every word of a prefix slot is in the same shard,
+                              so the n shards partition the words, with 4 * 3^(d-p) times
+                              the shard's slot count each (equal to within one slot); each
+                              shard's image and counters are exactly the part of the whole
+                              render that its words make, so the element-wise sums (uint32,
+                              modulo 2^32) of the n shards' images and counters are the
+                              whole render's.  Limit-set mode only; kl_eval_words ignores
+                              the shard fields; batches and the level-of-detail calls
+                              return KL_EINVAL for shard_count > 1.  The paper's loop is
+                              one index range on one machine; independent index ranges
+                              are what makes this split possible (Sec. "The revised
+                              deterministic approach": the words are in the integers). */
+  uint32_t shard_count;    /* 0 or 1: the whole render (default); n > 1: n shards, with
+                              shard_index < n (else KL_EINVAL) */
 } kl_params;
 
 /* Counters written by kl_render (uint64 each). */
@@ -423,9 +446,13 @@ KL_API int kl_render_fsa(const kl_fsa* f, const kl_params* p, uint32_t* d_image,
  *    loads the library, until the process exits, whether or not this call is
  *    used.  A request whose kl_workspace_bytes(p) exceeds it returns
  *    KL_ENOSPACE before anything is enqueued.
- *  - The first call on each device looks up the array's device address with
- *    that device current (cudaGetSymbolAddress) and caches it; make that first
- *    call before any stream capture.
+ *  - Every call whose stream is not capturing looks up the array's device
+ *    address with the calling device current (cudaGetSymbolAddress, which
+ *    allocates nothing), so the address always belongs to the current
+ *    context, also after a device reset.  A call on a capturing stream uses
+ *    the address the last uncaptured call on that device found, and returns
+ *    KL_EINVAL if there was none: make one uncaptured call on each device
+ *    before any stream capture.
  *  - All calls share the one array, which keeps the last call's tables; the
  *    render rebuilds and re-zeroes what it needs on every call.  Calls that
  *    overlap on the GPU (concurrent streams, or several host threads) race on

@@ -22,5 +22,9 @@ Parity status per function (what pins it is in ``tests/test_oracle_pins.py``):
   render_multiseed its point; consecutive points are images under the
                  generators (conjugation); brute-force scan with fixed seeds
   mlp (numpy)    pinned: central finite differences, closed-form tiny nets
+  prefix_rank,   pinned: (w_p, r) is a bijection of the prefixes onto
+  render_shard   4 x 3^(p-1) slots (brute force); the shards' images and
+                 counters sum to the whole per-word render; shard word counts
+                 equal the closed form 4 3^(d-p) (slots of the shard)
 """
 from .oracle import *  # noqa: F401,F403

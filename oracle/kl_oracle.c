@@ -335,6 +335,76 @@ OR_EXPORT int or_render_indexed(const double* gens, const double* seeds8, int d,
 }
 
 /*
+ * Sharded render (one process per GPU renders a share of the words and the
+ * shares' images are summed).  The paper's loop runs over one index range on
+ * one machine; its words are independent of one another (each is pulled out
+ * of its own integer, Sec. "The revised deterministic approach"), which is
+ * what allows any partition.  The library's partition is by prefix slot: with
+ * prefix length p, the prefix slot of w_1 .. w_d is
+ *     r = sum_{k=1}^{p-1} rank_k 3^(k-1),
+ * rank_k = the position of w_k among the three letters other than the inverse
+ * of its right neighbour w_{k+1}, in increasing order (so w_{p-1} is the most
+ * significant digit).  Shard k of n holds the words with
+ *     floor(k 3^(p-1) / n) <= r < floor((k+1) 3^(p-1) / n).
+ */
+static uint64_t prefix_rank(const uint8_t* w, int p) {
+  uint64_t r = 0, place = 1;
+  for (int k = 0; k + 1 < p; ++k) {   /* k = 0 is w_1 (weight 3^0) */
+    int banned = (w[k + 1] + 2) & 3;
+    int rank = -1, seen = -1;
+    for (int x = 0; x < 4; ++x) {
+      if (x == banned) continue;
+      ++seen;
+      if (x == w[k]) { rank = seen; break; }
+    }
+    r += (uint64_t)rank * place;
+    place *= 3;
+  }
+  return r;
+}
+
+/* Prefix slot ranks of n word indices at prefix length p (1 <= p <= d). */
+OR_EXPORT int or_prefix_rank(int d, int p, const uint64_t* idx, uint64_t n, uint64_t* out) {
+  if (or_word_count(d) == 0 || p < 1 || p > d) return -1;
+  uint8_t w[64];
+  for (uint64_t t = 0; t < n; ++t) {
+    if (or_decode(d, idx[t], w) != 0) return -1;
+    out[t] = prefix_rank(w, p);
+  }
+  return 0;
+}
+
+/* Per-word render of shard k of n (see above) of the words of length d. */
+OR_EXPORT int or_render_shard(const double* gens, const double* seeds8, int d,
+                              const double* window, int width, int height, int p, int shard,
+                              int n_shards, uint32_t* image, uint64_t* counters, double eta,
+                              uint64_t* edge_idx, double* edge_uv, uint64_t edge_cap,
+                              uint64_t* edge_count) {
+  mat2 g[4]; cx seeds[4];
+  load_group(gens, seeds8, g, seeds);
+  uint64_t n = or_word_count(d);
+  if (n == 0 || d > 40 || p < 1 || p > d || n_shards < 1 || shard < 0 || shard >= n_shards ||
+      width <= 0 || height <= 0)
+    return -1;
+  uint64_t np = pow3(p - 1);
+  uint64_t lo = (uint64_t)shard * np / (uint64_t)n_shards;
+  uint64_t hi = (uint64_t)(shard + 1) * np / (uint64_t)n_shards;
+  view_t v = make_view(window, width, height, eta);
+  uint64_t dummy = 0;
+  sink_t s = {image, 0, 0, edge_idx, edge_uv, edge_cap, edge_count ? edge_count : &dummy};
+  uint8_t w[64];
+  for (uint64_t i = 0; i < n; ++i) {
+    or_decode(d, i, w);
+    uint64_t r = prefix_rank(w, p);
+    if (r < lo || r >= hi) continue;
+    splat(&v, &s, i, word_value(g, seeds, w, d));
+  }
+  counters[0] += s.in_window;
+  counters[1] += s.dropped;
+  return 0;
+}
+
+/*
  * Tree-walk render ("mode B"): the same word values, reached from the inside
  * out.  A node at level k holds the value of its k innermost letters
  * (w_{d-k+1} .. w_d) applied to the seed of w_d; its children prepend one

@@ -43,6 +43,10 @@ def lib():
         L.or_fsa_count.restype = I
         L.or_render_fsa.argtypes = [I, P, P, P, I, P, I, I, U64, U64, P, P, D, P, P, U64, P]
         L.or_render_fsa.restype = I
+        L.or_prefix_rank.argtypes = [I, I, P, U64, P]
+        L.or_prefix_rank.restype = I
+        L.or_render_shard.argtypes = [P, P, I, P, I, I, I, I, I, P, P, D, P, P, U64, P]
+        L.or_render_shard.restype = I
         L.or_tree_jobs.argtypes = [I]
         L.or_tree_jobs.restype = I
         L.or_render_tree.restype = I
@@ -185,6 +189,43 @@ def render(gens, seeds8, d: int, window: Sequence[float], width: int, height: in
         raise ValueError(mode)
     if rc != 0:
         raise ValueError("bad render arguments")
+    k = int(min(int(ecount[0]), cap))
+    return Render(img, int(cnt[0]), int(cnt[1]), eidx[:k].copy(),
+                  euv[:2 * k].reshape(k, 2).copy(), int(ecount[0]))
+
+
+def prefix_rank(d: int, p: int, indices) -> np.ndarray:
+    """Prefix slot ranks r (uint64) of the given words at prefix length p:
+    the ranks of w_{p-1}, ..., w_1 among the letters other than the inverse of
+    their right neighbour, base 3, w_{p-1} most significant (see
+    or_render_shard)."""
+    idx = np.ascontiguousarray(indices, dtype=np.uint64).ravel()
+    out = np.zeros(idx.size, dtype=np.uint64)
+    if lib().or_prefix_rank(d, p, _ptr(idx), idx.size, _ptr(out)) != 0:
+        raise ValueError("bad depth, prefix length or index")
+    return out
+
+
+def render_shard(gens, seeds8, d: int, window: Sequence[float], width: int, height: int,
+                 p: int, shard: int, n_shards: int, eta: float = 0.0,
+                 edge_cap: int = 1 << 16) -> Render:
+    """Per-word render of shard `shard` of `n_shards` at prefix length p: the
+    words whose prefix slot rank r lies in [floor(k 3^(p-1)/n), floor((k+1)
+    3^(p-1)/n)) (see or_render_shard)."""
+    g = np.ascontiguousarray(gens, dtype=np.float64)
+    s = np.ascontiguousarray(seeds8, dtype=np.float64)
+    win = np.ascontiguousarray(window, dtype=np.float64)
+    img = np.zeros((height, width), dtype=np.uint32)
+    cnt = np.zeros(2, dtype=np.uint64)
+    cap = edge_cap if eta > 0 else 0
+    eidx = np.zeros(max(cap, 1), dtype=np.uint64)
+    euv = np.zeros(2 * max(cap, 1), dtype=np.float64)
+    ecount = np.zeros(1, dtype=np.uint64)
+    rc = lib().or_render_shard(_ptr(g), _ptr(s), d, _ptr(win), width, height, p, shard,
+                               n_shards, _ptr(img), _ptr(cnt), eta, _ptr(eidx), _ptr(euv), cap,
+                               _ptr(ecount))
+    if rc != 0:
+        raise ValueError("bad shard render arguments")
     k = int(min(int(ecount[0]), cap))
     return Render(img, int(cnt[0]), int(cnt[1]), eidx[:k].copy(),
                   euv[:2 * k].reshape(k, 2).copy(), int(ecount[0]))

@@ -47,6 +47,8 @@ class Params(ctypes.Structure):
         ("chunk_pairs", ctypes.c_uint32),
         ("mode", ctypes.c_uint32),
         ("cull", ctypes.c_uint32),
+        ("shard_index", ctypes.c_uint32),
+        ("shard_count", ctypes.c_uint32),
     ]
 
 

@@ -353,6 +353,7 @@ extern "C" int kl_batch_create(const kl_params* params, uint32_t n_groups, kl_ba
     if (!valid_view(&params[g]) || !same_frame(p0, params[g])) return KL_EINVAL;
     if (params[g].precision != KL_FP64 && params[g].precision != KL_MIXED) return KL_EINVAL;
     if (params[g].mode != KL_LIMIT_SET || params[g].cull > 1) return KL_EINVAL;
+    if (params[g].shard_count > 1) return KL_EINVAL;  // a batch is not sharded
     if (!(params[g].parabolic_tol >= 0.0)) return KL_EINVAL;
     if (params[g].depth < 2) return KL_EINVAL;
   }

@@ -54,6 +54,9 @@ struct Plan {
   uint32_t np;   // prefix slots per last letter: 3^(p-1)
   uint32_t ns;   // suffix points per first letter: 3^(s-1)
   uint32_t npairs;  // FP32 point pairs per first letter: ceil(ns / 2)
+  // prefix slots this render draws, per last letter: [r0, r0 + nr) (a shard of
+  // kl_params.shard_count > 1; else all np); tables and work cover only these
+  uint32_t r0, nr;
   uint32_t p3_q1, p3_pq, p3_so1, p3_si, p3_si1;  // 3^(q-1), 3^(p-q), 3^(so-1), 3^si, 3^(si-1)
   // culling blocks (kl_params.cull): level l = 0 .. clev-1 holds aligned blocks
   // of csz[l] = 3^(cj0 + l) suffix points (one subtree each), cnb[l] = ns /
@@ -341,7 +344,7 @@ __host__ __device__ __forceinline__ uint32_t parts_count(const Plan& L) {
          4u * L.p3_si1;
 }
 __host__ __device__ __forceinline__ uint32_t combine_count(const Plan& L) {
-  return 4u * L.np + 4u * L.ns;
+  return 4u * L.nr + 4u * L.ns;
 }
 
 __device__ void part_entry(const Group& G, const Plan& L, int renorm, uint32_t idx,
@@ -417,13 +420,14 @@ __device__ void part_entry(const Group& G, const Plan& L, int renorm, uint32_t i
   }
 }
 
-// Combine pass entry idx (prefix slots first, then suffix slots).  Fallback
-// prefixes (mixed mode) are appended to fb_list as (group << 32) | slot.
+// Combine pass entry idx (the render's prefix slots first, 4 nr of them:
+// last letter x, slot r0 + k; then the suffix slots).  Fallback prefixes
+// (mixed mode) are appended to fb_list as (group << 32) | slot.
 __device__ void combine_entry(const View& V, const Plan& L, double ptol, int mixed,
                               uint32_t idx, const Tables& T, uint32_t group,
                               unsigned long long* __restrict__ fb_list,
                               uint32_t* __restrict__ fb_count) {
-  const uint32_t nP = 4u * L.np;
+  const uint32_t nP = 4u * L.nr;
   if (idx >= nP) {
     const uint32_t slot = idx - nP;
     double2 v;
@@ -452,9 +456,9 @@ __device__ void combine_entry(const View& V, const Plan& L, double ptol, int mix
     }
     return;
   }
-  const uint32_t slot = idx;
-  const int x = (int)(slot / L.np);
-  const uint32_t r = slot % L.np;
+  const int x = (int)(idx / L.nr);
+  const uint32_t r = L.r0 + idx % L.nr;
+  const uint32_t slot = (uint32_t)x * L.np + r;
   const PartM& TL = T.Lt[(uint32_t)x * L.p3_q1 + r / L.p3_pq];
   const M2 P = L.p > L.q ? mmul(T.Ht[(uint32_t)TL.edge * L.p3_pq + r % L.p3_pq], TL.m) : TL.m;
   const dc det = mdet(P);
@@ -697,9 +701,9 @@ __device__ __forceinline__ void fp64_item(uint32_t item, const Work& Wk, const P
   int x, u;
   uint32_t pb, c;
   item_of(item, Wk, x, u, pb, c);
-  const uint32_t r = pb * BT + threadIdx.x;
-  if (r >= L.np) return;
-  const uint32_t slot = (uint32_t)x * L.np + r;
+  const uint32_t k = pb * BT + threadIdx.x;
+  if (k >= L.nr) return;
+  const uint32_t slot = (uint32_t)x * L.np + L.r0 + k;
   const uint32_t j0 = c * Wk.chunk, j1 = min(L.ns, j0 + Wk.chunk);
   words64(T.pre64[slot], T.flags[slot] & kDirect, T.suf64 + (size_t)u * L.ns, j0, j1, V, t,
           img);
@@ -818,9 +822,9 @@ __device__ __forceinline__ void mixed_item(uint32_t item, const Work& Wk, const 
   int x, u;
   uint32_t pb, c;
   item_of(item, Wk, x, u, pb, c);
-  const uint32_t r = pb * BT + (threadIdx.x % BT);
-  if (r >= L.np) return;
-  const uint32_t slot = (uint32_t)x * L.np + r;
+  const uint32_t k = pb * BT + (threadIdx.x % BT);
+  if (k >= L.nr) return;
+  const uint32_t slot = (uint32_t)x * L.np + L.r0 + k;
   if (T.flags[slot] & kFallback) return;
   const uint32_t k0 = c * Wk.chunk, k1 = min(L.npairs, k0 + Wk.chunk);
   mixed_slot_words<BBOX>(slot, u, k0, k1, L, V, T, t, words, img, B);
@@ -1245,9 +1249,9 @@ __device__ __forceinline__ void cull_item(CullWarp<MIXED>& w, uint32_t item, con
   int x, u;
   uint32_t pb, c;
   item_of(item, Wk, x, u, pb, c);
-  const uint32_t r = pb * 32 + w.lane;
-  const uint32_t slot = (uint32_t)x * L.np + r;
-  const bool live = r < L.np;
+  const uint32_t k = pb * 32 + w.lane;
+  const uint32_t slot = (uint32_t)x * L.np + L.r0 + k;
+  const bool live = k < L.nr;
   const bool f64 = !MIXED || (live && (T.flags[slot] & kFallback));
   const uint32_t b0 = c * Wk.chunk, b1 = min(top_blocks, b0 + Wk.chunk);
   w.item(L, V, T, img, live, slot, (uint32_t)u, f64, b0, b1);
@@ -1353,6 +1357,16 @@ inline int make_plan(const kl_params* p, Plan* L, bool batched) {
   L->np = pow3u(pl - 1);
   L->ns = sl > 0 ? pow3u(sl - 1) : 0;
   L->npairs = (L->ns + 1) / 2;
+  // shard k of n: prefix slots [floor(k np / n), floor((k+1) np / n)) per letter
+  if (p->shard_count > 1) {
+    if (batched || p->shard_index >= p->shard_count) return KL_EINVAL;
+    const uint64_t n = p->shard_count, k = p->shard_index;
+    L->r0 = (uint32_t)(k * L->np / n);
+    L->nr = (uint32_t)((k + 1) * L->np / n) - L->r0;
+  } else {
+    L->r0 = 0;
+    L->nr = L->np;
+  }
   L->q = (pl + 1) / 2;
   L->so = sl / 2;
   L->si = sl - L->so;
@@ -1460,7 +1474,13 @@ inline int device_slots(const void* kernel, int bt, int* sms, int* occ) {
 // point pairs).
 inline Work make_work(const Plan& L, int bt, uint32_t units, int slots, uint32_t chunk_units) {
   Work W;
-  W.n_pb = (L.np + bt - 1) / bt;
+  W.n_pb = (L.nr + bt - 1) / bt;
+  if (W.n_pb == 0) {  // an empty shard
+    W.n_chunks = 1;
+    W.chunk = units > 0 ? units : 1;
+    W.n_items = 0;
+    return W;
+  }
   const uint64_t base = 12ull * W.n_pb;
   if (chunk_units == 0) {
     const uint64_t target = 12ull * (uint64_t)slots;

@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(BT, 1024 / BT) lod_cull_kernel(
 int lod_plan(const kl_params* p, uint32_t lo, uint32_t hi, LodPlan* P, Plan* L) {
   if (!p || !valid_view(p)) return KL_EINVAL;
   if (p->precision != KL_FP64 && p->precision != KL_MIXED) return KL_EINVAL;
-  if (p->mode != KL_LIMIT_SET || p->cull != 0) return KL_EINVAL;
+  if (p->mode != KL_LIMIT_SET || p->cull != 0 || p->shard_count > 1) return KL_EINVAL;
   const int D = (int)p->depth;
   if (lo < 1 || lo > hi || (int)hi >= D || hi > (uint32_t)kMaxPrefix ||
       D - (int)hi > kMaxPlainSuffix)

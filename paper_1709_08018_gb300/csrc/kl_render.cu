@@ -336,6 +336,8 @@ int validate(const kl_params* p, size_t ws_bytes, void* ws, Plan* L) {
   if (p->precision != KL_FP64 && p->precision != KL_MIXED) return KL_EINVAL;
   if (p->mode != KL_LIMIT_SET && p->mode != KL_TILING) return KL_EINVAL;
   if (p->cull > 1) return KL_EINVAL;
+  if (p->shard_count > 1 && (p->mode != KL_LIMIT_SET || p->shard_index >= p->shard_count))
+    return KL_EINVAL;
   if (!(p->parabolic_tol >= 0.0)) return KL_EINVAL;
   const int st = make_plan(p, L, false);
   if (st != KL_OK) return st;
@@ -414,9 +416,15 @@ extern "C" int kl_decode_words(uint32_t depth, const uint64_t* d_index, uint64_t
   return check_launch();
 }
 
-extern "C" int kl_eval_words(const kl_params* p, const uint64_t* d_index, uint64_t n,
+extern "C" int kl_eval_words(const kl_params* p_in, const uint64_t* d_index, uint64_t n,
                              double* d_uv, void* d_workspace, size_t workspace_bytes,
                              void* stream) {
+  if (!p_in) return KL_EINVAL;
+  // every word can be asked for: the tables cover all prefix slots
+  kl_params q = *p_in;
+  q.shard_index = 0;
+  q.shard_count = 0;
+  const kl_params* p = &q;
   Plan L;
   int st = validate(p, workspace_bytes, d_workspace, &L);
   if (st != KL_OK) return st;
@@ -458,6 +466,7 @@ int render_length(const kl_params* p, uint32_t* d_image, unsigned long long* cnt
       if (cnt && cudaMemsetAsync(cnt, 0, KL_N_COUNTERS * sizeof(uint64_t), s) != cudaSuccess)
         return KL_ECUDA;
     }
+    if (L.nr == 0) return KL_OK;  // a shard without the one prefix slot
     render_single_letter_kernel<<<1, 32, 0, s>>>(G, V, d_image, cnt);
     return check_launch();
   }
@@ -520,8 +529,12 @@ extern "C" int kl_set_profile_events(void* ev_start, void* ev_stop) {
 // ---------------------------------------------------------------------------
 // kl_render without allocation: the workspace is a static device array of this
 // file.  In host code the symbol g_noalloc_scratch is only a host-side stand-in,
-// so its device address is looked up once per device (with that device
-// current) and cached.
+// so its device address is looked up with the calling device current.  The
+// lookup (cudaGetSymbolAddress, which allocates nothing) runs on every call
+// whose stream is not capturing, so the address always belongs to the context
+// current now (a device reset or a different context on the same device gets
+// its own address).  A call on a capturing stream cannot look it up and takes
+// the address the last uncaptured call on that device found.
 
 namespace {
 
@@ -531,15 +544,19 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 void* g_noalloc_ptr[kMaxDevices] = {};
 
-int noalloc_scratch(void** out) {
+int noalloc_scratch(cudaStream_t stream, void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return KL_ECUDA;
   if (dev < 0 || dev >= kMaxDevices) return KL_ERANGE;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) return KL_ECUDA;
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return KL_ECUDA;
     g_noalloc_ptr[dev] = ptr;
+  } else if (!g_noalloc_ptr[dev]) {
+    return KL_EINVAL;  // no uncaptured call has run on this device yet
   }
   *out = g_noalloc_ptr[dev];
   return KL_OK;
@@ -552,7 +569,7 @@ extern "C" int kl_render_noalloc(const kl_params* p, uint32_t* d_image, uint64_t
   if (!p) return KL_EINVAL;
   if (kl_workspace_bytes(p) > KL_STATIC_SCRATCH_BYTES) return KL_ENOSPACE;
   void* scratch = nullptr;
-  const int st = noalloc_scratch(&scratch);
+  const int st = noalloc_scratch((cudaStream_t)stream, &scratch);
   if (st != KL_OK) return st;
   return kl_render(p, d_image, d_counters, scratch, KL_STATIC_SCRATCH_BYTES, stream);
 }

@@ -1,6 +1,7 @@
-"""bench.py's multi-rank logic on CPU: world_size 2 over gloo.  Every rank
-renders the whole job (replicas); the job's time is the slowest rank's, and
-value counts the words of all ranks.  The reference arm runs on rank 0 only."""
+"""bench.py's multi-rank logic on CPU: world_size 2 over gloo.  The ranks
+share one job (each renders a shard of its words); the job's time is the
+slowest rank's, and value counts the job's words once.  The reference arm
+runs on rank 0 only."""
 import os
 import socket
 
@@ -26,7 +27,7 @@ def _rank_main(rank, world, port, out):
         barrier = bench.make_barrier(world)
         barrier()
         local_ms = [40.0, 55.0][rank]           # rank 1 is the slow one
-        value, job_ms = bench.job_rate(world, 1000, 10, local_ms,
+        value, job_ms = bench.job_rate(1000, 10, local_ms,
                                        bench.make_max_over_ranks(world, "cpu"))
         out[rank] = (value, job_ms)
         barrier()
@@ -43,11 +44,11 @@ def test_two_gloo_ranks_agree_on_the_job_rate():
     assert res[0] == res[1]
     value, job_ms = res[0]
     assert job_ms == 55.0
-    assert value == pytest.approx(world * 1000 * 10 / 0.055)
+    assert value == pytest.approx(1000 * 10 / 0.055)
 
 
 def test_single_rank_rate_needs_no_process_group():
-    value, job_ms = bench.job_rate(1, 516560652, 50, 20.0, bench.make_max_over_ranks(1, "cpu"))
+    value, job_ms = bench.job_rate(516560652, 50, 20.0, bench.make_max_over_ranks(1, "cpu"))
     assert job_ms == 20.0 and value == pytest.approx(516560652 * 50 / 0.020)
 
 
