@@ -1,244 +1,435 @@
 // The level-of-detail network: an MLP 8 -> 64 -> 64 -> 1 with ReLU, BF16
-// weights and activations on the tensor cores with FP32 accumulation, and
-// its training kernels (forward, backward, weight gradients, Adam).
+// weights and activations on the fifth-generation tensor cores (tcgen05,
+// FP32 accumulators in tensor memory), and its training kernels (forward and
+// backward with the weight gradients in one kernel, a fixed-order reduction,
+// Adam).
 //
 // Parameter vector (FP32 master copy, KL_MLP_NPARAMS floats):
 //   W1 [8][64] | b1 [64] | W2 [64][64] | b2 [64] | w3 [64] | b3
 // (W[in][out]: h_out = sum_in x_in W[in][out] + b_out).  Loss: mean squared
 // error over the batch.
 //
-// Tensor-core tiles use mma.sync.m16n8k16 (BF16 in, FP32 accumulate).  A warp
-// owns 16 rows; the FP32 accumulator fragment of one layer (rows g, g+8 and
-// columns 2c, 2c+1 of each 8-column tile, g = lane/4, c = lane%4) is exactly
-// the BF16 A-operand fragment of the next layer's 16-column k-step, so
-// activations never leave registers between layers.
+// A CTA of 128 threads takes tiles of 128 rows; thread t owns row t of the
+// tile, which is lane t of every accumulator in tensor memory (M = 128), so
+// bias, ReLU, the last layer's dot product and the error are row-local.  The
+// layer products run as tcgen05 MMAs on BF16 tiles in shared memory:
+//   H1 = X W1 (K = 16: 8 inputs and zero padding), H2 = H1 W2, dH1 = dH2 W2^T.
+// The gradients are sums over rows, i.e. products with the rows as the K
+// dimension, accumulated in tensor memory over all the CTA's tiles:
+//   [H1^T; H2^T] [dH2 | dy]   -> dW2 (rows 0..63, columns 0..63) and
+//                                dw3 (rows 64..127, column 64),
+//   [dH1^T; dH2^T] [X | 1]    -> dW1^T (rows 0..63, columns 0..7), db1 (rows
+//                                0..63, column 8) and db2 (rows 64..127,
+//                                column 8).
+// The transposed operands are written column-wise by the row-owning threads.
 #include "kl_mlp_dev.cuh"
+#include "kl_tc.cuh"
 
 namespace {
 
-__global__ void __launch_bounds__(128) mlp_forward_kernel(const float* __restrict__ P,
-                                                          const float* __restrict__ x,
-                                                          uint64_t n, float* __restrict__ y) {
-  __shared__ MlpSmem S;
-  load_mlp(S, P);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
-  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t tile = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-       tile * 16 < n; tile += warps) {
-    const uint64_t r0 = tile * 16;
-    uint32_t xa0, xa1;
-    x_fragment(x, n, r0, xa0, xa1);
-    Tile T;
-    forward_tile(S, xa0, xa1, T);
-    if (c == 0) {
-      if (r0 + g < n) y[r0 + g] = T.y0;
-      if (r0 + g + 8 < n) y[r0 + g + 8] = T.y1;
-    }
+constexpr int kTile = 128;                        // rows per tile = TMEM lanes = threads
+constexpr long long kWaitCycles = 2000000000ll;   // bound on an MMA wait (about a second)
+
+// Shared memory (bytes from a 1024-aligned base).  K-major BF16 tiles
+// (kl_tc.cuh); LBO = 16 x rows for tiles written row by row, plus 16 bytes
+// for tiles written column-wise (thread = K index), so that the four K
+// chunks a warp's 32 threads write fall in different banks.
+constexpr uint32_t kLboW = 64 * 16;           // weight tiles, 64 rows
+constexpr uint32_t kLboRow = kTile * 16;      // X, H1, dH2: 128 rows, row-wise
+constexpr uint32_t kLboA = kTile * 16 + 16;   // [H1^T; H2^T], [dH1^T; dH2^T]: 128 rows
+constexpr uint32_t kLboB1 = 80 * 16 + 16;     // [dH2 | dy | 0]^T: 80 rows
+constexpr uint32_t kLboB2 = 16 * 16 + 16;     // [X | 1 | 0]^T: 16 rows
+
+// training kernel
+constexpr uint32_t SM_W1 = 0;                      // B of layer 1: [h][f], f < 16
+constexpr uint32_t SM_W2 = SM_W1 + 2 * kLboW;      // B of layer 2: [out][in] (W2^T)
+constexpr uint32_t SM_W2T = SM_W2 + 8 * kLboW;     // B of dH1:     [in][out] (W2)
+constexpr uint32_t SM_X = SM_W2T + 8 * kLboW;      // A of layer 1: [row][f]
+constexpr uint32_t SM_H1 = SM_X + 2 * kLboRow;     // A of layer 2: [row][in]
+constexpr uint32_t SM_DH2 = SM_H1 + 8 * kLboRow;   // A of dH1:     [row][out]
+constexpr uint32_t SM_A1 = SM_DH2 + 8 * kLboRow;   // [H1^T; H2^T]:  [m][row]
+constexpr uint32_t SM_A2 = SM_A1 + 16 * kLboA;     // [dH1^T; dH2^T]: [m][row]
+constexpr uint32_t SM_B1 = SM_A2 + 16 * kLboA;     // [n][row], n < 80
+constexpr uint32_t SM_B2 = SM_B1 + 16 * kLboB1;    // [n][row], n < 16
+constexpr uint32_t SM_PAR = SM_B2 + 16 * kLboB2;   // b1, b2, w3 (FP32)
+constexpr uint32_t SM_RED = SM_PAR + 3 * kHid * 4; // per-warp loss and db3
+constexpr uint32_t SM_BAR = SM_RED + 32;           // mbarrier, TMEM address
+constexpr uint32_t kGradSmem = SM_BAR + 16;
+
+// forward kernel
+constexpr uint32_t FW_W1 = 0;
+constexpr uint32_t FW_W2 = FW_W1 + 2 * kLboW;
+constexpr uint32_t FW_X = FW_W2 + 8 * kLboW;
+constexpr uint32_t FW_H1 = FW_X + 2 * kLboRow;
+constexpr uint32_t FW_PAR = FW_H1 + 8 * kLboRow;   // b1, b2, w3
+constexpr uint32_t FW_BAR = FW_PAR + 3 * kHid * 4;
+// 64 KB per CTA keeps at most 3 CTAs (3 x 128 TMEM columns) on an SM, so a
+// TMEM allocation never waits for another CTA
+constexpr uint32_t kFwdSmem = 64 * 1024;
+static_assert(FW_BAR + 16 <= kFwdSmem, "forward shared memory");
+static_assert(kGradSmem <= 227 * 1024, "training shared memory");
+
+// TMEM columns: layer outputs and dH1 (64 each), the two gradient accumulators.
+constexpr uint32_t TD1 = 0, TD2 = 64, TWA = 128, TWB = 224;
+
+__device__ __forceinline__ void st_bf16(unsigned char* p, float v) {
+  *reinterpret_cast<__nv_bfloat16*>(p) = __float2bfloat16_rn(v);
+}
+
+// Weights as BF16 B operands, biases and w3 in FP32.
+__device__ void stage_weights(unsigned char* sm, uint32_t w1, uint32_t w2, int w2t,
+                              uint32_t par, const float* __restrict__ P) {
+  for (int i = threadIdx.x; i < kHid * 16; i += blockDim.x) {
+    const int h = i / 16, f = i % 16;
+    st_bf16(sm + w1 + tc_off(h, f, kLboW), f < kIn ? P[OFF_W1 + f * kHid + h] : 0.0f);
   }
+  for (int i = threadIdx.x; i < kHid * kHid; i += blockDim.x) {
+    const int in = i / kHid, out = i % kHid;
+    const float w = P[OFF_W2 + i];
+    st_bf16(sm + w2 + tc_off(out, in, kLboW), w);
+    if (w2t >= 0) st_bf16(sm + (uint32_t)w2t + tc_off(in, out, kLboW), w);
+  }
+  float* q = reinterpret_cast<float*>(sm + par);
+  for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
+    q[i] = P[OFF_B1 + i];
+    q[kHid + i] = P[OFF_B2 + i];
+    q[2 * kHid + i] = P[OFF_W3 + i];
+  }
+}
+
+// Hand the tiles just written to the tensor cores and order the TMEM reads
+// before the next MMA: every thread fences, then the block synchronises.
+__device__ __forceinline__ void sync_for_mma() {
+  fence_smem_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+}
+
+// Row t of a row-wise tile: 16 values (columns c .. c+15) as two 16-byte chunks.
+__device__ __forceinline__ void st_row16(unsigned char* base, int t, int c, const float* v) {
+  uint4 a, b;
+  a.x = pack_bf16(v[0], v[1]); a.y = pack_bf16(v[2], v[3]);
+  a.z = pack_bf16(v[4], v[5]); a.w = pack_bf16(v[6], v[7]);
+  b.x = pack_bf16(v[8], v[9]); b.y = pack_bf16(v[10], v[11]);
+  b.z = pack_bf16(v[12], v[13]); b.w = pack_bf16(v[14], v[15]);
+  *reinterpret_cast<uint4*>(base + tc_off(t, c, kLboRow)) = a;
+  *reinterpret_cast<uint4*>(base + tc_off(t, c + 8, kLboRow)) = b;
+}
+
+// Wait for the MMAs committed last (block-uniform result); on a timeout the
+// caller stops issuing work.
+__device__ __forceinline__ bool mma_done(uint64_t* bar, uint32_t& phase) {
+  const bool ok = mbar_wait(bar, phase, kWaitCycles);
+  phase ^= 1u;
+  return __syncthreads_and(ok) != 0;
+}
+
+__global__ void __launch_bounds__(kTile, 1) mlp_forward_kernel(const float* __restrict__ P,
+                                                               const float* __restrict__ x,
+                                                               uint64_t n,
+                                                               float* __restrict__ y) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int t = threadIdx.x, warp = t >> 5;
+  const float* b1 = reinterpret_cast<const float*>(sm + FW_PAR);
+  const float* b2 = b1 + kHid;
+  const float* w3 = b2 + kHid;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + FW_BAR);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(sm + FW_BAR + 8);
+  stage_weights(sm, FW_W1, FW_W2, -1, FW_PAR, P);
+  const float b3 = P[OFF_B3];
+  *reinterpret_cast<uint4*>(sm + FW_X + tc_off(t, 8, kLboRow)) = make_uint4(0u, 0u, 0u, 0u);
+  if (t == 0) mbar_init(bar, 1);
+  if (warp == 0) tc_alloc(slot, 128);
+  sync_for_mma();
+  const uint32_t tm = *slot;
+  const uint32_t la = tm + ((uint32_t)(warp * 32) << 16);
+  const uint32_t id64 = tc_idesc_bf16(128, 64);
+  const uint32_t aX = smem_u32(sm + FW_X), aH1 = smem_u32(sm + FW_H1);
+  const uint32_t aW1 = smem_u32(sm + FW_W1), aW2 = smem_u32(sm + FW_W2);
+  uint32_t phase = 0;
+  bool ok = true;
+  const uint64_t tiles = (n + kTile - 1) / kTile;
+  for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const uint64_t row = tile * kTile + t;
+    if (!ok) {   // an MMA did not finish: mark this CTA's outputs
+      if (row < n) y[row] = __int_as_float(0x7FC00000);
+      continue;
+    }
+    float xv[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    if (row < n) {
+      const float4 u = *reinterpret_cast<const float4*>(x + row * kIn);
+      const float4 w = *reinterpret_cast<const float4*>(x + row * kIn + 4);
+      xv[0] = u.x; xv[1] = u.y; xv[2] = u.z; xv[3] = u.w;
+      xv[4] = w.x; xv[5] = w.y; xv[6] = w.z; xv[7] = w.w;
+    }
+    *reinterpret_cast<uint4*>(sm + FW_X + tc_off(t, 0, kLboRow)) =
+        make_uint4(pack_bf16(xv[0], xv[1]), pack_bf16(xv[2], xv[3]), pack_bf16(xv[4], xv[5]),
+                   pack_bf16(xv[6], xv[7]));
+    sync_for_mma();
+    if (t == 0) {
+      tc_mma(tm + TD1, tc_desc(aX, kLboRow), tc_desc(aW1, kLboW), id64, 0u);
+      tc_commit(bar);
+    }
+    ok = mma_done(bar, phase);
+    if (!ok) {
+      if (row < n) y[row] = __int_as_float(0x7FC00000);
+      continue;
+    }
+    tc_fence_after();
+#pragma unroll
+    for (int c = 0; c < kHid; c += 16) {
+      float v[16];
+      tc_ld16(la + TD1 + c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j] + b1[c + j], 0.0f);
+      st_row16(sm + FW_H1, t, c, v);
+    }
+    sync_for_mma();
+    if (t == 0) {
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks)
+        tc_mma(tm + TD2, tc_desc(aH1 + 2 * ks * kLboRow, kLboRow),
+               tc_desc(aW2 + 2 * ks * kLboW, kLboW), id64, ks > 0 ? 1u : 0u);
+      tc_commit(bar);
+    }
+    ok = mma_done(bar, phase);
+    if (!ok) {
+      if (row < n) y[row] = __int_as_float(0x7FC00000);
+      continue;
+    }
+    tc_fence_after();
+    float acc = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kHid; c += 16) {
+      float v[16];
+      tc_ld16(la + TD2 + c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc += fmaxf(v[j] + b2[c + j], 0.0f) * w3[c + j];
+    }
+    if (row < n) y[row] = acc + b3;
+    tc_fence_before();
+  }
+  if (!ok) mbar_wait(bar, phase ^ 1u, kWaitCycles);   // let a late MMA finish first
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tc_dealloc(tm, 128);
 }
 
 // Gradients are summed in a fixed order, so that a training run repeats
-// bit for bit: every block of mlp_backward_kernel and of mlp_wgrad_kernel
-// writes its partial sums to scratch, and mlp_reduce_kernel adds them up in a
-// fixed order.  Per-block partial of the backward pass:
-// db1 [64] | db2 [64] | dw3 [64] | db3 | loss.
+// bit for bit: every block of mlp_grad_kernel writes its partial sums to
+// scratch (its tiles are fixed by its index), and mlp_reduce_kernel adds
+// them up in a fixed order.  Per-block partials:
+//   backward: db1 [64] | db2 [64] | dw3 [64] | db3 | loss;
+//   weights:  dW2 [64][64] | dW1 [8][64].
 constexpr int kBwdPart = 3 * kHid + 2;
-constexpr int kWgPart = kHid * kHid + kIn * kHid;  // dW2 [64][64] | dW1 [8][64]
+constexpr int kWgPart = kHid * kHid + kIn * kHid;
 constexpr int kBwdMaxBlocks = 512, kWgMaxBlocks = 256;
 
-// Forward + backward of 16-row tiles.  Per-parameter gradients of the
-// biases and w3, and the loss, are accumulated in registers over all tiles
-// of the warp and reduced once; the activations the weight gradients need
-// (H1, dH2 and dH1, BF16) go to scratch for mlp_wgrad_kernel.
-__global__ void __launch_bounds__(128) mlp_backward_kernel(
+__global__ void __launch_bounds__(kTile, 1) mlp_grad_kernel(
     const float* __restrict__ P, const float* __restrict__ x, const float* __restrict__ tgt,
-    uint64_t n, float under, float* __restrict__ part,
-    __nv_bfloat16* __restrict__ h1s, __nv_bfloat16* __restrict__ dh2s,
-    __nv_bfloat16* __restrict__ dh1s) {
-  __shared__ MlpSmem S;
-  load_mlp(S, P);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+    uint64_t n, float under, float* __restrict__ bwd_part, float* __restrict__ wg_part) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const float* b1 = reinterpret_cast<const float*>(sm + SM_PAR);
+  const float* b2 = b1 + kHid;
+  const float* w3 = b2 + kHid;
+  float* red = reinterpret_cast<float*>(sm + SM_RED);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + SM_BAR);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(sm + SM_BAR + 8);
+  stage_weights(sm, SM_W1, SM_W2, (int)SM_W2T, SM_PAR, P);
+  const float b3 = P[OFF_B3];
+  // constant parts of the operand tiles: X padding, the zero rows of B1 and B2
+  *reinterpret_cast<uint4*>(sm + SM_X + tc_off(t, 8, kLboRow)) = make_uint4(0u, 0u, 0u, 0u);
+  for (int r = kHid + 1; r < 80; ++r) st_bf16(sm + SM_B1 + tc_off(r, t, kLboB1), 0.0f);
+  for (int r = kIn + 1; r < 16; ++r) st_bf16(sm + SM_B2 + tc_off(r, t, kLboB2), 0.0f);
+  if (t == 0) mbar_init(bar, 1);
+  if (warp == 0) tc_alloc(slot, 256);
+  sync_for_mma();
+  const uint32_t tm = *slot;
+  const uint32_t la = tm + ((uint32_t)(warp * 32) << 16);
+  const uint32_t id64 = tc_idesc_bf16(128, 64), id80 = tc_idesc_bf16(128, 80),
+                 id16 = tc_idesc_bf16(128, 16);
+  const uint32_t aX = smem_u32(sm + SM_X), aH1 = smem_u32(sm + SM_H1),
+                 aDH2 = smem_u32(sm + SM_DH2), aA1 = smem_u32(sm + SM_A1),
+                 aA2 = smem_u32(sm + SM_A2), aB1 = smem_u32(sm + SM_B1),
+                 aB2 = smem_u32(sm + SM_B2), aW1 = smem_u32(sm + SM_W1),
+                 aW2 = smem_u32(sm + SM_W2), aW2T = smem_u32(sm + SM_W2T);
   const float inv_n = 1.0f / (float)n;
-  float gb1[16], gb2[16], gw3[16];
+  float lsum = 0.0f, gb3 = 0.0f;
+  uint32_t phase = 0;
+  bool ok = true, first = true;
+  const uint64_t tiles = (n + kTile - 1) / kTile;
+  for (uint64_t tile = blockIdx.x; ok && tile < tiles; tile += gridDim.x) {
+    const uint64_t row = tile * kTile + t;
+    const bool valid = row < n;
+    float xv[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    float tg = 0.0f;
+    if (valid) {
+      const float4 u = *reinterpret_cast<const float4*>(x + row * kIn);
+      const float4 w = *reinterpret_cast<const float4*>(x + row * kIn + 4);
+      xv[0] = u.x; xv[1] = u.y; xv[2] = u.z; xv[3] = u.w;
+      xv[4] = w.x; xv[5] = w.y; xv[6] = w.z; xv[7] = w.w;
+      tg = tgt[row];
+    }
+    *reinterpret_cast<uint4*>(sm + SM_X + tc_off(t, 0, kLboRow)) =
+        make_uint4(pack_bf16(xv[0], xv[1]), pack_bf16(xv[2], xv[3]), pack_bf16(xv[4], xv[5]),
+                   pack_bf16(xv[6], xv[7]));
 #pragma unroll
-  for (int i = 0; i < 16; ++i) gb1[i] = gb2[i] = gw3[i] = 0.0f;
-  float gb3 = 0.0f, lsum = 0.0f;
-  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t tile = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-       tile * 16 < n; tile += warps) {
-    const uint64_t r0 = tile * 16, ra = r0 + g, rb = r0 + g + 8;
-    uint32_t xa0, xa1;
-    x_fragment(x, n, r0, xa0, xa1);
-    Tile T;
-    forward_tile(S, xa0, xa1, T);
-    const bool va = ra < n, vb = rb < n;
-    const float ea = va ? T.y0 - tgt[ra] : 0.0f, eb = vb ? T.y1 - tgt[rb] : 0.0f;
+    for (int f = 0; f < kIn; ++f) st_bf16(sm + SM_B2 + tc_off(f, t, kLboB2), xv[f]);
+    st_bf16(sm + SM_B2 + tc_off(kIn, t, kLboB2), valid ? 1.0f : 0.0f);
+    // layer 1: H1 = relu(X W1 + b1)
+    sync_for_mma();
+    if (t == 0) {
+      tc_mma(tm + TD1, tc_desc(aX, kLboRow), tc_desc(aW1, kLboW), id64, 0u);
+      tc_commit(bar);
+    }
+    if (!(ok = mma_done(bar, phase))) break;
+    tc_fence_after();
+    uint64_t m1 = 0;
+#pragma unroll
+    for (int c = 0; c < kHid; c += 16) {
+      float v[16];
+      tc_ld16(la + TD1 + c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float a = v[j] + b1[c + j];
+        m1 |= (uint64_t)(a > 0.0f) << (c + j);
+        v[j] = fmaxf(a, 0.0f);
+        st_bf16(sm + SM_A1 + tc_off(c + j, t, kLboA), v[j]);
+      }
+      st_row16(sm + SM_H1, t, c, v);
+    }
+    // layer 2: H2 = relu(H1 W2 + b2), y = H2 . w3 + b3
+    sync_for_mma();
+    if (t == 0) {
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks)
+        tc_mma(tm + TD2, tc_desc(aH1 + 2 * ks * kLboRow, kLboRow),
+               tc_desc(aW2 + 2 * ks * kLboW, kLboW), id64, ks > 0 ? 1u : 0u);
+      tc_commit(bar);
+    }
+    if (!(ok = mma_done(bar, phase))) break;
+    tc_fence_after();
+    uint64_t m2 = 0;
+    float yv = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kHid; c += 16) {
+      float v[16];
+      tc_ld16(la + TD2 + c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float a = v[j] + b2[c + j];
+        m2 |= (uint64_t)(a > 0.0f) << (c + j);
+        const float h = fmaxf(a, 0.0f);
+        yv += h * w3[c + j];
+        st_bf16(sm + SM_A1 + tc_off(kHid + c + j, t, kLboA), h);
+      }
+    }
+    yv += b3;
     // weighted squared error: weight `under` where the output is below the target
-    const float wa = ea < 0.0f ? under : 1.0f, wb = eb < 0.0f ? under : 1.0f;
-    if (c == 0) lsum += wa * ea * ea + wb * eb * eb;
-    const float dya = 2.0f * wa * ea * inv_n, dyb = 2.0f * wb * eb * inv_n;
-    if (c == 0) gb3 += dya + dyb;
-    // dH2 = dy w3 (ReLU mask), dw3 += H2^T dy, db2 += dH2
-    float dh2[8][4];
+    const float e = yv - tg;
+    const float wgt = e < 0.0f ? under : 1.0f;
+    const float dy = valid ? 2.0f * wgt * e * inv_n : 0.0f;
+    if (valid) lsum += wgt * e * e;
+    gb3 += dy;
+    // dH2 = dy w3 through the second ReLU
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      const int j = 8 * t + 2 * c;
-      gw3[2 * t] += T.h2[t][0] * dya + T.h2[t][2] * dyb;
-      gw3[2 * t + 1] += T.h2[t][1] * dya + T.h2[t][3] * dyb;
-      dh2[t][0] = T.h2[t][0] > 0.0f ? dya * S.w3[j] : 0.0f;
-      dh2[t][1] = T.h2[t][1] > 0.0f ? dya * S.w3[j + 1] : 0.0f;
-      dh2[t][2] = T.h2[t][2] > 0.0f ? dyb * S.w3[j] : 0.0f;
-      dh2[t][3] = T.h2[t][3] > 0.0f ? dyb * S.w3[j + 1] : 0.0f;
-      gb2[2 * t] += dh2[t][0] + dh2[t][2];
-      gb2[2 * t + 1] += dh2[t][1] + dh2[t][3];
-    }
-    // dH1 = dH2 W2^T (tensor cores; dH2 fragments reused as A operands), ReLU mask
-    uint32_t a[4][4];
+    for (int c = 0; c < kHid; c += 16) {
+      float v[16];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      a[s][0] = pack_bf16(dh2[2 * s][0], dh2[2 * s][1]);
-      a[s][1] = pack_bf16(dh2[2 * s][2], dh2[2 * s][3]);
-      a[s][2] = pack_bf16(dh2[2 * s + 1][0], dh2[2 * s + 1][1]);
-      a[s][3] = pack_bf16(dh2[2 * s + 1][2], dh2[2 * s + 1][3]);
-    }
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&S.w2[8 * t + g][16 * s + 2 * c]);
-        const uint32_t b1 =
-            *reinterpret_cast<const uint32_t*>(&S.w2[8 * t + g][16 * s + 8 + 2 * c]);
-        mma_bf16(d, a[s][0], a[s][1], a[s][2], a[s][3], b0, b1);
+      for (int j = 0; j < 16; ++j) {
+        v[j] = ((m2 >> (c + j)) & 1ull) ? dy * w3[c + j] : 0.0f;
+        st_bf16(sm + SM_B1 + tc_off(c + j, t, kLboB1), v[j]);
+        st_bf16(sm + SM_A2 + tc_off(kHid + c + j, t, kLboA), v[j]);
       }
-      d[0] = T.h1[t][0] > 0.0f ? d[0] : 0.0f;
-      d[1] = T.h1[t][1] > 0.0f ? d[1] : 0.0f;
-      d[2] = T.h1[t][2] > 0.0f ? d[2] : 0.0f;
-      d[3] = T.h1[t][3] > 0.0f ? d[3] : 0.0f;
-      gb1[2 * t] += d[0] + d[2];
-      gb1[2 * t + 1] += d[1] + d[3];
-      const int j = 8 * t + 2 * c;
-      if (va) {
-        *reinterpret_cast<uint32_t*>(h1s + ra * kHid + j) = pack_bf16(T.h1[t][0], T.h1[t][1]);
-        *reinterpret_cast<uint32_t*>(dh2s + ra * kHid + j) = pack_bf16(dh2[t][0], dh2[t][1]);
-        *reinterpret_cast<uint32_t*>(dh1s + ra * kHid + j) = pack_bf16(d[0], d[1]);
-      }
-      if (vb) {
-        *reinterpret_cast<uint32_t*>(h1s + rb * kHid + j) = pack_bf16(T.h1[t][2], T.h1[t][3]);
-        *reinterpret_cast<uint32_t*>(dh2s + rb * kHid + j) = pack_bf16(dh2[t][2], dh2[t][3]);
-        *reinterpret_cast<uint32_t*>(dh1s + rb * kHid + j) = pack_bf16(d[2], d[3]);
-      }
+      st_row16(sm + SM_DH2, t, c, v);
     }
+    st_bf16(sm + SM_B1 + tc_off(kHid, t, kLboB1), dy);
+    // dH1 = dH2 W2^T through the first ReLU
+    sync_for_mma();
+    if (t == 0) {
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks)
+        tc_mma(tm + TD1, tc_desc(aDH2 + 2 * ks * kLboRow, kLboRow),
+               tc_desc(aW2T + 2 * ks * kLboW, kLboW), id64, ks > 0 ? 1u : 0u);
+      tc_commit(bar);
+    }
+    if (!(ok = mma_done(bar, phase))) break;
+    tc_fence_after();
+#pragma unroll
+    for (int c = 0; c < kHid; c += 16) {
+      float v[16];
+      tc_ld16(la + TD1 + c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        st_bf16(sm + SM_A2 + tc_off(c + j, t, kLboA), ((m1 >> (c + j)) & 1ull) ? v[j] : 0.0f);
+    }
+    // the sums over this tile's rows, added to the CTA's accumulators
+    sync_for_mma();
+    if (t == 0) {
+#pragma unroll
+      for (int ks = 0; ks < kTile / 16; ++ks)
+        tc_mma(tm + TWA, tc_desc(aA1 + 2 * ks * kLboA, kLboA),
+               tc_desc(aB1 + 2 * ks * kLboB1, kLboB1), id80, (!first || ks > 0) ? 1u : 0u);
+#pragma unroll
+      for (int ks = 0; ks < kTile / 16; ++ks)
+        tc_mma(tm + TWB, tc_desc(aA2 + 2 * ks * kLboA, kLboA),
+               tc_desc(aB2 + 2 * ks * kLboB2, kLboB2), id16, (!first || ks > 0) ? 1u : 0u);
+      tc_commit(bar);
+    }
+    if (!(ok = mma_done(bar, phase))) break;
+    first = false;
   }
-  // reduce over the 8 row groups (lanes with the same c), then one atomic per value
+  // this block's partials
+  float* bp = bwd_part + (size_t)blockIdx.x * kBwdPart;
+  float* wp = wg_part + (size_t)blockIdx.x * kWgPart;
+  if (!ok) mbar_wait(bar, phase ^ 1u, kWaitCycles);   // let a late MMA finish first
+  tc_fence_after();
+  if (ok && !first) {
+    // lanes 0..63: dW2 rows, dW1^T rows and db1; lanes 64..127: dw3 and db2
+    const int m = t;
+    float v[16];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
+    for (int c = 0; c < kHid; c += 16) {
+      tc_ld16(la + TWA + c, v);
+      if (m < kHid)
 #pragma unroll
-    for (int o = 4; o < 32; o <<= 1) {
-      gb1[i] += __shfl_xor_sync(0xFFFFFFFFu, gb1[i], o);
-      gb2[i] += __shfl_xor_sync(0xFFFFFFFFu, gb2[i], o);
-      gw3[i] += __shfl_xor_sync(0xFFFFFFFFu, gw3[i], o);
+        for (int j = 0; j < 16; ++j) wp[m * kHid + c + j] = v[j];
     }
+    tc_ld16(la + TWA + kHid, v);
+    if (m >= kHid) bp[2 * kHid + (m - kHid)] = v[0];
+    tc_ld16(la + TWB, v);
+    if (m < kHid) {
+#pragma unroll
+      for (int f = 0; f < kIn; ++f) wp[kHid * kHid + f * kHid + m] = v[f];
+      bp[m] = v[kIn];
+    } else {
+      bp[kHid + (m - kHid)] = v[kIn];
+    }
+  } else {
+    for (int i = t; i < kWgPart; i += blockDim.x) wp[i] = 0.0f;
+    for (int i = t; i < 3 * kHid; i += blockDim.x) bp[i] = 0.0f;
   }
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    gb3 += __shfl_xor_sync(0xFFFFFFFFu, gb3, o);
+  for (int o = 16; o > 0; o >>= 1) {
     lsum += __shfl_xor_sync(0xFFFFFFFFu, lsum, o);
-  }
-  // the block's four warp partials, added in warp order: one partial per block
-  __shared__ float wp[4][kBwdPart];
-  float* out = wp[threadIdx.x >> 5];
-  if (g == 0) {
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      const int j = 8 * t + 2 * c;
-      out[j] = gb1[2 * t];
-      out[j + 1] = gb1[2 * t + 1];
-      out[kHid + j] = gb2[2 * t];
-      out[kHid + j + 1] = gb2[2 * t + 1];
-      out[2 * kHid + j] = gw3[2 * t];
-      out[2 * kHid + j + 1] = gw3[2 * t + 1];
-    }
+    gb3 += __shfl_xor_sync(0xFFFFFFFFu, gb3, o);
   }
   if (lane == 0) {
-    out[3 * kHid] = gb3;
-    out[3 * kHid + 1] = lsum * inv_n;
+    red[2 * warp] = lsum;
+    red[2 * warp + 1] = gb3;
   }
+  tc_fence_before();
   __syncthreads();
-  for (int i = threadIdx.x; i < kBwdPart; i += blockDim.x)
-    part[(size_t)blockIdx.x * kBwdPart + i] = ((wp[0][i] + wp[1][i]) + wp[2][i]) + wp[3][i];
-}
-
-__device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16* p, uint64_t stride, uint64_t n,
-                                            uint64_t r, int col) {
-  const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
-  const __nv_bfloat16 lo = r < n ? p[r * stride + col] : z;
-  const __nv_bfloat16 hi = r + 1 < n ? p[(r + 1) * stride + col] : z;
-  __nv_bfloat162 v;
-  v.x = lo;
-  v.y = hi;
-  return *reinterpret_cast<const uint32_t*>(&v);
-}
-
-// Weight gradients, split over the batch: dW2 = H1^T dH2 (64x64) and
-// dW1 = X^T dH1 (8x64), K = the batch rows.  Block = 5 warps: warps 0..3 own
-// the 16-row m-tiles of dW2, warp 4 the (padded) m-tile of dW1; each block
-// takes one row range, accumulates in registers and writes its partial once.
-__global__ void __launch_bounds__(160) mlp_wgrad_kernel(
-    const float* __restrict__ x, uint64_t n, const __nv_bfloat16* __restrict__ h1s,
-    const __nv_bfloat16* __restrict__ dh2s, const __nv_bfloat16* __restrict__ dh1s,
-    uint64_t rows_per_block, float* __restrict__ part) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
-  const uint64_t r_begin = blockIdx.x * rows_per_block;
-  const uint64_t r_end = min(n, r_begin + rows_per_block);
-  float acc[8][4];
-#pragma unroll
-  for (int t = 0; t < 8; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.0f;
-  const __nv_bfloat16* B = warp < 4 ? dh2s : dh1s;
-  for (uint64_t r0 = r_begin; r0 < r_end; r0 += 16) {
-    uint32_t a0, a1, a2, a3;
-    if (warp < 4) {
-      const int m = 16 * warp + g;
-      a0 = ld_pair(h1s, kHid, r_end, r0 + 2 * c, m);
-      a1 = ld_pair(h1s, kHid, r_end, r0 + 2 * c, m + 8);
-      a2 = ld_pair(h1s, kHid, r_end, r0 + 2 * c + 8, m);
-      a3 = ld_pair(h1s, kHid, r_end, r0 + 2 * c + 8, m + 8);
-    } else {
-      // X^T rows are features: g < 8 real, g + 8 padding
-      const uint64_t ra = r0 + 2 * c, rb = r0 + 2 * c + 8;
-      const float xa = ra < r_end ? x[ra * kIn + g] : 0.0f;
-      const float xb = ra + 1 < r_end ? x[(ra + 1) * kIn + g] : 0.0f;
-      const float xc = rb < r_end ? x[rb * kIn + g] : 0.0f;
-      const float xd = rb + 1 < r_end ? x[(rb + 1) * kIn + g] : 0.0f;
-      a0 = pack_bf16(xa, xb);
-      a1 = 0u;
-      a2 = pack_bf16(xc, xd);
-      a3 = 0u;
-    }
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      const uint32_t b0 = ld_pair(B, kHid, r_end, r0 + 2 * c, 8 * t + g);
-      const uint32_t b1 = ld_pair(B, kHid, r_end, r0 + 2 * c + 8, 8 * t + g);
-      mma_bf16(acc[t], a0, a1, a2, a3, b0, b1);
-    }
+  tc_fence_after();
+  if (t == 0) {
+    bp[3 * kHid] = ((red[1] + red[3]) + red[5]) + red[7];
+    bp[3 * kHid + 1] =
+        ok ? (((red[0] + red[2]) + red[4]) + red[6]) * inv_n : __int_as_float(0x7FC00000);
   }
-  float* out = part + (size_t)blockIdx.x * kWgPart;
-#pragma unroll
-  for (int t = 0; t < 8; ++t) {
-    const int col = 8 * t + 2 * c;
-    if (warp < 4) {
-      const int m = 16 * warp + g;
-      out[m * kHid + col] = acc[t][0];
-      out[m * kHid + col + 1] = acc[t][1];
-      out[(m + 8) * kHid + col] = acc[t][2];
-      out[(m + 8) * kHid + col + 1] = acc[t][3];
-    } else {
-      out[kHid * kHid + g * kHid + col] = acc[t][0];
-      out[kHid * kHid + g * kHid + col + 1] = acc[t][1];
-    }
-  }
+  if (warp == 0) tc_dealloc(tm, 256);
 }
 
 // grad[i] (and, for i = KL_MLP_NPARAMS, the loss) = the sum of the partials
@@ -299,17 +490,21 @@ extern "C" int kl_mlp_forward(const float* d_params, const float* d_x, uint64_t 
                               void* stream) {
   if (n == 0) return KL_OK;
   if (!d_params || !d_x || !d_y) return KL_EINVAL;
+  if (((uintptr_t)d_x & 15u) != 0) return KL_EINVAL;
   const int sms = sm_count();
   if (sms <= 0) return KL_ECUDA;
-  const uint64_t tiles = (n + 15) / 16, blocks = (tiles + 3) / 4;
-  const unsigned grid = (unsigned)(blocks < (uint64_t)sms * 8 ? blocks : (uint64_t)sms * 8);
-  mlp_forward_kernel<<<grid, 128, 0, (cudaStream_t)stream>>>(d_params, d_x, n, d_y);
+  if (cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kFwdSmem) != cudaSuccess)
+    return KL_ECUDA;
+  const uint64_t tiles = (n + kTile - 1) / kTile;
+  const unsigned grid = (unsigned)(tiles < (uint64_t)sms * 3 ? tiles : (uint64_t)sms * 3);
+  mlp_forward_kernel<<<grid, kTile, kFwdSmem, (cudaStream_t)stream>>>(d_params, d_x, n, d_y);
   return check_launch();
 }
 
 extern "C" size_t kl_mlp_scratch_bytes(uint64_t n) {
-  return 3 * align256((size_t)n * kHid * sizeof(__nv_bfloat16)) +
-         align256((size_t)kBwdMaxBlocks * kBwdPart * sizeof(float)) +
+  (void)n;
+  return align256((size_t)kBwdMaxBlocks * kBwdPart * sizeof(float)) +
          align256((size_t)kWgMaxBlocks * kWgPart * sizeof(float));
 }
 
@@ -319,34 +514,25 @@ extern "C" int kl_mlp_grad(const float* d_params, const float* d_x, const float*
   if (n == 0 || !d_params || !d_x || !d_t || !d_grad || !d_loss || !d_scratch) return KL_EINVAL;
   if (!(under_weight > 0.0f)) return KL_EINVAL;
   if (scratch_bytes < kl_mlp_scratch_bytes(n)) return KL_ENOSPACE;
-  if (((uintptr_t)d_scratch & 255u) != 0) return KL_EINVAL;
+  if (((uintptr_t)d_scratch & 255u) != 0 || ((uintptr_t)d_x & 15u) != 0) return KL_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   const int sms = sm_count();
   if (sms <= 0) return KL_ECUDA;
-  const size_t part = align256((size_t)n * kHid * sizeof(__nv_bfloat16));
-  char* base = (char*)d_scratch;
-  __nv_bfloat16* h1s = (__nv_bfloat16*)base;
-  __nv_bfloat16* dh2s = (__nv_bfloat16*)(base + part);
-  __nv_bfloat16* dh1s = (__nv_bfloat16*)(base + 2 * part);
-  float* bwd_part = (float*)(base + 3 * part);
+  if (cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kGradSmem) != cudaSuccess)
+    return KL_ECUDA;
+  float* bwd_part = (float*)d_scratch;
   float* wg_part =
-      (float*)(base + 3 * part + align256((size_t)kBwdMaxBlocks * kBwdPart * sizeof(float)));
-  // backward: 4 warps per block, 16-row tiles, at most 4 blocks per SM
-  const uint64_t tiles = (n + 15) / 16, blocks = (tiles + 3) / 4;
-  uint64_t grid = blocks < (uint64_t)sms * 4 ? blocks : (uint64_t)sms * 4;
-  if (grid > (uint64_t)kBwdMaxBlocks) grid = kBwdMaxBlocks;
-  mlp_backward_kernel<<<(unsigned)grid, 128, 0, s>>>(d_params, d_x, d_t, n, under_weight,
-                                                     bwd_part, h1s, dh2s, dh1s);
+      (float*)((char*)d_scratch + align256((size_t)kBwdMaxBlocks * kBwdPart * sizeof(float)));
+  // one CTA per SM (its shared memory allows no second), tiles of 128 rows
+  const uint64_t tiles = (n + kTile - 1) / kTile;
+  uint64_t grid = tiles < (uint64_t)sms ? tiles : (uint64_t)sms;
+  if (grid > (uint64_t)kWgMaxBlocks) grid = kWgMaxBlocks;
+  mlp_grad_kernel<<<(unsigned)grid, kTile, kGradSmem, s>>>(d_params, d_x, d_t, n, under_weight,
+                                                           bwd_part, wg_part);
   if (check_launch() != KL_OK) return KL_ECUDA;
-  // weight gradients: row ranges of at least 64 rows, at most kWgMaxBlocks of them
-  uint64_t rows_per_block = (n + kWgMaxBlocks - 1) / kWgMaxBlocks;
-  rows_per_block = rows_per_block < 64 ? 64 : (rows_per_block + 15) / 16 * 16;
-  const uint64_t wblocks = (n + rows_per_block - 1) / rows_per_block;
-  mlp_wgrad_kernel<<<(unsigned)wblocks, 160, 0, s>>>(d_x, n, h1s, dh2s, dh1s, rows_per_block,
-                                                     wg_part);
-  if (check_launch() != KL_OK) return KL_ECUDA;
-  mlp_reduce_kernel<<<KL_MLP_NPARAMS + 1, 128, 0, s>>>(bwd_part, (int)grid, wg_part,
-                                                       (int)wblocks, d_grad, d_loss);
+  mlp_reduce_kernel<<<KL_MLP_NPARAMS + 1, 128, 0, s>>>(bwd_part, (int)grid, wg_part, (int)grid,
+                                                       d_grad, d_loss);
   return check_launch();
 }
 
