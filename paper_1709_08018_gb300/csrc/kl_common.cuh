@@ -740,13 +740,29 @@ __device__ __noinline__ UnitTally fallback_unit(const Pre64* __restrict__ pre,
 // infinity or NaN gives a t whose bits put col outside [0, W) (|axi| < 2^20
 // and W <= 2^16), so one unsigned compare per coordinate rejects
 // out-of-window and non-finite words alike.  Within one prefix kx and ky are
-// fixed, so two words share a pixel exactly when their t bits agree: the
-// current run keeps its pixel's (t_u, t_u) and (t_v, t_v) bit pairs, and a
-// pair of words that both fall in that pixel is settled by two 64-bit compares,
-// without forming pixel ids; the run's length is taken from the pair index
-// when the run ends.
+// fixed, so two words share a pixel exactly when their t bits agree.
+//
+// Runs: consecutive suffix points usually land in one pixel.  The current
+// run is kept as its pixel's t bits (cu, cv), doubled into the packed CU, CV,
+// so that a pair of words that both fall in it is settled by two 64-bit
+// compares; the run's length is taken from the pair index when it ends, and
+// only then is its pixel id formed and one atomic issued.  A run may lie
+// outside the window (its words are then dropped when it ends), so words
+// outside the window also take the two-compare path while they keep to one
+// (virtual) pixel.  Runs start afresh for every prefix.
+__device__ __forceinline__ void flush_run(uint32_t cu, uint32_t cv, uint32_t n, const Pre32& k,
+                                          const View& V, Tally& t,
+                                          uint32_t* __restrict__ img) {
+  const int col = (int)cu - k.kx, row = (int)cv - k.ky;
+  if (n && (uint32_t)col < V.W && (uint32_t)row < V.H) {
+    atomicAdd(img + (uint32_t)row * V.W + (uint32_t)col, n);
+    ++t.atomics;
+    t.in_window += n;
+  }
+}
+
 // Mixed words of prefix slot `slot` on suffix point pairs [k0, k1) of first
-// letter u (see the comment above for the pixel arithmetic).
+// letter u (see the comment above for the pixel arithmetic and the runs).
 template <bool BBOX = false>
 __device__ __forceinline__ void mixed_slot_words(uint32_t slot, int u, uint32_t k0, uint32_t k1,
                                                  const Plan& L, const View& V, const Tables& T,
@@ -758,13 +774,17 @@ __device__ __forceinline__ void mixed_slot_words(uint32_t slot, int u, uint32_t 
   const f2 C1 = pk(k.c1, k.c1), C2 = pk(k.c2, k.c2), C3 = pk(k.c3, k.c3), C4 = pk(k.c4, k.c4);
   const f2 AX = pk(k.axf, k.axf), AY = pk(k.ayf, k.ayf);
   const f2 magic = 0x4B4000004B400000ull;  // (1.5 * 2^23, 1.5 * 2^23)
-  const int W = (int)V.W;
   const float4* src = T.suf32p + (size_t)u * L.npairs;
   int bc0 = 0x7FFFFFFF, bc1 = -0x7FFFFFFF, br0 = 0x7FFFFFFF, br1 = -0x7FFFFFFF;
-  // t bits of the current run's pixel, doubled; 0 (never a t value) = no
-  // in-window run.  Runs start afresh for every prefix (t.flush below).
+  t.flush(img);
+  t.cur = -1;
+  // the current run: its pixel's t bits, doubled, in CU and CV (the low
+  // halves are the bits); `run` words before pair e_run, and every pair from
+  // e_run on that matched it.  It starts as bits (0, 0) with no word (no
+  // in-window word has them).
+  uint32_t run = 0;
   f2 CU = 0, CV = 0;
-  uint32_t e_run = k0;  // pairs [e_run, e) took the fast path into the current run
+  uint32_t e_run = k0;
 #pragma unroll 4
   for (uint32_t e = k0; e < k1; ++e) {
     const float4 s = __ldg(src + e);
@@ -779,19 +799,18 @@ __device__ __forceinline__ void mixed_slot_words(uint32_t slot, int u, uint32_t 
     const f2 TU = add2_rm(fma2(tx, rr, AX), magic);
     const f2 TV = add2_rm(fma2(ty, rr, AY), magic);
     if (!((TU == CU) & (TV == CV))) {
-      t.run += 2u * (e - e_run);
+      const uint32_t ua = (uint32_t)TU, ub = (uint32_t)(TU >> 32);
+      const uint32_t va = (uint32_t)TV, vb = (uint32_t)(TV >> 32);
+      const uint32_t cu = (uint32_t)CU, cv = (uint32_t)CV;
+      const bool a_in = (ua == cu) & (va == cv);
+      const bool ab = (ua == ub) & (va == vb);
+      run += 2u * (e - e_run) + (a_in ? 1u : 0u);
       e_run = e + 1;
-      float tua, tub, tva, tvb;
-      upk(TU, tua, tub);
-      upk(TV, tva, tvb);
-      const int ca = __float_as_int(tua) - k.kx, cb = __float_as_int(tub) - k.kx;
-      const int ra = __float_as_int(tva) - k.ky, rb = __float_as_int(tvb) - k.ky;
-      const bool oka = ((uint32_t)ca < V.W) & ((uint32_t)ra < V.H);
-      const bool okb = ((uint32_t)cb < V.W) & ((uint32_t)rb < V.H);
-      t.add(oka ? ra * W + ca : -1, img);
-      t.add(okb ? rb * W + cb : -1, img);
-      CU = okb ? pk(tub, tub) : 0ull;
-      CV = okb ? pk(tvb, tvb) : 0ull;
+      flush_run(cu, cv, run, k, V, t, img);
+      if (!a_in && !ab) flush_run(ua, va, 1u, k, V, t, img);  // word a on its own
+      run = (!a_in && ab) ? 2u : 1u;
+      CU = TU >> 32 | (TU & 0xFFFFFFFF00000000ull);
+      CV = TV >> 32 | (TV & 0xFFFFFFFF00000000ull);
     }
     if (BBOX) {
       float ua, ub, va, vb;
@@ -807,9 +826,9 @@ __device__ __forceinline__ void mixed_slot_words(uint32_t slot, int u, uint32_t 
       }
     }
   }
-  t.run += 2u * (k1 - e_run);
+  run += 2u * (k1 - e_run);
+  flush_run((uint32_t)CU, (uint32_t)CV, run, k, V, t, img);
   words += min(2u * k1, L.ns) - 2u * k0;
-  t.flush(img);
   if (BBOX) box_merge(*B, slot, bc0, bc1, br0, br1);
 }
 
