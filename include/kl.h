@@ -465,8 +465,9 @@ KL_API int kl_render_noalloc(const kl_params* p, uint32_t* d_image, uint64_t* d_
  * ev_stop (cudaEvent_t, created by the caller) on its stream immediately
  * before and after its main per-word kernel (the FP64 or mixed render
  * kernel), so that the caller can time that kernel alone with
- * cudaEventElapsedTime.  NULL, NULL switches it off.  The setting is global to
- * the process and applies to every following kl_render call.  This is an
+ * cudaEventElapsedTime.  NULL, NULL switches it off.  The setting belongs to
+ * the calling host thread and applies to every following kl_render call made
+ * from that thread (other threads are not affected).  This is an
  * addition of this library (the paper reports no timings); it changes no
  * result. */
 KL_API int kl_set_profile_events(void* ev_start, void* ev_stop);

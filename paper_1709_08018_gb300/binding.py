@@ -278,6 +278,22 @@ def render_multiseed(p: "Params", points, image=None, counters=None, workspace=N
     return out
 
 
+def render_repetends(p: "Params", image=None, counters=None, workspace=None, stream=None,
+                     device="cuda"):
+    """Repetend points: every word w of p drawn at w(fix t) for the parabolic
+    tails t, the limits of the infinite words w t t t ... (near a cusp the
+    orbit w t^n(z) reaches that limit only like 1/n, so a fixed-depth render
+    leaves it out).  The parabolic tails are the cyclic permutations of the
+    commutator abAB and of its inverse; their fixed points are the four
+    commutator points of kl_cusp_seeds (entries 4..7), and after any last
+    letter of w some reduced tail reaches each of them, so this is the
+    multi-seed render over those four points (4 N_d words drawn).  Add it to
+    p's ordinary render (accumulate = 1) to fill in the cusps."""
+    s16 = cusp_seeds(list(p.gens))
+    points = [complex(s16[2 * i], s16[2 * i + 1]) for i in range(4, 8)]
+    return render_multiseed(p, points, image, counters, workspace, stream, device)
+
+
 def params_group(gens, seeds8, depth: int, width: int, height: int, window: Sequence[float],
                  precision: int = FP64, **fields) -> Params:
     """Parameters for the caller's own generators and seeds (32 and 8

@@ -6,13 +6,16 @@
   python -m paper_1709_08018_gb300.cli --lod [--train-groups 4] [--train-steps 300]
       [--per-level 20000] [--held-out 1] [--repeat N]
   python -m paper_1709_08018_gb300.cli --scan [--depth 14] [--repeat N]
+  python -m paper_1709_08018_gb300.cli --mlp ROWS [--repeat N]
 
 Prints the counters and the device time of the last render.  With --repeat N
 the render runs N times (the first ones serve as warm-up for profilers).
 --batch G renders the first G groups of the seeded 256-group sweep (depth
 12..18, 1024^2 each) in one batched launch.  --lod trains the pruning network
 briefly on a few seeded groups (labels, gradient and Adam kernels) and runs
-the pruned depth-22 render of one held-out group at 8192^2.
+the pruned depth-22 render of one held-out group at 8192^2.  --mlp ROWS
+times the network's training step (gradient and Adam kernels) on ROWS seeded
+random rows, N steps after 3 untimed ones.
 """
 import argparse
 import os
@@ -48,6 +51,7 @@ def main(argv=None):
     ap.add_argument("--per-level", type=int, default=20_000)
     ap.add_argument("--held-out", type=int, default=1)
     ap.add_argument("--scan", action="store_true")
+    ap.add_argument("--mlp", type=int, default=0, help="rows of a training-step timing")
     ap.add_argument("--tiling", action="store_true")
     ap.add_argument("--cull", action="store_true", help="place certified blocks of words at once")
     a = ap.parse_args(argv)
@@ -57,6 +61,8 @@ def main(argv=None):
         return run_lod(a, kl, klsynth, torch)
     if a.scan:
         return run_scan(a, kl, klsynth, torch)
+    if a.mlp:
+        return run_mlp(a, kl, torch)
     c = named[a.config]
     ta = a.ta if a.ta is not None else c.group.ta
     tb = a.tb if a.tb is not None else c.group.tb
@@ -119,6 +125,28 @@ def run_scan(a, kl, klsynth, torch):
     c = cnt.cpu().tolist()
     print(f"scan d={d}: strings {4 ** d}, kept {c[2]}, in-window {c[0]}, "
           f"{e0.elapsed_time(e1):.3f} ms")
+
+
+def run_mlp(a, kl, torch):
+    """Training steps of the network (kl_mlp_grad + kl_mlp_adam) on --mlp
+    seeded random rows; the per-step time of the last --repeat steps."""
+    g = torch.Generator(device="cuda")
+    g.manual_seed(1709)
+    params = 0.1 * torch.randn(kl.KL_MLP_NPARAMS, device="cuda", generator=g)
+    x = torch.randn(a.mlp, 8, device="cuda", generator=g)
+    t = torch.randn(a.mlp, device="cuda", generator=g)
+    tr = kl.MlpTrainer(params, lr=1e-3)
+    for _ in range(3):
+        tr.step(x, t)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.repeat):
+        tr.step(x, t)
+    e1.record()
+    torch.cuda.synchronize()
+    print(f"mlp training: {a.mlp} rows, {a.repeat} steps, "
+          f"{1000.0 * e0.elapsed_time(e1) / a.repeat:.1f} us per step, "
+          f"loss {float(tr.loss.item()):.4f}")
 
 
 def run_lod(a, kl, klsynth, torch):

@@ -402,7 +402,12 @@ __device__ void part_entry(const Group& G, const Plan& L, int renorm, uint32_t i
     e.pad[0] = e.pad[1] = e.pad[2] = 0;
     T.Sot[slot] = e;
   } else {
-    // suffix tail: the orbit of the seed of w_d, innermost letter first
+    // suffix tail: the orbit of the seed of w_d, innermost letter first.  A
+    // plan always has at least one tail letter (si >= 1 for suffixes of one
+    // or more letters); words of length 1 build no tables (their callers
+    // render them directly or reject them), and a plan without tail letters
+    // has no tail entries to build: w_{si-1} would not exist.
+    if (L.si < 1) return;
     const uint32_t slot = idx - nL - nH - nSo;
     int w[kMaxSuffix];
     w[0] = (int)(slot / L.p3_si1);

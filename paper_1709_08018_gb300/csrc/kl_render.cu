@@ -276,8 +276,9 @@ __global__ void eval_kernel(const uint64_t* __restrict__ idx, uint64_t n, uint64
 // ---------------------------------------------------------------------------
 // host side
 
-// caller events recorded around the main per-word kernel (kl_set_profile_events)
-cudaEvent_t g_prof_start = nullptr, g_prof_stop = nullptr;
+// caller events recorded around the main per-word kernel (kl_set_profile_events),
+// one setting per host thread
+thread_local cudaEvent_t g_prof_start = nullptr, g_prof_stop = nullptr;
 
 int prof_mark(cudaEvent_t e, cudaStream_t s) {
   if (!e) return KL_OK;

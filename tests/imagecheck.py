@@ -57,3 +57,39 @@ def iou(a: np.ndarray, b: np.ndarray) -> float:
     oa, ob = a > 0, b > 0
     union = np.logical_or(oa, ob).sum()
     return 1.0 if union == 0 else float(np.logical_and(oa, ob).sum()) / float(union)
+
+
+def check_band_image(got: np.ndarray, ref, eta: float):
+    """check_fp64_image for large edge logs (vectorised), same rules: with
+    S = the oracle image less its edge words, GPU - S must be >= 0, at most
+    the number of edge words whose candidate pixels (floor(c +- eta) in each
+    coordinate) include the pixel, and its total between the edge words that
+    cannot leave the window and all edge words.  eta < 1/2.  Returns the
+    number of edge-word hits the GPU image holds."""
+    assert eta < 0.5
+    H, W = ref.image.shape
+    assert got.shape == (H, W)
+    assert ref.edge_total == len(ref.edge_idx), "edge log overflowed"
+    u = ref.edge_uv[:, 0]
+    v = ref.edge_uv[:, 1]
+    S = ref.image.astype(np.int64).ravel().copy()
+    ins = (u >= 0) & (u < W) & (v >= 0) & (v < H)
+    own = np.floor(v[ins]).astype(np.int64) * W + np.floor(u[ins]).astype(np.int64)
+    S -= np.bincount(own, minlength=H * W)
+    assert (S >= 0).all()
+    c_lo, c_hi = np.floor(u - eta), np.floor(u + eta)
+    r_lo, r_hi = np.floor(v - eta), np.floor(v + eta)
+    cap = np.zeros(H * W, dtype=np.int64)
+    for r, rok in ((r_lo, np.ones_like(u, dtype=bool)), (r_hi, r_hi != r_lo)):
+        for c, cok in ((c_lo, np.ones_like(u, dtype=bool)), (c_hi, c_hi != c_lo)):
+            sel = rok & cok & (r >= 0) & (r < H) & (c >= 0) & (c < W)
+            cap += np.bincount(r[sel].astype(np.int64) * W + c[sel].astype(np.int64),
+                               minlength=H * W)
+    may_drop = (c_lo < 0) | (c_hi >= W) | (r_lo < 0) | (r_hi >= H)
+    must_land = int((~may_drop).sum())
+    D = got.astype(np.int64).ravel() - S
+    assert (D >= 0).all(), f"GPU misses hits at {np.argwhere(D < 0)[:10].ravel().tolist()}"
+    assert (D <= cap).all(), f"GPU extra hits at {np.argwhere(D > cap)[:10].ravel().tolist()}"
+    extra = int(D.sum())
+    assert must_land <= extra <= ref.edge_total, (must_land, extra, ref.edge_total)
+    return extra

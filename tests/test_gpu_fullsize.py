@@ -12,7 +12,7 @@ import pytest
 
 import klsynth
 import oracle
-from imagecheck import check_fp64_image, iou
+from imagecheck import check_band_image, check_fp64_image, iou
 
 pytestmark = pytest.mark.gpu
 
@@ -85,6 +85,29 @@ def test_gasket_d18_mixed_image(kl, c2_oracle):
     diff = np.abs(got.astype(np.int64) - c2_oracle.image.astype(np.int64)).sum()
     print(f"\ngasket d18 mixed: IoU {v:.6f}, L1 hit difference {diff} of {cfg.n_words}, "
           f"fp64 words {int(c[2])}")
+
+
+def test_gasket_d18_mixed_image_band(kl):
+    """The mixed image pixel by pixel at the mixed tolerance: every word whose
+    value lies farther than 2e-5 max(1, |z|) from a pixel edge lands in the
+    oracle's pixel (the gasket's limit set has |z| <= 1.4, so the band is
+    2e-5 x 1.4 in z, 0.038 px), and every other word in one of its candidate
+    pixels.  The split is the one the benchmark times (prefix 10, suffix 8)."""
+    cfg = klsynth.C2
+    g, s = oracle.group(cfg.group.ta, cfg.group.tb)
+    sx = cfg.width / (cfg.window[1] - cfg.window[0])
+    eta = TOL32 * 1.4 * sx
+    ref = oracle.render(g, s, cfg.depth, cfg.window, cfg.width, cfg.height, eta=eta,
+                        edge_cap=1 << 27)
+    p = kl.params_init(cfg.group.ta, cfg.group.tb, cfg.depth, cfg.width, cfg.height,
+                       cfg.window, kl.MIXED)
+    img, cnt = kl.render(p)
+    got = img.cpu().numpy().view(np.uint32)
+    extra = check_band_image(got, ref, eta)
+    c = cnt.cpu().numpy()
+    assert int(c[0]) + int(c[1]) == cfg.n_words
+    print(f"\ngasket d18 mixed, band {eta:.4f} px: edge words {ref.edge_total}, "
+          f"their hits in the image {extra}")
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])

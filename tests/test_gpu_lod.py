@@ -118,24 +118,64 @@ def test_labels_recursion_and_oracle(kl):
                 assert lab == 1 + max(ch)
             else:
                 assert lab in (0, 1)
+    # Level-hi labels, exactly: the label kernel bins each word at the value
+    # the render computes (the mixed FP32 local frame, or FP64 for fallback
+    # prefixes) into 1/256-pixel fixed point.  kl_eval_words returns those same
+    # values for the same plan (prefix length hi), so boxes built from them
+    # must give the same resolved / unresolved decision for every node.
     g, s = oracle.group(group.ta, group.tb)
-    agree = 0
     nh = 4 * 3 ** (hi - 1)
     ext = 256  # extent 1 pixel, in 1/256-pixel fixed point
-    for slot in range(nh):
-        u, v = subtree_pixels(g, s, d, hi, slot, window, size)
+    q = kl.Params.from_buffer_copy(p)
+    q.prefix_len = hi
+    sat = float(1 << 30)
+
+    def resolved_of(u, v):
         fin = np.isfinite(u) & np.isfinite(v)
         if not fin.any():
-            resolved = True
-        else:
-            cu = np.floor(256.0 * u[fin]).astype(np.int64)
-            cv = np.floor(256.0 * v[fin]).astype(np.int64)
-            outside = cu.max() < 0 or cu.min() >= 256 * size or cv.max() < 0 or \
-                cv.min() >= 256 * size
-            small = cu.max() - cu.min() < ext and cv.max() - cv.min() < ext
-            resolved = outside or small
-        agree += (labels[base[hi] + slot] == 0) == resolved
-    assert agree >= 0.995 * nh, (agree, nh)
+            return True
+        # floor(256 u), saturated as the kernel saturates far words
+        cu = np.clip(np.floor(256.0 * u[fin]), -sat, sat).astype(np.int64)
+        cv = np.clip(np.floor(256.0 * v[fin]), -sat, sat).astype(np.int64)
+        far_u, far_v = np.abs(u[fin]) >= 2.0 ** 20, np.abs(v[fin]) >= 2.0 ** 20
+        cu[far_u] = np.sign(u[fin][far_u]).astype(np.int64) * (1 << 30)
+        cv[far_v] = np.sign(v[fin][far_v]).astype(np.int64) * (1 << 30)
+        outside = cu.max() < 0 or cu.min() >= 256 * size or cv.max() < 0 or \
+            cv.min() >= 256 * size
+        small = cu.max() - cu.min() < ext and cv.max() - cv.min() < ext
+        return outside or small
+
+    ids_all = [node_word_ids(d, hi, slot) for slot in range(nh)]
+    uv = kl.eval_words(q, dev_index(np.concatenate(ids_all))).cpu().numpy()
+    same, agree_oracle, off = 0, 0, 0
+    for slot in range(nh):
+        n_w = len(ids_all[slot])
+        mine = resolved_of(uv[off:off + n_w, 0], uv[off:off + n_w, 1])
+        off += n_w
+        same += (labels[base[hi] + slot] == 0) == mine
+        u, v = subtree_pixels(g, s, d, hi, slot, window, size)
+        agree_oracle += (labels[base[hi] + slot] == 0) == resolved_of(u, v)
+    assert same == nh, (same, nh)
+    # against the oracle's FP64 values the decisions may differ only where a
+    # box side lies within rounding of the one-pixel extent or of the window
+    # border (the mixed words differ from the oracle's by ~1e-8 relative)
+    assert agree_oracle >= 0.995 * nh, (agree_oracle, nh)
+
+
+def dev_index(idx):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(idx, dtype=np.uint64).view(np.int64)).cuda()
+
+
+def node_word_ids(d, k, slot):
+    """Word indices of the 3^(d-k) words below level-k node `slot`."""
+    prefix = node_letters(k, slot)
+    idx = prefix[0]
+    for j in range(1, k):
+        ban = (prefix[j - 1] + 2) % 4
+        idx = idx * 3 + [y for y in range(4) if y != ban].index(prefix[j])
+    m = d - k
+    return np.arange(idx * 3 ** m, (idx + 1) * 3 ** m, dtype=np.uint64)
 
 
 def node_letters(k, slot):
@@ -205,4 +245,16 @@ def test_trained_network_gain(kl):
         e = lod.evaluate(p, mlp, lo, hi, tuned["margin"], tuned["edge"], repeats=2)
         assert e.words == kl.word_count(d)
         assert e.iou >= 0.999, (e, tuned)
+        # the gain over the method without the network: the per-word render
         assert e.pruned_ms < 0.8 * e.exact_ms, (e, tuned)
+        # and the comparison with the exact culled render (kl_params.cull),
+        # which certifies the same sub-pixel subtrees exactly: measured and
+        # reported, not asserted in the network's favour (it loses, see the
+        # bench line's lod.culled)
+        q = kl.Params.from_buffer_copy(p)
+        q.cull = 1
+        rc = kl.Renderer(q)
+        culled_ms = lod.time_ms(lambda: rc(), 2)
+        print(f"\nheld-out group: per-word {e.exact_ms:.2f} ms, pruned {e.pruned_ms:.2f} ms "
+              f"(IoU {e.iou:.5f}), culled exact {culled_ms:.2f} ms")
+        assert culled_ms < e.exact_ms

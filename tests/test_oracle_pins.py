@@ -440,3 +440,81 @@ def test_multiseed_render_matches_the_scan(ta, tb, d):
     r = oracle.render_multiseed(g, pts, d, window, 64, 48, threads=2)
     assert np.array_equal(r.image.astype(np.int64), img)
     assert r.dropped == dropped and r.in_window + r.dropped == 8 * oracle.word_count(d)
+
+
+# --------------------------------------------------------------------------
+# repetends (Sec. "The revised deterministic approach": near (nearly)
+# parabolic points orbits run slower and slower; the book the paper builds on
+# adds "repetends").  Reading: a repetend is a periodic tail t of an infinite
+# word w t t t ..., whose limit point is w(fix t).  The parabolic tails are the
+# cyclic permutations of the commutator abAB and of its inverse BAba.
+
+PARABOLIC_TAILS = ["abAB", "bABa", "ABab", "BabA", "BAba", "AbaB", "baBA", "aBAb"]
+CODE = {"a": 0, "b": 1, "A": 2, "B": 3}
+
+
+def word_matrix(G, letters):
+    M = np.eye(2, dtype=complex)
+    for x in letters:
+        M = M @ G[CODE[x]]
+    return M
+
+
+@pytest.mark.parametrize("ta,tb", [GASKET, NEAR_CUSP] + TRACE_PAIRS[3:5])
+def test_repetend_points_are_the_commutator_fixed_points(ta, tb):
+    """The 8 parabolic tails fix 4 distinct points, the last four points of
+    the multi-seed list (a tail and its inverse share a fixed point); after
+    any last letter w_d, each of the 4 points is the limit of a reduced
+    continuation (a tail whose first letter is not the inverse of w_d)."""
+    G, _, g, _ = mats(ta, tb)
+    out = oracle.cusp_seeds(g)
+    cusps = [complex(out[2 * i], out[2 * i + 1]) for i in range(4, 8)]
+    for t in PARABOLIC_TAILS:
+        T = word_matrix(G, t)
+        assert abs(np.trace(T) + 2) < 1e-9 * max(1.0, np.abs(T).max() ** 2)
+        d = [abs(mob(T, z) - z) / max(1.0, abs(z)) for z in cusps]
+        assert min(d) < 1e-7, t
+    for wd in "abAB":
+        inv = {"a": "A", "A": "a", "b": "B", "B": "b"}[wd]
+        reached = set()
+        for t in PARABOLIC_TAILS:
+            if t[0] != inv:
+                T = word_matrix(G, t)
+                reached.add(int(np.argmin([abs(mob(T, z) - z) for z in cusps])))
+        assert reached == {0, 1, 2, 3}, wd
+
+
+@pytest.mark.parametrize("ta,tb", [GASKET, NEAR_CUSP])
+def test_parabolic_tails_converge_like_one_over_n(ta, tb):
+    """w t^n (z) -> w(fix t) only like 1/n for a parabolic tail t (the slow
+    orbits of the paper's remark), against geometric convergence for a
+    loxodromic tail: the error falls about tenfold from n = 100 to 1000."""
+    G, seeds, g, _ = mats(ta, tb)
+    out = oracle.cusp_seeds(g)
+    cusps = [complex(out[2 * i], out[2 * i + 1]) for i in range(4, 8)]
+    W = word_matrix(G, "abaBA")   # any reduced head; its last letter A
+    for t in ["baBA", "aBAb"]:     # tails allowed after A (first letter not a)
+        T = word_matrix(G, t)
+        fix = cusps[int(np.argmin([abs(mob(T, z) - z) for z in cusps]))]
+        z = seeds[CODE[t[-1]]]
+        err = {}
+        for n in range(1, 1001):
+            z = mob(T, z)
+            if n in (100, 1000):
+                err[n] = abs(mob(W, z) - mob(W, fix))
+        assert 7.0 < err[100] / err[1000] < 13.0, (t, err)
+
+
+def test_loxodromic_tail_converges_geometrically():
+    """The contrast: a loxodromic generator's orbit reaches its attracting
+    fixed point geometrically (a batch group, Re tr a > 2)."""
+    ta, tb = TRACE_PAIRS[3]
+    G, seeds, g, _ = mats(ta, tb)
+    a = G[0]
+    z, fix = 0.3 + 0.1j, seeds[0]
+    errs = []
+    for n in range(1, 41):
+        z = mob(a, z)
+        if n in (10, 20):
+            errs.append(abs(z - fix))
+    assert errs[1] < 1e-3 * errs[0]
