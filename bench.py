@@ -935,6 +935,7 @@ def run_ours(args):
         fp64_2, fp64_2_img = secondary(kl, klsynth.C2, kl.FP64, flush, stream, dev,
                                        max(3, KS // 4))
         mixed2["speedup_over_fp64"] = fp64_2["ms_per_step"] / mixed2["ms_per_step"]
+        fp64_1, fp64_1_img = secondary(kl, klsynth.C1, kl.FP64, flush, stream, dev, KS)
         uv = {(c.name, prec): eval_sample(kl, c, prec, dev)
               for c in (klsynth.C3, klsynth.C2) for prec in (kl.FP64, kl.MIXED)}
         if not args.no_cpu_baseline:
@@ -957,13 +958,16 @@ def run_ours(args):
             fp64_2["accuracy"] = dict(image_agreement(fp64_2_img, ref2),
                                       **sample_dz(klsynth.C2, uv[(klsynth.C2.name, kl.FP64)],
                                                   z2))
+            ref1, _, _ = oracle_render(klsynth.C1)
+            fp64_1["accuracy"] = image_agreement(fp64_1_img, ref1)
             line["iou_vs_oracle"] = line["accuracy"]["iou_vs_oracle"]
             line["max_dz_rel"] = line["accuracy"]["max_dz_rel"]
             del ref2
-        del fp64_img, mixed3_img, mixed2_img, fp64_2_img
+        del fp64_img, mixed3_img, mixed2_img, fp64_2_img, fp64_1_img
         line["mixed_nearcusp_d20"] = mixed3
         line["mixed_gasket_d18"] = mixed2
         line["fp64_gasket_d18"] = fp64_2
+        line["fp64_gasket_d10"] = fp64_1
         if not args.no_tiling:
             line["tiling"] = tiling_config(kl, dev, K, flush)
         if not args.no_scan:

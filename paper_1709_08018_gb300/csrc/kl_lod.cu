@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(BT, 1536 / BT) lod_exact_kernel(
     if (item >= total) break;
     if (MIXED && item < n64) {
       const uint32_t unit = item * BT + threadIdx.x;
-      if (unit < fb_units) {
+      if (MIXED && unit < fb_units) {
         const uint32_t e = unit / (3u * chunks), rem = unit % (3u * chunks);
         const uint32_t slot = (uint32_t)(T.fb[e] & 0xFFFFFFFFull);
         const UnitTally r = fallback_unit<true>(T.pre64, T.flags, T.suf64, slot, rem / chunks,
