@@ -40,6 +40,9 @@ FP32_OPS_PER_WORD = 12    # FP32 operations of the mixed per-word map: w = v + g
                           # |w|^2 (2), M w (4), M w / |w|^2 + alpha (2), the two floors (2)
 FP64_OPS_PER_WORD = 13    # FP64 operations of the plain per-word map: w = v + gamma (2),
                           # |w|^2 (2), reciprocal refinement (3), M w (4), final FMAs (2)
+DF64_OPS_PER_WORD = 151   # FP32 operations of the double-float per-word map: 6 double-float
+                          # sums (11 each), 2 squares and 6 products (7 each), the reciprocal's
+                          # Newton step (10), and the two pixel keys (4 each)
 SMS = 152
 FP32_LANES_PER_SM = 128
 FP64_LANES_PER_SM = 2
@@ -776,6 +779,16 @@ def roofline32(words_fp32, kern_ms, wl):
             "traffic": traffic_for("render_mixed_kernel", wl), "kernel_ms": kern_ms}
 
 
+def roofline_df(words_df, kern_ms, wl):
+    fp32_peak = fp_peaks()[0]
+    ach = words_df * DF64_OPS_PER_WORD / (kern_ms / 1000.0) / 1e12
+    return {"bound": "alu", "kernel": "render_df64_kernel", "achieved": ach, "peak": fp32_peak,
+            "unit": "T FP32-op/s", "frac": ach / fp32_peak,
+            "peak_kind": "derived: 152 SMs x 128 FP32 lanes x max SM clock",
+            "ops_per_word": DF64_OPS_PER_WORD,
+            "traffic": traffic_for("render_df64_kernel", wl), "kernel_ms": kern_ms}
+
+
 def secondary(kl, cfg, prec, flush, stream, dev, K):
     """One more whole-job render timed like the headline (N = 1): its rates,
     the roofline of its per-word kernel, its atomics and its image (host copy)
@@ -790,12 +803,16 @@ def secondary(kl, cfg, prec, flush, stream, dev, K):
     ms, kms = statistics.median(step_ms), statistics.median(kern_ms)
     cnt = [int(x) for x in r.counters.cpu().tolist()]
     assert cnt[0] + cnt[1] == cfg.n_words
-    out = {"workload": describe(cfg, "FP64" if prec == kl.FP64 else
-                                "mixed (FP32 per-word map, FP64 prefixes and fallback words)"),
+    name = {kl.FP64: "FP64",
+            kl.MIXED: "mixed (FP32 per-word map, FP64 prefixes and fallback words)",
+            kl.DF64: "double-float (per-word map in hi+lo float pairs on the FP32 pipe, "
+                     "FP64 prefixes and fallback words)"}[prec]
+    roof = (roofline64(cfg.n_words, kms, cfg.name) if prec == kl.FP64 else
+            roofline_df(cfg.n_words - cnt[2], kms, cfg.name) if prec == kl.DF64 else
+            roofline32(cfg.n_words - cnt[2], kms, cfg.name))
+    out = {"workload": describe(cfg, name),
            "words_per_step": cfg.n_words, "ms_per_step": ms,
-           "words_per_s": cfg.n_words / (ms / 1000.0), "steps": K,
-           "roofline": (roofline64(cfg.n_words, kms, cfg.name) if prec == kl.FP64 else
-                        roofline32(cfg.n_words - cnt[2], kms, cfg.name)),
+           "words_per_s": cfg.n_words / (ms / 1000.0), "steps": K, "roofline": roof,
            "counters": {"in_window": cnt[0], "dropped": cnt[1], "fp64_words": cnt[2],
                         "atomics": cnt[3]},
            "atomics_per_s": cnt[3] / (kms / 1000.0)}
@@ -931,13 +948,15 @@ def run_ours(args):
         KS = max(5, min(K, 20))
         mixed3, mixed3_img = secondary(kl, klsynth.C3, kl.MIXED, flush, stream, dev, KS)
         mixed3["speedup_over_fp64"] = (total_ms / K) / mixed3["ms_per_step"]
+        df3, df3_img = secondary(kl, klsynth.C3, kl.DF64, flush, stream, dev, KS)
+        df3["speedup_over_fp64"] = (total_ms / K) / df3["ms_per_step"]
         mixed2, mixed2_img = secondary(kl, klsynth.C2, kl.MIXED, flush, stream, dev, KS)
         fp64_2, fp64_2_img = secondary(kl, klsynth.C2, kl.FP64, flush, stream, dev,
                                        max(3, KS // 4))
         mixed2["speedup_over_fp64"] = fp64_2["ms_per_step"] / mixed2["ms_per_step"]
         fp64_1, fp64_1_img = secondary(kl, klsynth.C1, kl.FP64, flush, stream, dev, KS)
         uv = {(c.name, prec): eval_sample(kl, c, prec, dev)
-              for c in (klsynth.C3, klsynth.C2) for prec in (kl.FP64, kl.MIXED)}
+              for c in (klsynth.C3, klsynth.C2) for prec in (kl.FP64, kl.MIXED, kl.DF64)}
         if not args.no_cpu_baseline:
             # the oracle legs: the whole headline workload (the CPU baseline and
             # the reference image), the gasket render and the two samples
@@ -949,6 +968,8 @@ def run_ours(args):
             mixed3["accuracy"] = dict(image_agreement(mixed3_img, ref3),
                                       **sample_dz(klsynth.C3, uv[(klsynth.C3.name, kl.MIXED)],
                                                   z3))
+            df3["accuracy"] = dict(image_agreement(df3_img, ref3),
+                                   **sample_dz(klsynth.C3, uv[(klsynth.C3.name, kl.DF64)], z3))
             del ref3
             ref2, _, _ = oracle_render(klsynth.C2)
             idx2, z2 = oracle_sample(klsynth.C2)
@@ -963,7 +984,8 @@ def run_ours(args):
             line["iou_vs_oracle"] = line["accuracy"]["iou_vs_oracle"]
             line["max_dz_rel"] = line["accuracy"]["max_dz_rel"]
             del ref2
-        del fp64_img, mixed3_img, mixed2_img, fp64_2_img, fp64_1_img
+        del fp64_img, mixed3_img, mixed2_img, fp64_2_img, fp64_1_img, df3_img
+        line["df64_nearcusp_d20"] = df3
         line["mixed_nearcusp_d20"] = mixed3
         line["mixed_gasket_d18"] = mixed2
         line["fp64_gasket_d18"] = fp64_2

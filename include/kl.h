@@ -61,8 +61,18 @@ typedef enum {
 /* Arithmetic of the per-word work. */
 typedef enum {
   KL_FP64 = 0,   /* every step in FP64 */
-  KL_MIXED = 1   /* prefix products, renormalisation and near-parabolic words in
+  KL_MIXED = 1,  /* prefix products, renormalisation and near-parabolic words in
                     FP64; the per-word map in FP32 in a per-prefix local frame */
+  KL_DF64 = 2    /* prefix products, tables and pole-form constants in FP64; the
+                    per-word map in double-float arithmetic on the FP32 pipe (each
+                    value an unevaluated sum of two floats, about 48 significant bits,
+                    error-free sums and products built from FP32 adds and fused
+                    multiply-adds), giving word values within the FP64 tolerance
+                    (1e-9 relative) at FP32-pipe speed.  Prefixes whose pole form is
+                    invalid or out of float range (P10 ~ 0, pixel offsets >= 2^20,
+                    constants outside [1e-30, 1e30]) run in FP64.  kl_render (limit
+                    set and tiling), kl_render_noalloc and kl_eval_words only; not
+                    with cull = 1 */
 } kl_precision;
 
 /* Which words a render draws (Sec. "Implementation": the two drawing modes). */
@@ -153,7 +163,7 @@ typedef struct {
 enum {
   KL_CNT_IN_WINDOW = 0,    /* words drawn into the image */
   KL_CNT_DROPPED = 1,      /* words outside the window or non-finite */
-  KL_CNT_FP64_WORDS = 2,   /* KL_MIXED: words evaluated on the FP64 path */
+  KL_CNT_FP64_WORDS = 2,   /* KL_MIXED, KL_DF64: words evaluated on the FP64 path */
   KL_CNT_ATOMICS = 3,      /* image atomics issued (after run-length merging) */
   KL_N_COUNTERS = 4
 };

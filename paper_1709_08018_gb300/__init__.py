@@ -8,7 +8,7 @@ and fails loudly if it has not been built (``__graft_entry__.build()`` or
 ``python -m paper_1709_08018_gb300.build``).
 """
 from .binding import (  # noqa: F401
-    FP64, KL_CNT_ATOMICS, KL_CNT_DROPPED, KL_CNT_FP64_WORDS, KL_CNT_IN_WINDOW, KL_MLP_NPARAMS,
+    DF64, FP64, KL_CNT_ATOMICS, KL_CNT_DROPPED, KL_CNT_FP64_WORDS, KL_CNT_IN_WINDOW, KL_MLP_NPARAMS,
     KL_N_COUNTERS, KL_STATIC_SCRATCH_BYTES, LIMIT_SET, MIXED, TILING, Batch, KlError,
     LodRenderer, MlpTrainer, Params, Renderer, lod_labels, lod_node_count, Fsa, fsa, fsa_count,
     fsa_from_params, maskit, params_group, cusp_seeds, render_multiseed, render_repetends,

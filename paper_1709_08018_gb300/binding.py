@@ -8,7 +8,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libkl.so")
 
-FP64, MIXED = 0, 1
+FP64, MIXED, DF64 = 0, 1, 2
 LIMIT_SET, TILING = 0, 1  # kl_mode
 KL_CNT_IN_WINDOW, KL_CNT_DROPPED, KL_CNT_FP64_WORDS, KL_CNT_ATOMICS, KL_N_COUNTERS = 0, 1, 2, 3, 4
 

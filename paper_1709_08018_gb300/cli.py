@@ -40,7 +40,7 @@ def main(argv=None):
     ap.add_argument("--tb", type=complex)
     ap.add_argument("--depth", type=int)
     ap.add_argument("--size", type=int)
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "df64"], default="mixed")
     ap.add_argument("--prefix-len", type=int, default=0)
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--out")
@@ -69,7 +69,7 @@ def main(argv=None):
     depth = a.depth or c.depth
     W = H = a.size or c.width
     p = kl.params_init(ta, tb, depth, W, H, c.window,
-                       kl.MIXED if a.precision == "mixed" else kl.FP64,
+                       {"mixed": kl.MIXED, "fp64": kl.FP64, "df64": kl.DF64}[a.precision],
                        prefix_len=a.prefix_len, mode=kl.TILING if a.tiling else kl.LIMIT_SET,
                        cull=int(a.cull))
     r = kl.Renderer(p)

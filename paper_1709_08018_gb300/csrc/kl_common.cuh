@@ -42,7 +42,8 @@ constexpr int kMaxCullLevels = 8;
 constexpr uint32_t kDirect = 1u;     // P10 ~ 0: pole form invalid, use the direct map
 constexpr uint32_t kNearPar = 2u;    // |tr^2 - 4 det| small: near-parabolic (cusp) prefix
 constexpr uint32_t kWide = 4u;       // local FP32 frame unsafe (far or huge offsets)
-constexpr uint32_t kFallback = 8u;   // KL_MIXED: words of this prefix run in FP64
+constexpr uint32_t kFallback = 8u;   // KL_MIXED, KL_DF64: words of this prefix run in FP64
+constexpr uint32_t kDfRange = 16u;   // a pole-form constant outside the double-float range
 
 // FP64 fallback work unit: a chunk of this many suffix points.
 constexpr uint32_t kFbChunk = 64;
@@ -64,7 +65,8 @@ struct Plan {
   uint32_t cj0, clev, ndisks;
   uint32_t csz[kMaxCullLevels], cnb[kMaxCullLevels], cdisk[kMaxCullLevels];
   size_t off_pre64, off_pre32, off_flags, off_suf64, off_suf32, off_fb, off_fbcount;
-  size_t off_L, off_H, off_So, off_Si, off_disk32, off_disk64, off_nrm32, off_nrm64, total;
+  size_t off_L, off_H, off_So, off_Si, off_disk32, off_disk64, off_nrm32, off_nrm64;
+  size_t off_predf, off_sufdf, total;
 };
 
 struct View {
@@ -86,6 +88,13 @@ struct __align__(16) Pre32 {
   float gr, gi, axf, ayf, c1, c2, c3, c4;
   int axi, ayi;  // integer part of the pixel coordinates of alpha
   int kx, ky;    // 0x4B400000 - axi, 0x4B400000 - ayi (see mixed_item)
+};
+
+// Pole-form constants of one prefix as double-floats (KL_DF64): each FP64
+// constant d as hi = fl32(d), lo = fl32(d - hi), in the order gr, gi, ax,
+// ay, c1, c2, c3, c4 (ax, ay: pixel coordinates of alpha, no local frame).
+struct __align__(16) PreDF {
+  float h[8], l[8];
 };
 
 // Disk bounding one culling block of suffix points (FP64 points).
@@ -124,6 +133,9 @@ struct Tables {
   Disk64* disk64;  // the same for the FP64 points
   float* nrm32;    // per prefix slot: operator norm of the FP32 pole-form matrix
   double* nrm64;   // the same in FP64
+  PreDF* predf;    // KL_DF64: per prefix slot, the pole-form constants as double-floats
+  float4* sufdf;   // KL_DF64: per suffix point pair (a, b) two float4s:
+                   // (re_hi a, re_hi b, re_lo a, re_lo b), (im_hi a, im_hi b, im_lo a, im_lo b)
 };
 
 // Work items of the persistent render kernels: item = (q, prefix block pb,
@@ -425,13 +437,21 @@ __device__ void part_entry(const Group& G, const Plan& L, int renorm, uint32_t i
   }
 }
 
+// A double as a double-float: hi = fl32(d), lo = fl32(d - hi).
+__device__ __forceinline__ void split_df(double d, float& hi, float& lo) {
+  hi = __double2float_rn(d);
+  lo = __double2float_rn(d - (double)hi);
+}
+
 // Combine pass entry idx (the render's prefix slots first, 4 nr of them:
-// last letter x, slot r0 + k; then the suffix slots).  Fallback prefixes
-// (mixed mode) are appended to fb_list as (group << 32) | slot.
-__device__ void combine_entry(const View& V, const Plan& L, double ptol, int mixed,
+// last letter x, slot r0 + k; then the suffix slots).  prec: the kl_precision
+// of the render.  Fallback prefixes (KL_MIXED, KL_DF64) are appended to
+// fb_list as (group << 32) | slot.
+__device__ void combine_entry(const View& V, const Plan& L, double ptol, int prec,
                               uint32_t idx, const Tables& T, uint32_t group,
                               unsigned long long* __restrict__ fb_list,
                               uint32_t* __restrict__ fb_count) {
+  const bool mixed = prec == KL_MIXED, df = prec == KL_DF64;
   const uint32_t nP = 4u * L.nr;
   if (idx >= nP) {
     const uint32_t slot = idx - nP;
@@ -458,6 +478,19 @@ __device__ void combine_entry(const View& V, const Plan& L, double ptol, int mix
     if (j + 1u == L.ns && (L.ns & 1u)) {
       e[1] = __int_as_float(0x7FC00000);
       e[3] = __int_as_float(0x7FC00000);
+    }
+    if (df) {
+      // pair-interleaved double-float table, padded with NaN like the FP32 one
+      float* q = (float*)T.sufdf + 8ull * ((uint64_t)u * L.npairs + j / 2u);
+      float rh, rl, ih, il;
+      split_df(v.x, rh, rl);
+      split_df(v.y, ih, il);
+      q[j & 1u] = rh;
+      q[2 + (j & 1u)] = rl;
+      q[4 + (j & 1u)] = ih;
+      q[6 + (j & 1u)] = il;
+      if (j + 1u == L.ns && (L.ns & 1u))
+        for (int c = 1; c < 8; c += 2) q[c] = __int_as_float(0x7FC00000);
     }
     return;
   }
@@ -508,7 +541,20 @@ __device__ void combine_entry(const View& V, const Plan& L, double ptol, int mix
     c32.kx = 0x4B400000 - (int)axi;
     c32.ky = 0x4B400000 - (int)ayi;
   }
-  if (mixed && (fl & (kDirect | kNearPar | kWide))) {
+  if (df) {
+    // the double-float constants; a constant (nonzero) outside [1e-30, 1e30]
+    // would leave the float range in the per-word products
+    PreDF cd;
+    const double cv[8] = {c64.gr, c64.gi, c64.ax, c64.ay, c64.c1, c64.c2, c64.c3, c64.c4};
+    for (int q = 0; q < 8; ++q) {
+      split_df(cv[q], cd.h[q], cd.l[q]);
+      const double a = fabs(cv[q]);
+      if (!(a < 1e30) || (a != 0.0 && a < 1e-30)) fl |= kDfRange;
+    }
+    if (!(fl & kDirect)) T.predf[slot] = cd;
+  }
+  if ((mixed && (fl & (kDirect | kNearPar | kWide))) ||
+      (df && (fl & (kDirect | kWide | kDfRange)))) {
     fl |= kFallback;
     const uint32_t k = atomicAdd(fb_count, 1u);
     fb_list[k] = ((unsigned long long)group << 32) | slot;
@@ -854,6 +900,185 @@ __device__ __forceinline__ void mixed_item(uint32_t item, const Work& Wk, const 
   mixed_slot_words<BBOX>(slot, u, k0, k1, L, V, T, t, words, img, B);
 }
 
+
+// ---------------------------------------------------------------------------
+// double-float per-word map (KL_DF64), two words per packed f32x2 instruction
+//
+// A value is an unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2
+// (Dekker 1971; the "double-double" arithmetic of Hida, Li and Bailey 2001,
+// here on floats): about 48 significant bits.  Sums use Knuth's two-sum and
+// Dekker's fast two-sum; products use the fused multiply-add for the exact
+// rounding error of hi * hi.  Every operation below is an FP32 add, multiply
+// or fused multiply-add, so the map runs on the FP32 pipe.
+
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+  f2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// both halves negated (their sign bits flipped; an integer operation)
+__device__ __forceinline__ f2 neg2(f2 a) { return a ^ 0x8000000080000000ull; }
+
+struct DD {
+  f2 hi, lo;
+};
+
+// s + e = a + b exactly (two-sum)
+__device__ __forceinline__ void two_sum2(f2 a, f2 b, f2& s, f2& e) {
+  s = add2(a, b);
+  const f2 bb = sub2(s, a);
+  e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+// s + e = a + b exactly when |a| >= |b| (fast two-sum)
+__device__ __forceinline__ void fast_two_sum2(f2 a, f2 b, f2& s, f2& e) {
+  s = add2(a, b);
+  e = sub2(b, sub2(s, a));
+}
+__device__ __forceinline__ DD dd_add(const DD& a, const DD& b) {
+  f2 s, e;
+  two_sum2(a.hi, b.hi, s, e);
+  e = add2(e, add2(a.lo, b.lo));
+  DD r;
+  fast_two_sum2(s, e, r.hi, r.lo);
+  return r;
+}
+__device__ __forceinline__ DD dd_mul(const DD& a, const DD& b) {
+  const f2 p = mul2(a.hi, b.hi);
+  f2 e = fma2(a.hi, b.hi, neg2(p));  // the rounding error of a.hi b.hi, exactly
+  e = fma2(a.hi, b.lo, e);
+  e = fma2(a.lo, b.hi, e);
+  DD r;
+  fast_two_sum2(p, e, r.hi, r.lo);
+  return r;
+}
+__device__ __forceinline__ DD dd_sqr(const DD& a) {
+  const f2 p = mul2(a.hi, a.hi);
+  f2 e = fma2(a.hi, a.hi, neg2(p));
+  e = fma2(add2(a.hi, a.hi), a.lo, e);
+  DD r;
+  fast_two_sum2(p, e, r.hi, r.lo);
+  return r;
+}
+// 1/m: the hardware seed y (about 2^-23) and one Newton step y + y (1 - m y),
+// with the residual 1 - m y formed from the exact product m.hi y: about 2^-46
+__device__ __forceinline__ DD dd_rcp(const DD& m) {
+  float ma, mb;
+  upk(m.hi, ma, mb);
+  const f2 y = pk(rcp32(ma), rcp32(mb));
+  const f2 one = 0x3F8000003F800000ull;
+  const f2 p = mul2(m.hi, y);
+  const f2 pe = fma2(m.hi, y, neg2(p));       // m.hi y = p + pe
+  const f2 res = sub2(sub2(sub2(one, p), pe), mul2(m.lo, y));
+  DD r;
+  fast_two_sum2(y, mul2(y, res), r.hi, r.lo);
+  return r;
+}
+
+// Pole-form constants of a prefix as double-floats, each in both halves.
+struct DfConst {
+  DD k[8];  // gr, gi, ax, ay, c1, c2, c3, c4
+};
+__device__ __forceinline__ DfConst df_const(const PreDF& c) {
+  DfConst K;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    K.k[q].hi = pk(c.h[q], c.h[q]);
+    K.k[q].lo = pk(c.l[q], c.l[q]);
+  }
+  return K;
+}
+
+// Pixel coordinates (u, v) of two words with suffix points (vr, vi):
+// u = ax + (c1 wr + c2 wi) / |w|^2, v = ay + (c3 wr + c4 wi) / |w|^2, w = v + gamma.
+__device__ __forceinline__ void uv_df2(const DfConst& K, const DD& vr, const DD& vi, DD& u,
+                                       DD& v) {
+  const DD wr = dd_add(vr, K.k[0]);
+  const DD wi = dd_add(vi, K.k[1]);
+  const DD r = dd_rcp(dd_add(dd_sqr(wr), dd_sqr(wi)));
+  const DD tx = dd_add(dd_mul(K.k[4], wr), dd_mul(K.k[5], wi));
+  const DD ty = dd_add(dd_mul(K.k[6], wr), dd_mul(K.k[7], wi));
+  u = dd_add(K.k[2], dd_mul(tx, r));
+  v = dd_add(K.k[3], dd_mul(ty, r));
+}
+
+// Pixel keys 0x4B400000 + floor(u) of two double-float coordinates: floor
+// of u.hi from its rounding toward minus infinity after adding 1.5 2^23, less
+// one where u.lo takes u below that integer (the sign of the exact fraction
+// u.hi - floor(u.hi) plus u.lo, which |u.lo| <= ulp(u.hi)/2 keeps exact).
+// As for the mixed path, any |u| >= 2^22, infinity or NaN gives a key whose
+// column or row falls outside the image.
+__device__ __forceinline__ void floor_keys(const DD& u, uint32_t& ka, uint32_t& kb) {
+  const f2 magic = 0x4B4000004B400000ull;
+  const f2 t = add2_rm(u.hi, magic);
+  const f2 sl = add2(sub2(u.hi, sub2(t, magic)), u.lo);
+  ka = (uint32_t)t - ((uint32_t)sl >> 31);
+  kb = (uint32_t)(t >> 32) - ((uint32_t)(sl >> 32) >> 31);
+}
+
+// One run of n words ending in the pixel of keys (cu, cv) (absolute pixel
+// keys: col = cu - 0x4B400000).
+__device__ __forceinline__ void flush_key(uint32_t cu, uint32_t cv, uint32_t n, const View& V,
+                                          Tally& t, uint32_t* __restrict__ img) {
+  const uint32_t col = cu - 0x4B400000u, row = cv - 0x4B400000u;
+  if (n && col < V.W && row < V.H) {
+    atomicAdd(img + row * V.W + col, n);
+    ++t.atomics;
+    t.in_window += n;
+  }
+}
+
+// Double-float words of prefix slot `slot` on suffix point pairs [k0, k1) of
+// first letter u, with the run-length splat of mixed_slot_words on pixel keys.
+__device__ __forceinline__ void df64_slot_words(uint32_t slot, int u, uint32_t k0, uint32_t k1,
+                                                const Plan& L, const View& V, const Tables& T,
+                                                Tally& t, uint32_t& words,
+                                                uint32_t* __restrict__ img) {
+  const DfConst K = df_const(T.predf[slot]);
+  const float4* src = T.sufdf + 2ull * (size_t)u * L.npairs;
+  t.flush(img);
+  t.cur = -1;
+  uint32_t cu = 0, cv = 0, run = 0;  // keys (0, 0): no in-window pixel
+  uint32_t e_run = k0;
+  for (uint32_t e = k0; e < k1; ++e) {
+    const float4 a = __ldg(src + 2 * e), b = __ldg(src + 2 * e + 1);
+    const DD vr = {pk(a.x, a.y), pk(a.z, a.w)}, vi = {pk(b.x, b.y), pk(b.z, b.w)};
+    DD U, Vv;
+    uv_df2(K, vr, vi, U, Vv);
+    uint32_t ua, ub, va, vb;
+    floor_keys(U, ua, ub);
+    floor_keys(Vv, va, vb);
+    if (!((ua == cu) & (ub == cu) & (va == cv) & (vb == cv))) {
+      const bool a_in = (ua == cu) & (va == cv);
+      const bool ab = (ua == ub) & (va == vb);
+      run += 2u * (e - e_run) + (a_in ? 1u : 0u);
+      e_run = e + 1;
+      flush_key(cu, cv, run, V, t, img);
+      if (!a_in && !ab) flush_key(ua, va, 1u, V, t, img);  // word a on its own
+      run = (!a_in && ab) ? 2u : 1u;
+      cu = ub;
+      cv = vb;
+    }
+  }
+  run += 2u * (k1 - e_run);
+  flush_key(cu, cv, run, V, t, img);
+  words += min(2u * k1, L.ns) - 2u * k0;
+}
+
+// One double-float item: this thread's prefix on one chunk of suffix pairs.
+template <int BT>
+__device__ __forceinline__ void df64_item(uint32_t item, const Work& Wk, const Plan& L,
+                                          const View& V, const Tables& T, Tally& t,
+                                          uint32_t& words, uint32_t* __restrict__ img) {
+  int x, u;
+  uint32_t pb, c;
+  item_of(item, Wk, x, u, pb, c);
+  const uint32_t k = pb * BT + (threadIdx.x % BT);
+  if (k >= L.nr) return;
+  const uint32_t slot = (uint32_t)x * L.np + L.r0 + k;
+  if (T.flags[slot] & kFallback) return;
+  const uint32_t k0 = c * Wk.chunk, k1 = min(L.npairs, k0 + Wk.chunk);
+  df64_slot_words(slot, u, k0, k1, L, V, T, t, words, img);
+}
 
 // ---------------------------------------------------------------------------
 // culled renders (kl_params.cull), shared by the single and batched renders
@@ -1433,6 +1658,10 @@ inline int make_plan(const kl_params* p, Plan* L, bool batched) {
   L->off_disk64 = off; off = align256(off + nD * sizeof(Disk64));
   L->off_nrm32 = off; off = align256(off + nN * sizeof(float));
   L->off_nrm64 = off; off = align256(off + nN * sizeof(double));
+  // double-float constants and suffix pairs exist in KL_DF64 plans only
+  const bool df = p->precision == KL_DF64;
+  L->off_predf = off; off = align256(off + (df ? nP : 0) * sizeof(PreDF));
+  L->off_sufdf = off; off = align256(off + (df ? 8ull * L->npairs : 0) * sizeof(float4));
   L->total = off;
   return KL_OK;
 }
@@ -1470,7 +1699,8 @@ inline Tables carve(const Plan& L, void* ws) {
           (M2*)(b + L.off_H),                  (PartM*)(b + L.off_So),
           (double2*)(b + L.off_Si),            (float4*)(b + L.off_disk32),
           (Disk64*)(b + L.off_disk64),         (float*)(b + L.off_nrm32),
-          (double*)(b + L.off_nrm64)};
+          (double*)(b + L.off_nrm64),          (PreDF*)(b + L.off_predf),
+          (float4*)(b + L.off_sufdf)};
 }
 
 inline int sm_count() {

@@ -38,13 +38,13 @@ __global__ void parts_kernel(Group G, Plan L, int renorm, Tables T, Clear C,
               (size_t)(gridDim.x - part_blocks) * blockDim.x);
 }
 
-__global__ void combine_kernel(View V, Plan L, double ptol, int mixed, Tables T) {
+__global__ void combine_kernel(View V, Plan L, double ptol, int prec, Tables T) {
   pdl_trigger();
   pdl_wait();
   const uint32_t total = combine_count(L);
   for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += gridDim.x * blockDim.x)
-    combine_entry(V, L, ptol, mixed, idx, T, 0u, T.fb, T.fbcount);
+    combine_entry(V, L, ptol, prec, idx, T, 0u, T.fb, T.fbcount);
 }
 
 // ---------------------------------------------------------------------------
@@ -105,6 +105,45 @@ __global__ void __launch_bounds__(BT, 1280 / BT) render_mixed_kernel(
       continue;
     }
     mixed_item<32>(item - n64, Wk, L, V, T, t, words, img);
+  }
+  publish_counts(t.in_window, words, fp64_words, t.atomics, counters);
+}
+
+// Double-float (KL_DF64): the queue holds first the FP64 fallback items (the
+// direct-form, far and out-of-float-range prefixes), then the double-float
+// items (32 prefixes x one chunk of suffix pairs), drawn per warp like the
+// mixed render's.  The per-word map is about 150 FP32 operations, so the FMA
+// pipe, not issue, bounds the loop.
+template <int BT>
+__global__ void __launch_bounds__(BT, 512 / BT) render_df64_kernel(
+    Tables T, Plan L, View V, Work Wk, uint32_t* __restrict__ img,
+    unsigned long long* counters) {
+  pdl_wait();
+  const uint32_t chunks = (L.ns + kFbChunk - 1) / kFbChunk;
+  const uint32_t fb_units = 3u * chunks * (*T.fbcount);
+  const uint32_t n64 = (fb_units + 31) / 32;
+  const uint32_t total = n64 + Wk.n_items;
+  const uint32_t lane = threadIdx.x & 31;
+  Tally t;
+  uint32_t words = 0, fp64_words = 0;
+  for (;;) {
+    const uint32_t item = next_item_warp(T.fbcount + 1);
+    if (item >= total) break;
+    if (item < n64) {
+      const uint32_t unit = item * 32 + lane;
+      if (unit < fb_units) {
+        const uint32_t e = unit / (3u * chunks), rem = unit % (3u * chunks);
+        const uint32_t slot = (uint32_t)(T.fb[e] & 0xFFFFFFFFull);
+        const UnitTally r = fallback_unit(T.pre64, T.flags, T.suf64, slot, rem / chunks,
+                                          rem % chunks, L.np, L.ns, V, img);
+        words += r.words;
+        fp64_words += r.words;
+        t.in_window += r.in_window;
+        t.atomics += r.atomics;
+      }
+      continue;
+    }
+    df64_item<32>(item - n64, Wk, L, V, T, t, words, img);
   }
   publish_counts(t.in_window, words, fp64_words, t.atomics, counters);
 }
@@ -189,7 +228,7 @@ __global__ void render_single_letter_kernel(Group G, View V, uint32_t* img,
 // per length, whose launches would cost more than its words.
 constexpr uint32_t kShortTiling = 9;
 
-__global__ void tiling_short_kernel(Group G, View V, uint32_t k0, int mixed,
+__global__ void tiling_short_kernel(Group G, View V, uint32_t k0, int fp64_count,
                                     uint32_t* __restrict__ img, unsigned long long* counters) {
   uint64_t total = 0, nk = 4;
   for (uint32_t k = 1; k <= k0; ++k, nk *= 3) total += nk;
@@ -221,11 +260,12 @@ __global__ void tiling_short_kernel(Group G, View V, uint32_t k0, int mixed,
       ++atomics;
     }
   }
-  publish_counts(in_window, words, mixed ? words : 0u, atomics, counters);
+  publish_counts(in_window, words, fp64_count ? words : 0u, atomics, counters);
 }
 
 __global__ void eval_kernel(const uint64_t* __restrict__ idx, uint64_t n, uint64_t N, Group G,
-                            Plan L, View V, int mixed, Tables T, double* __restrict__ out) {
+                            Plan L, View V, int prec, Tables T, double* __restrict__ out) {
+  const bool mixed = prec == KL_MIXED, df = prec == KL_DF64;
   for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n;
        t += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t i = idx[t];
@@ -255,6 +295,20 @@ __global__ void eval_kernel(const uint64_t* __restrict__ idx, uint64_t n, uint64
           uv_pole32(c, (jj & 1u) ? e.y : e.x, (jj & 1u) ? e.w : e.z, uf, vf);
           uu = (double)c.axi + (double)uf;
           vv = (double)c.ayi + (double)vf;
+        } else if (df && !(fl & kFallback)) {
+          // the render's pair arithmetic, with this word in both halves
+          const DfConst K = df_const(T.predf[slot]);
+          const float4* q = T.sufdf + 2ull * ((uint64_t)w[L.p] * L.npairs + jj / 2u);
+          const float4 a = q[0], b = q[1];
+          const bool odd = jj & 1u;
+          const float rh = odd ? a.y : a.x, rl = odd ? a.w : a.z;
+          const float ih = odd ? b.y : b.x, il = odd ? b.w : b.z;
+          const DD vr = {pk(rh, rh), pk(rl, rl)}, vi = {pk(ih, ih), pk(il, il)};
+          DD U, Vv;
+          uv_df2(K, vr, vi, U, Vv);
+          uu = (double)__uint_as_float((uint32_t)U.hi) + (double)__uint_as_float((uint32_t)U.lo);
+          vv = (double)__uint_as_float((uint32_t)Vv.hi) +
+               (double)__uint_as_float((uint32_t)Vv.lo);
         } else if (fl & kDirect) {
           const double2 s = T.suf64[sslot];
           uv_direct64(T.pre64[slot], s.x, s.y, V, uu, vv);
@@ -289,7 +343,7 @@ int prof_mark(cudaEvent_t e, cudaStream_t s) {
 // then combine, launched as a programmatic dependent of parts.
 int build_tables(const kl_params* p, const Plan& L, const View& V, const Group& G,
                  const Tables& T, cudaStream_t st, const Clear& C = Clear{}) {
-  const int mixed = p->precision == KL_MIXED;
+  const int prec = (int)p->precision;
   const uint32_t nParts = parts_count(L);
   const uint32_t part_blocks = (nParts + kPartLanes - 1) / kPartLanes;
   uint32_t clear_blocks = 0;
@@ -304,7 +358,7 @@ int build_tables(const kl_params* p, const Plan& L, const View& V, const Group& 
   if (check_launch() != KL_OK) return KL_ECUDA;
   const uint32_t n = combine_count(L);
   return launch_dependent(combine_kernel, dim3((n + 127) / 128), dim3(128), st, V, L,
-                          p->parabolic_tol, mixed, T);
+                          p->parabolic_tol, prec, T);
 }
 
 // Length k of a tiling render of *p: a limit-set render of the words of
@@ -336,9 +390,10 @@ size_t plan_bytes(const kl_params* p) {
 
 int validate(const kl_params* p, size_t ws_bytes, void* ws, Plan* L) {
   if (!p || !valid_view(p)) return KL_EINVAL;
-  if (p->precision != KL_FP64 && p->precision != KL_MIXED) return KL_EINVAL;
+  if (p->precision != KL_FP64 && p->precision != KL_MIXED && p->precision != KL_DF64)
+    return KL_EINVAL;
   if (p->mode != KL_LIMIT_SET && p->mode != KL_TILING) return KL_EINVAL;
-  if (p->cull > 1) return KL_EINVAL;
+  if (p->cull > 1 || (p->cull && p->precision == KL_DF64)) return KL_EINVAL;
   if (p->shard_count > 1 && (p->mode != KL_LIMIT_SET || p->shard_index >= p->shard_count))
     return KL_EINVAL;
   if (!(p->parabolic_tol >= 0.0)) return KL_EINVAL;
@@ -376,6 +431,16 @@ int launch_render(const kl_params* p, const Plan& L, const View& V, const Tables
                          : launch_dependent(cull_kernel<BT, false>, dim3(sms * occ), dim3(BT),
                                             s, T, L, V, Wk, img, cnt);
     if (st != KL_OK) return KL_ECUDA;
+    return prof_mark(ev1, s);
+  }
+  if (p->precision == KL_DF64) {
+    if (device_slots((const void*)render_df64_kernel<BT>, BT, &sms, &occ) != KL_OK)
+      return KL_ECUDA;
+    const Work Wk = make_work(L, 32, L.npairs, sms * occ * (BT / 32), p->chunk_pairs);
+    if (prof_mark(ev0, s) != KL_OK) return KL_ECUDA;
+    if (launch_dependent(render_df64_kernel<BT>, dim3(sms * occ), dim3(BT), s, T, L, V, Wk,
+                         img, cnt) != KL_OK)
+      return KL_ECUDA;
     return prof_mark(ev1, s);
   }
   if (p->precision == KL_FP64) {
@@ -450,7 +515,7 @@ extern "C" int kl_eval_words(const kl_params* p_in, const uint64_t* d_index, uin
   const uint64_t blocks = (n + 127) / 128;
   const unsigned g = (unsigned)(blocks < (uint64_t)sms * 16 ? blocks : (uint64_t)sms * 16);
   eval_kernel<<<g, 128, 0, s>>>(d_index, n, kl_word_count(p->depth), G, L, V,
-                                p->precision == KL_MIXED, T, d_uv);
+                                (int)p->precision, T, d_uv);
   return check_launch();
 }
 
@@ -519,7 +584,7 @@ extern "C" int kl_render(const kl_params* p, uint32_t* d_image, uint64_t* d_coun
     const int sms = sm_count();
     if (sms <= 0) return KL_ECUDA;
     tiling_short_kernel<<<sms * 4, 256, 0, s>>>(make_group(p), make_view(p), k0,
-                                                p->precision == KL_MIXED, d_image, cnt);
+                                                p->precision != KL_FP64, d_image, cnt);
     return check_launch();
   }
   return render_length(p, d_image, cnt, d_workspace, s, true);
