@@ -153,9 +153,14 @@ def run_lod(a, kl, klsynth, torch):
     """Train the pruning network on --train-groups groups (--per-level nodes
     per level, --train-steps steps; bench.py's setting is 64, 60000, 10000)
     and run the pruned render (margin -0.8, edge 1/512 px) of the first
-    --held-out held-out groups, --repeat times each."""
+    --held-out held-out groups, --repeat times each, at depth --depth (22) and
+    --size (8192) pixels."""
     from paper_1709_08018_gb300 import lod
-    d, size, lo, hi, extent = 22, 8192, 8, 15, 1.0 / 32
+    # bench.py's setting by default; --depth and --size give a smaller case
+    # (levels lo..hi follow the depth: hi = d - 7, lo = hi - 7)
+    d, size, extent = a.depth or 22, a.size or 8192, 1.0 / 32
+    hi = min(15, d - 7)
+    lo = max(1, hi - 7)
     W = (-2.0, 2.0, -2.0, 2.0)
     mk = lambda g: kl.params_init(g.ta, g.tb, d, size, size, W, kl.MIXED)
     tr = [mk(g) for g, _ in klsynth.draw_groups(klsynth.LOD_TRAIN_SEED, a.train_groups)]

@@ -21,7 +21,8 @@
 //   [dH1^T; dH2^T] [X | 1]    -> dW1^T (rows 0..63, columns 0..7), db1 (rows
 //                                0..63, column 8) and db2 (rows 64..127,
 //                                column 8).
-// The transposed operands are written column-wise by the row-owning threads.
+// The transposed operands are stored MN-major, so that a row-owning thread
+// writes 8 of its values with one 16-byte store.
 #include "kl_mlp_dev.cuh"
 #include "kl_tc.cuh"
 
@@ -30,15 +31,16 @@ namespace {
 constexpr int kTile = 128;                        // rows per tile = TMEM lanes = threads
 constexpr long long kWaitCycles = 2000000000ll;   // bound on an MMA wait (about a second)
 
-// Shared memory (bytes from a 1024-aligned base).  K-major BF16 tiles
-// (kl_tc.cuh); LBO = 16 x rows for tiles written row by row, plus 16 bytes
-// for tiles written column-wise (thread = K index), so that the four K
-// chunks a warp's 32 threads write fall in different banks.
+// Shared memory (bytes from a 1024-aligned base).  BF16 tiles (kl_tc.cuh):
+// K-major where the threads own the rows of the tile (the layer inputs) or
+// where the tile is staged once (the weights), MN-major where a thread owns
+// one K index (the row of the batch) of the gradient products' operands.
+// LBO = 16 x (rows, or MN extent) in both cases.
 constexpr uint32_t kLboW = 64 * 16;           // weight tiles, 64 rows
 constexpr uint32_t kLboRow = kTile * 16;      // X, H1, dH2: 128 rows, row-wise
-constexpr uint32_t kLboA = kTile * 16 + 16;   // [H1^T; H2^T], [dH1^T; dH2^T]: 128 rows
-constexpr uint32_t kLboB1 = 80 * 16 + 16;     // [dH2 | dy | 0]^T: 80 rows
-constexpr uint32_t kLboB2 = 16 * 16 + 16;     // [X | 1 | 0]^T: 16 rows
+constexpr uint32_t kLboA = kTile * 16;        // [H1^T; H2^T], [dH1^T; dH2^T]: M = 128, MN-major
+constexpr uint32_t kLboB1 = 80 * 16;          // [dH2 | dy | 0]: N = 80, MN-major
+constexpr uint32_t kLboB2 = 16 * 16;          // [X | 1 | 0]: N = 16, MN-major
 
 // training kernel
 constexpr uint32_t SM_W1 = 0;                      // B of layer 1: [h][f], f < 16
@@ -72,23 +74,49 @@ static_assert(kGradSmem <= 227 * 1024, "training shared memory");
 // TMEM columns: layer outputs and dH1 (64 each), the two gradient accumulators.
 constexpr uint32_t TD1 = 0, TD2 = 64, TWA = 128, TWB = 224;
 
-__device__ __forceinline__ void st_bf16(unsigned char* p, float v) {
-  *reinterpret_cast<__nv_bfloat16*>(p) = __float2bfloat16_rn(v);
+
+// Eight values as one 16-byte chunk of BF16.
+__device__ __forceinline__ uint4 pack8(const float* v) {
+  return make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                    pack_bf16(v[6], v[7]));
 }
 
-// Weights as BF16 B operands, biases and w3 in FP32.
+// MN elements m .. m+7 (m a multiple of 8) of K index t of an MN-major tile.
+__device__ __forceinline__ void st_mn8(unsigned char* base, uint32_t lbo, int m, int t,
+                                       const float* v) {
+  *reinterpret_cast<uint4*>(base + tc_off_mn(m, t, lbo)) = pack8(v);
+}
+
+// Weights as BF16 B operands (K-major, 16-byte chunks of 8 K elements: one
+// store per chunk), biases and w3 in FP32.
 __device__ void stage_weights(unsigned char* sm, uint32_t w1, uint32_t w2, int w2t,
                               uint32_t par, const float* __restrict__ P) {
-  for (int i = threadIdx.x; i < kHid * 16; i += blockDim.x) {
-    const int h = i / 16, f = i % 16;
-    st_bf16(sm + w1 + tc_off(h, f, kLboW), f < kIn ? P[OFF_W1 + f * kHid + h] : 0.0f);
+  // W1 as B of layer 1: (n = h, k = f), f = 0..15 with zeros from 8 on
+  for (int i = threadIdx.x; i < kHid * 2; i += blockDim.x) {
+    const int h = i % kHid, kc = i / kHid;
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = kc == 0 ? P[OFF_W1 + j * kHid + h] : 0.0f;
+    *reinterpret_cast<uint4*>(sm + w1 + tc_off(h, 8 * kc, kLboW)) = pack8(v);
   }
-  for (int i = threadIdx.x; i < kHid * kHid; i += blockDim.x) {
-    const int in = i / kHid, out = i % kHid;
-    const float w = P[OFF_W2 + i];
-    st_bf16(sm + w2 + tc_off(out, in, kLboW), w);
-    if (w2t >= 0) st_bf16(sm + (uint32_t)w2t + tc_off(in, out, kLboW), w);
+  // W2 as B of layer 2: (n = out, k = in), 8 inputs per chunk (a column of W2,
+  // read with consecutive threads on consecutive outputs)
+  for (int i = threadIdx.x; i < kHid * 8; i += blockDim.x) {
+    const int out = i % kHid, kc = i / kHid;
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = P[OFF_W2 + (8 * kc + j) * kHid + out];
+    *reinterpret_cast<uint4*>(sm + w2 + tc_off(out, 8 * kc, kLboW)) = pack8(v);
   }
+  // W2 as B of dH1 = dH2 W2^T: (n = in, k = out), 8 outputs per chunk (part of a row)
+  if (w2t >= 0)
+    for (int i = threadIdx.x; i < kHid * 8; i += blockDim.x) {
+      const int in = i / 8, kc = i % 8;
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = P[OFF_W2 + in * kHid + 8 * kc + j];
+      *reinterpret_cast<uint4*>(sm + (uint32_t)w2t + tc_off(in, 8 * kc, kLboW)) = pack8(v);
+    }
   float* q = reinterpret_cast<float*>(sm + par);
   for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
     q[i] = P[OFF_B1 + i];
@@ -240,17 +268,16 @@ __global__ void __launch_bounds__(kTile, 1) mlp_grad_kernel(
   uint32_t* slot = reinterpret_cast<uint32_t*>(sm + SM_BAR + 8);
   stage_weights(sm, SM_W1, SM_W2, (int)SM_W2T, SM_PAR, P);
   const float b3 = P[OFF_B3];
-  // constant parts of the operand tiles: X padding, the zero rows of B1 and B2
+  // constant parts of the operand tiles: X padding, the zero columns 72..79 of B1
   *reinterpret_cast<uint4*>(sm + SM_X + tc_off(t, 8, kLboRow)) = make_uint4(0u, 0u, 0u, 0u);
-  for (int r = kHid + 1; r < 80; ++r) st_bf16(sm + SM_B1 + tc_off(r, t, kLboB1), 0.0f);
-  for (int r = kIn + 1; r < 16; ++r) st_bf16(sm + SM_B2 + tc_off(r, t, kLboB2), 0.0f);
+  *reinterpret_cast<uint4*>(sm + SM_B1 + tc_off_mn(72, t, kLboB1)) = make_uint4(0u, 0u, 0u, 0u);
   if (t == 0) mbar_init(bar, 1);
   if (warp == 0) tc_alloc(slot, 256);
   sync_for_mma();
   const uint32_t tm = *slot;
   const uint32_t la = tm + ((uint32_t)(warp * 32) << 16);
-  const uint32_t id64 = tc_idesc_bf16(128, 64), id80 = tc_idesc_bf16(128, 80),
-                 id16 = tc_idesc_bf16(128, 16);
+  const uint32_t id64 = tc_idesc_bf16(128, 64), id80 = tc_idesc_bf16(128, 80, 1, 1),
+                 id16 = tc_idesc_bf16(128, 16, 1, 1);
   const uint32_t aX = smem_u32(sm + SM_X), aH1 = smem_u32(sm + SM_H1),
                  aDH2 = smem_u32(sm + SM_DH2), aA1 = smem_u32(sm + SM_A1),
                  aA2 = smem_u32(sm + SM_A2), aB1 = smem_u32(sm + SM_B1),
@@ -276,9 +303,11 @@ __global__ void __launch_bounds__(kTile, 1) mlp_grad_kernel(
     *reinterpret_cast<uint4*>(sm + SM_X + tc_off(t, 0, kLboRow)) =
         make_uint4(pack_bf16(xv[0], xv[1]), pack_bf16(xv[2], xv[3]), pack_bf16(xv[4], xv[5]),
                    pack_bf16(xv[6], xv[7]));
-#pragma unroll
-    for (int f = 0; f < kIn; ++f) st_bf16(sm + SM_B2 + tc_off(f, t, kLboB2), xv[f]);
-    st_bf16(sm + SM_B2 + tc_off(kIn, t, kLboB2), valid ? 1.0f : 0.0f);
+    st_mn8(sm + SM_B2, kLboB2, 0, t, xv);
+    {
+      const float one[8] = {valid ? 1.0f : 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+      st_mn8(sm + SM_B2, kLboB2, kIn, t, one);
+    }
     // layer 1: H1 = relu(X W1 + b1)
     sync_for_mma();
     if (t == 0) {
@@ -297,8 +326,9 @@ __global__ void __launch_bounds__(kTile, 1) mlp_grad_kernel(
         const float a = v[j] + b1[c + j];
         m1 |= (uint64_t)(a > 0.0f) << (c + j);
         v[j] = fmaxf(a, 0.0f);
-        st_bf16(sm + SM_A1 + tc_off(c + j, t, kLboA), v[j]);
       }
+      st_mn8(sm + SM_A1, kLboA, c, t, v);
+      st_mn8(sm + SM_A1, kLboA, c + 8, t, v + 8);
       st_row16(sm + SM_H1, t, c, v);
     }
     // layer 2: H2 = relu(H1 W2 + b2), y = H2 . w3 + b3
@@ -322,10 +352,11 @@ __global__ void __launch_bounds__(kTile, 1) mlp_grad_kernel(
       for (int j = 0; j < 16; ++j) {
         const float a = v[j] + b2[c + j];
         m2 |= (uint64_t)(a > 0.0f) << (c + j);
-        const float h = fmaxf(a, 0.0f);
-        yv += h * w3[c + j];
-        st_bf16(sm + SM_A1 + tc_off(kHid + c + j, t, kLboA), h);
+        v[j] = fmaxf(a, 0.0f);
+        yv += v[j] * w3[c + j];
       }
+      st_mn8(sm + SM_A1, kLboA, kHid + c, t, v);
+      st_mn8(sm + SM_A1, kLboA, kHid + c + 8, t, v + 8);
     }
     yv += b3;
     // weighted squared error: weight `under` where the output is below the target
@@ -339,14 +370,17 @@ __global__ void __launch_bounds__(kTile, 1) mlp_grad_kernel(
     for (int c = 0; c < kHid; c += 16) {
       float v[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        v[j] = ((m2 >> (c + j)) & 1ull) ? dy * w3[c + j] : 0.0f;
-        st_bf16(sm + SM_B1 + tc_off(c + j, t, kLboB1), v[j]);
-        st_bf16(sm + SM_A2 + tc_off(kHid + c + j, t, kLboA), v[j]);
-      }
+      for (int j = 0; j < 16; ++j) v[j] = ((m2 >> (c + j)) & 1ull) ? dy * w3[c + j] : 0.0f;
+      st_mn8(sm + SM_B1, kLboB1, c, t, v);
+      st_mn8(sm + SM_B1, kLboB1, c + 8, t, v + 8);
+      st_mn8(sm + SM_A2, kLboA, kHid + c, t, v);
+      st_mn8(sm + SM_A2, kLboA, kHid + c + 8, t, v + 8);
       st_row16(sm + SM_DH2, t, c, v);
     }
-    st_bf16(sm + SM_B1 + tc_off(kHid, t, kLboB1), dy);
+    {
+      const float dyv[8] = {dy, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+      st_mn8(sm + SM_B1, kLboB1, kHid, t, dyv);
+    }
     // dH1 = dH2 W2^T through the first ReLU
     sync_for_mma();
     if (t == 0) {
@@ -363,8 +397,9 @@ __global__ void __launch_bounds__(kTile, 1) mlp_grad_kernel(
       float v[16];
       tc_ld16(la + TD1 + c, v);
 #pragma unroll
-      for (int j = 0; j < 16; ++j)
-        st_bf16(sm + SM_A2 + tc_off(c + j, t, kLboA), ((m1 >> (c + j)) & 1ull) ? v[j] : 0.0f);
+      for (int j = 0; j < 16; ++j) v[j] = ((m1 >> (c + j)) & 1ull) ? v[j] : 0.0f;
+      st_mn8(sm + SM_A2, kLboA, c, t, v);
+      st_mn8(sm + SM_A2, kLboA, c + 8, t, v + 8);
     }
     // the sums over this tile's rows, added to the CTA's accumulators
     sync_for_mma();

@@ -22,6 +22,16 @@ __host__ __device__ constexpr uint32_t tc_off(uint32_t r, uint32_t k, uint32_t l
   return (r / 8) * kTcSBO + (k / 8) * lbo + (r % 8) * 16 + (k % 8) * 2;
 }
 
+// The same tile stored MN-major: the 8 MN elements of a core matrix row are
+// contiguous (16 bytes) and its 8 K values lie 16 bytes apart.  Element
+// (r, k) at (r / 8) * SBO + (k / 8) * LBO + (k % 8) * 16 + (r % 8) * 2; the
+// descriptor takes LBO and SBO in the same roles, and the instruction
+// descriptor marks the operand MN-major.  A thread owning one K index (a
+// row of the batch) writes 8 consecutive MN elements with one 16-byte store.
+__host__ __device__ constexpr uint32_t tc_off_mn(uint32_t r, uint32_t k, uint32_t lbo) {
+  return (r / 8) * kTcSBO + (k / 8) * lbo + (k % 8) * 16 + (r % 8) * 2;
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -34,10 +44,12 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo) {
 }
 
 // Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
-// A and B (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 in
-// bits 17-22, M / 16 in bits 24-28.
-__host__ __device__ constexpr uint32_t tc_idesc_bf16(uint32_t M, uint32_t N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+// A and B (bits 7-9 and 10-12 = 1), A and B K-major (bits 15, 16 = 0) or
+// MN-major (= 1), N / 8 in bits 17-22, M / 16 in bits 24-28.
+__host__ __device__ constexpr uint32_t tc_idesc_bf16(uint32_t M, uint32_t N, uint32_t a_mn = 0,
+                                                     uint32_t b_mn = 0) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (a_mn << 15) | (b_mn << 16) | ((N >> 3) << 17) |
+         ((M >> 4) << 24);
 }
 
 // TMEM columns [0, ncols) for this CTA (one full warp calls it); the address
