@@ -40,9 +40,10 @@ FP32_OPS_PER_WORD = 12    # FP32 operations of the mixed per-word map: w = v + g
                           # |w|^2 (2), M w (4), M w / |w|^2 + alpha (2), the two floors (2)
 FP64_OPS_PER_WORD = 13    # FP64 operations of the plain per-word map: w = v + gamma (2),
                           # |w|^2 (2), reciprocal refinement (3), M w (4), final FMAs (2)
-DF64_OPS_PER_WORD = 151   # FP32 operations of the double-float per-word map: 6 double-float
-                          # sums (11 each), 2 squares and 6 products (7 each), the reciprocal's
-                          # Newton step (10), and the two pixel keys (4 each)
+DF64_OPS_PER_WORD = 127   # FP32 operations of the double-float per-word map: w = v + gamma
+                          # (2 double-float sums, 11 each), |w|^2 (19), the reciprocal's Newton
+                          # step (10), the two numerators (dot products, 19 each), a + b c for
+                          # the two coordinates (15 each), and the two pixel keys (4 each)
 SMS = 152
 FP32_LANES_PER_SM = 128
 FP64_LANES_PER_SM = 2
@@ -439,14 +440,15 @@ def maskit_config(kl, dev, flush):
                        "window [-1,1]x[-0.08,1.92], 4096^2",
            "nodes": nodes, "strings_scanned": sum(4 ** k for k in range(1, d + 1)),
            "paper_scan_fp64_ms": scan_ms}
-    for name, prec in (("fp64", kl.FP64), ("mixed", kl.MIXED)):
+    for name, prec in (("fp64", kl.FP64), ("df64", kl.DF64), ("mixed", kl.MIXED)):
         p = kl.params_group(gens, seeds8, d, W, W, window, prec, mode=kl.TILING)
         r = kl.Renderer(p, device=dev)
         out[f"indexed_{name}_ms"] = timed(lambda: r())
-        if name == "fp64":
+        if name in ("fp64", "df64"):
             diff = int((r.image.to(torch.int64) - scan_img.to(torch.int64)).abs().sum().item())
-            out["fp64_images_differ_in_hits"] = diff
+            out[f"{name}_images_differ_in_hits"] = diff
     out["speedup_indexed_fp64_over_scan"] = scan_ms / out["indexed_fp64_ms"]
+    out["speedup_indexed_df64_over_scan"] = scan_ms / out["indexed_df64_ms"]
     out["speedup_indexed_mixed_over_scan"] = scan_ms / out["indexed_mixed_ms"]
     return out
 
@@ -478,7 +480,7 @@ def multiseed_config(kl, dev, flush):
 
     out = {"workload": "gasket ta=tb=2, length 18, 8 seed points, 4096^2, window [-1.5,1.5]^2",
            "points": 8, "words_per_render": c.n_words, "words_per_call": 8 * c.n_words}
-    for name, prec in (("fp64", kl.FP64), ("mixed", kl.MIXED)):
+    for name, prec in (("fp64", kl.FP64), ("df64", kl.DF64), ("mixed", kl.MIXED)):
         p = kl.params_init(c.group.ta, c.group.tb, c.depth, W, W, c.window, prec)
         s16 = kl.cusp_seeds(list(p.gens))
         pts = [complex(s16[2 * i], s16[2 * i + 1]) for i in range(8)]
