@@ -344,6 +344,17 @@ KL_API int kl_mlp_grad(const float* d_params, const float* d_x, const float* d_t
 KL_API int kl_mlp_adam(float* d_params, float* d_m, float* d_v, float* d_grad, uint32_t step,
                        float lr, float beta1, float beta2, float eps, void* stream);
 
+/* One training step: the gradient of kl_mlp_grad, then, in the same pass that
+ * sums the partials (in the same fixed order), the Adam step of kl_mlp_adam
+ * applied to d_params, d_m and d_v.  The parameters that result are bit for bit
+ * those of kl_mlp_grad followed by kl_mlp_adam, one launch fewer.  d_loss: the
+ * loss before the step; d_grad: receives the gradient if not null.  d_scratch
+ * as for kl_mlp_grad. */
+KL_API int kl_mlp_train_step(float* d_params, float* d_m, float* d_v, const float* d_x,
+                             const float* d_t, uint64_t n, float under_weight, uint32_t step,
+                             float lr, float beta1, float beta2, float eps, float* d_loss,
+                             float* d_grad, void* d_scratch, size_t scratch_bytes, void* stream);
+
 /* Level-of-detail labels and pruned render.
  *
  * Tree levels: a node at level k is a reduced prefix w_1 .. w_k (the letters

@@ -19,7 +19,7 @@ API = ("kl_status_string", "kl_word_count", "kl_grandma", "kl_seeds", "kl_maskit
        "kl_decode_words", "kl_workspace_bytes", "kl_eval_words", "kl_render",
        "kl_batch_create", "kl_batch_workspace_bytes", "kl_batch_render", "kl_batch_capture",
        "kl_batch_replay", "kl_batch_destroy", "kl_mlp_forward", "kl_mlp_scratch_bytes",
-       "kl_mlp_grad", "kl_mlp_adam", "kl_lod_node_count", "kl_lod_label_bytes", "kl_lod_labels",
+       "kl_mlp_grad", "kl_mlp_adam", "kl_mlp_train_step", "kl_lod_node_count", "kl_lod_label_bytes", "kl_lod_labels",
        "kl_lod_render_bytes", "kl_render_lod", "kl_render_lod_labels", "kl_fsa_count",
        "kl_render_fsa", "kl_render_noalloc", "kl_set_profile_events")
 KL_MLP_NPARAMS = 4801
@@ -183,6 +183,10 @@ def lib():
         L.kl_mlp_adam.argtypes = [P, P, P, P, U32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                   ctypes.c_float, P]
         L.kl_mlp_adam.restype = I
+        L.kl_mlp_train_step.argtypes = [P, P, P, P, P, U64, ctypes.c_float, U32, ctypes.c_float,
+                                        ctypes.c_float, ctypes.c_float, ctypes.c_float, P, P, P,
+                                        SZ, P]
+        L.kl_mlp_train_step.restype = I
         L.kl_lod_node_count.argtypes = [U32, U32]
         L.kl_lod_node_count.restype = U64
         L.kl_lod_label_bytes.argtypes = [ctypes.POINTER(Params), U32, U32]
@@ -496,6 +500,24 @@ class MlpTrainer:
         return self.grad, self.loss
 
     def step(self, x, t, stream=None):
+        """One Adam step on rows x, targets t (kl_mlp_train_step: gradient,
+        fixed-order sum and Adam update); returns the loss before the step."""
+        torch = _torch()
+        n = x.shape[0]
+        need = int(lib().kl_mlp_scratch_bytes(n))
+        if self.scratch is None or self.scratch.numel() < need:
+            self.scratch = torch.empty(need, dtype=torch.uint8, device=x.device)
+        self.step_no += 1
+        _check(lib().kl_mlp_train_step(self.params.data_ptr(), self.m.data_ptr(),
+                                       self.v.data_ptr(), x.data_ptr(), t.data_ptr(), n,
+                                       self.under_weight, self.step_no, self.lr, self.b1, self.b2,
+                                       self.eps, self.loss.data_ptr(), self.grad.data_ptr(),
+                                       self.scratch.data_ptr(), self.scratch.numel(),
+                                       _stream_handle(stream)), "kl_mlp_train_step")
+        return self.loss
+
+    def step_separate(self, x, t, stream=None):
+        """The same step as two calls, kl_mlp_grad then kl_mlp_adam."""
         self.gradient(x, t, stream)
         self.step_no += 1
         _check(lib().kl_mlp_adam(self.params.data_ptr(), self.m.data_ptr(), self.v.data_ptr(),

@@ -467,13 +467,29 @@ __global__ void __launch_bounds__(kTile, 1) mlp_grad_kernel(
   if (warp == 0) tc_dealloc(tm, 256);
 }
 
+// One Adam step (Kingma and Ba, 2015) for parameter i with gradient g.
+struct AdamStep {
+  float* p;  // null: no step
+  float* m;
+  float* v;
+  float lr, b1, b2, eps, c1, c2;  // c1, c2: the bias corrections 1 - beta^step
+};
+__device__ __forceinline__ void adam_one(const AdamStep& A, int i, float g) {
+  const float mi = A.b1 * A.m[i] + (1.0f - A.b1) * g;
+  const float vi = A.b2 * A.v[i] + (1.0f - A.b2) * g * g;
+  A.m[i] = mi;
+  A.v[i] = vi;
+  A.p[i] -= A.lr * (mi / A.c1) / (sqrtf(vi / A.c2) + A.eps);
+}
+
 // grad[i] (and, for i = KL_MLP_NPARAMS, the loss) = the sum of the partials
 // of output i: one block per output, thread t takes partials t, t + 128, ...
-// in order, then a fixed reduction tree.
+// in order, then a fixed reduction tree.  With an Adam step, the block then
+// applies it to parameter i (grad may then be null).
 __global__ void __launch_bounds__(128) mlp_reduce_kernel(const float* __restrict__ bwd, int n_bwd,
                                                          const float* __restrict__ wg, int n_wg,
                                                          float* __restrict__ grad,
-                                                         float* __restrict__ loss) {
+                                                         float* __restrict__ loss, AdamStep A) {
   const int i = blockIdx.x;
   const float* src;
   int stride, count;
@@ -500,23 +516,26 @@ __global__ void __launch_bounds__(128) mlp_reduce_kernel(const float* __restrict
   __syncthreads();
   if (threadIdx.x == 0) {
     const float v = (ws[0] + ws[1]) + (ws[2] + ws[3]);
-    if (i == KL_MLP_NPARAMS) *loss = v;
-    else grad[i] = v;
+    if (i == KL_MLP_NPARAMS) {
+      *loss = v;
+    } else {
+      if (grad) grad[i] = v;
+      if (A.p) adam_one(A, i, v);
+    }
   }
 }
 
-__global__ void adam_kernel(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
-                            float* __restrict__ g, int n, float lr, float b1, float b2, float eps,
-                            float c1, float c2) {
+__global__ void adam_kernel(float* __restrict__ g, int n, AdamStep A) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.0f - b1) * gi;
-    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    adam_one(A, i, g[i]);
     g[i] = 0.0f;
   }
+}
+
+AdamStep adam_args(float* p, float* m, float* v, uint32_t step, float lr, float beta1,
+                   float beta2, float eps) {
+  return {p, m, v, lr, beta1, beta2, eps, 1.0f - powf(beta1, (float)step),
+          1.0f - powf(beta2, (float)step)};
 }
 
 }  // namespace
@@ -543,14 +562,16 @@ extern "C" size_t kl_mlp_scratch_bytes(uint64_t n) {
          align256((size_t)kWgMaxBlocks * kWgPart * sizeof(float));
 }
 
-extern "C" int kl_mlp_grad(const float* d_params, const float* d_x, const float* d_t, uint64_t n,
-                           float under_weight, float* d_grad, float* d_loss, void* d_scratch,
-                           size_t scratch_bytes, void* stream) {
-  if (n == 0 || !d_params || !d_x || !d_t || !d_grad || !d_loss || !d_scratch) return KL_EINVAL;
+namespace {
+
+// Gradient pass, then the fixed-order reduce (with an Adam step when A.p).
+int grad_pass(const float* d_params, const float* d_x, const float* d_t, uint64_t n,
+              float under_weight, float* d_grad, float* d_loss, void* d_scratch,
+              size_t scratch_bytes, cudaStream_t s, const AdamStep& A) {
+  if (n == 0 || !d_params || !d_x || !d_t || !d_loss || !d_scratch) return KL_EINVAL;
   if (!(under_weight > 0.0f)) return KL_EINVAL;
   if (scratch_bytes < kl_mlp_scratch_bytes(n)) return KL_ENOSPACE;
   if (((uintptr_t)d_scratch & 255u) != 0 || ((uintptr_t)d_x & 15u) != 0) return KL_EINVAL;
-  cudaStream_t s = (cudaStream_t)stream;
   const int sms = sm_count();
   if (sms <= 0) return KL_ECUDA;
   if (cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -567,15 +588,35 @@ extern "C" int kl_mlp_grad(const float* d_params, const float* d_x, const float*
                                                            bwd_part, wg_part);
   if (check_launch() != KL_OK) return KL_ECUDA;
   mlp_reduce_kernel<<<KL_MLP_NPARAMS + 1, 128, 0, s>>>(bwd_part, (int)grid, wg_part, (int)grid,
-                                                       d_grad, d_loss);
+                                                       d_grad, d_loss, A);
   return check_launch();
+}
+
+}  // namespace
+
+extern "C" int kl_mlp_grad(const float* d_params, const float* d_x, const float* d_t, uint64_t n,
+                           float under_weight, float* d_grad, float* d_loss, void* d_scratch,
+                           size_t scratch_bytes, void* stream) {
+  if (!d_grad) return KL_EINVAL;
+  return grad_pass(d_params, d_x, d_t, n, under_weight, d_grad, d_loss, d_scratch, scratch_bytes,
+                   (cudaStream_t)stream, AdamStep{});
 }
 
 extern "C" int kl_mlp_adam(float* d_params, float* d_m, float* d_v, float* d_grad, uint32_t step,
                            float lr, float beta1, float beta2, float eps, void* stream) {
   if (!d_params || !d_m || !d_v || !d_grad || step == 0) return KL_EINVAL;
-  const float c1 = 1.0f - powf(beta1, (float)step), c2 = 1.0f - powf(beta2, (float)step);
   adam_kernel<<<(KL_MLP_NPARAMS + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
-      d_params, d_m, d_v, d_grad, KL_MLP_NPARAMS, lr, beta1, beta2, eps, c1, c2);
+      d_grad, KL_MLP_NPARAMS, adam_args(d_params, d_m, d_v, step, lr, beta1, beta2, eps));
   return check_launch();
+}
+
+extern "C" int kl_mlp_train_step(float* d_params, float* d_m, float* d_v, const float* d_x,
+                                 const float* d_t, uint64_t n, float under_weight, uint32_t step,
+                                 float lr, float beta1, float beta2, float eps, float* d_loss,
+                                 float* d_grad, void* d_scratch, size_t scratch_bytes,
+                                 void* stream) {
+  if (!d_params || !d_m || !d_v || step == 0) return KL_EINVAL;
+  return grad_pass(d_params, d_x, d_t, n, under_weight, d_grad, d_loss, d_scratch, scratch_bytes,
+                   (cudaStream_t)stream,
+                   adam_args(d_params, d_m, d_v, step, lr, beta1, beta2, eps));
 }

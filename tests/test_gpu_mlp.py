@@ -107,3 +107,24 @@ def test_training_is_deterministic(kl):
         runs.append((losses, params.cpu().numpy().copy()))
     assert runs[0][0] == runs[1][0]
     assert np.array_equal(runs[0][1], runs[1][1])
+
+
+def test_train_step_equals_gradient_then_adam(kl):
+    """kl_mlp_train_step (gradient, fixed-order sum and Adam in one pass) gives
+    bit for bit the parameters, moments and losses of kl_mlp_grad followed by
+    kl_mlp_adam."""
+    import torch
+    p, x, t = setup(9000, 21)
+    X = torch.tensor(x, dtype=torch.float32, device="cuda")
+    T = torch.tensor(t, dtype=torch.float32, device="cuda")
+    runs = []
+    for fused in (True, False):
+        params = torch.tensor(p * 0.5, dtype=torch.float32, device="cuda")
+        tr = kl.MlpTrainer(params, lr=3e-3, under_weight=4.0)
+        step = tr.step if fused else tr.step_separate
+        losses = [float(step(X, T).item()) for _ in range(10)]
+        runs.append((losses, params.cpu().numpy().copy(), tr.m.cpu().numpy().copy(),
+                     tr.v.cpu().numpy().copy()))
+    assert runs[0][0] == runs[1][0]
+    for a, b in zip(runs[0][1:], runs[1][1:]):
+        assert np.array_equal(a, b)
