@@ -635,8 +635,8 @@ def lod_config(kl, n_train: int = 64, n_test: int = 16, n_valid: int = 8):
     torch.cuda.synchronize()
     t2 = time.time()
     tuned = lod.tune_prune(va, mlp, lo, hi, target=0.9995)
-    margin, edge = tuned["margin"], tuned["edge"]
-    evals = [lod.evaluate(p, mlp, lo, hi, margin, edge, repeats=3) for p in te]
+    margin, edge, hi_r = tuned["margin"], tuned["edge"], tuned["hi"]
+    evals = [lod.evaluate(p, mlp, lo, hi_r, margin, edge, repeats=3) for p in te]
     s = lod.summarize(evals)
     # the exact culled render of the same groups (no network; every word placed)
     cul_ms, cul_iou, cul_diff = 0.0, 1.0, 0
@@ -662,10 +662,10 @@ def lod_config(kl, n_train: int = 64, n_test: int = 16, n_valid: int = 8):
                           f"({kl.word_count(d)} words each), 8192^2 over [-2,2]^2; network "
                           f"trained on {n_train} groups (seed 1710); pruning setting chosen "
                           f"on {n_valid} validation groups (seed 1712)",
-              "levels": [lo, hi], "label_extent_px": extent, "under_weight": under,
-              "margin": margin, "edge_px": edge,
-              "valid_settings": [{"margin": m, "edge_px": e, "iou_min": round(i, 6),
-                                  "ms": round(t, 3)} for m, e, i, t in tuned["tried"]],
+              "levels": [lo, hi], "render_levels": [lo, hi_r], "label_extent_px": extent,
+              "under_weight": under, "margin": margin, "edge_px": edge,
+              "valid_settings": [{"margin": m, "edge_px": e, "hi": h, "iou_min": round(i, 6),
+                                  "ms": round(t, 3)} for m, e, h, i, t in tuned["tried"]],
               "train_samples": int(x.shape[0]), "train_steps": 10000,
               "loss_first_last": [losses[0], losses[-1]], "label_seconds": t1 - t0,
               "train_seconds": t2 - t1,

@@ -1127,6 +1127,114 @@ __device__ __forceinline__ void df64_item(uint32_t item, const Work& Wk, const P
 }
 
 // ---------------------------------------------------------------------------
+// scalar double-floats: one value per thread (the level-of-detail expansion,
+// where each lane holds its own node matrix).  The same arithmetic as the
+// packed pairs above.
+
+struct D1 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ D1 d1_of(double d) {
+  D1 r;
+  split_df(d, r.hi, r.lo);
+  return r;
+}
+__device__ __forceinline__ D1 d1_neg(D1 a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ void two_sum1(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ D1 fast_two_sum1(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ D1 d1_add(D1 a, D1 b) {
+  float s, e;
+  two_sum1(a.hi, b.hi, s, e);
+  return fast_two_sum1(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ D1 d1_mul(D1 a, D1 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return fast_two_sum1(p, e);
+}
+// sum of N products a_i b_i: high products and their exact errors, an exact
+// running sum of the products, the cross terms, one renormalisation
+template <int N>
+__device__ __forceinline__ D1 d1_dot(const D1 (&a)[N], const D1 (&b)[N]) {
+  float s = __fmul_rn(a[0].hi, b[0].hi);
+  float e = __fmaf_rn(a[0].hi, b[0].hi, -s);
+#pragma unroll
+  for (int i = 1; i < N; ++i) {
+    const float p = __fmul_rn(a[i].hi, b[i].hi);
+    e = __fadd_rn(e, __fmaf_rn(a[i].hi, b[i].hi, -p));
+    float t;
+    two_sum1(s, p, s, t);
+    e = __fadd_rn(e, t);
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    e = __fmaf_rn(a[i].hi, b[i].lo, e);
+    e = __fmaf_rn(a[i].lo, b[i].hi, e);
+  }
+  return fast_two_sum1(s, e);
+}
+// 1/m: hardware seed and one Newton step with the residual from m.hi y exactly
+__device__ __forceinline__ D1 d1_rcp(D1 m) {
+  const float y = rcp32(m.hi);
+  const float p = __fmul_rn(m.hi, y);
+  const float pe = __fmaf_rn(m.hi, y, -p);
+  const float res = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, p), pe), __fmul_rn(m.lo, y));
+  return fast_two_sum1(y, __fmul_rn(y, res));
+}
+
+struct C1 {
+  D1 re, im;
+};
+struct M1 {
+  C1 p, q, r, s;
+};
+
+__device__ __forceinline__ M1 m1_of(const M2& a) {
+  return {{d1_of(a.p.re), d1_of(a.p.im)}, {d1_of(a.q.re), d1_of(a.q.im)},
+          {d1_of(a.r.re), d1_of(a.r.im)}, {d1_of(a.s.re), d1_of(a.s.im)}};
+}
+// a b + c d (complex), each part one 4-term dot product
+__device__ __forceinline__ C1 c1_mul_add(C1 a, C1 b, C1 c, C1 d) {
+  const D1 xr[4] = {a.re, d1_neg(a.im), c.re, d1_neg(c.im)};
+  const D1 yr[4] = {b.re, b.im, d.re, d.im};
+  const D1 xi[4] = {a.re, a.im, c.re, c.im};
+  const D1 yi[4] = {b.im, b.re, d.im, d.re};
+  return {d1_dot<4>(xr, yr), d1_dot<4>(xi, yi)};
+}
+__device__ __forceinline__ M1 m1_mul(const M1& a, const M1& b) {
+  return {c1_mul_add(a.p, b.p, a.q, b.r), c1_mul_add(a.p, b.q, a.q, b.s),
+          c1_mul_add(a.r, b.p, a.s, b.r), c1_mul_add(a.r, b.q, a.s, b.s)};
+}
+// a v + b (complex)
+__device__ __forceinline__ C1 c1_affine(C1 a, C1 v, C1 b) {
+  const D1 one = {1.0f, 0.0f};
+  const D1 xr[3] = {a.re, d1_neg(a.im), b.re};
+  const D1 yr[3] = {v.re, v.im, one};
+  const D1 xi[3] = {a.re, a.im, b.im};
+  const D1 yi[3] = {v.im, v.re, one};
+  return {d1_dot<3>(xr, yr), d1_dot<3>(xi, yi)};
+}
+// P(v) = (p v + q) / (r v + s) as n conj(m) / |m|^2
+__device__ __forceinline__ C1 m1_apply(const M1& P, C1 v) {
+  const C1 n = c1_affine(P.p, v, P.q), m = c1_affine(P.r, v, P.s);
+  const D1 mm[2] = {m.re, m.im};
+  const D1 k = d1_rcp(d1_dot<2>(mm, mm));
+  const D1 ar[2] = {n.re, n.im}, br[2] = {m.re, m.im};
+  const D1 ai[2] = {n.im, d1_neg(n.re)}, bi[2] = {m.re, m.im};
+  return {d1_mul(d1_dot<2>(ar, br), k), d1_mul(d1_dot<2>(ai, bi), k)};
+}
+
+// ---------------------------------------------------------------------------
 // culled renders (kl_params.cull), shared by the single and batched renders
 //
 // The suffix points of one first letter come in aligned blocks of 3^j

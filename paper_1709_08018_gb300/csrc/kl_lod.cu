@@ -46,18 +46,29 @@ __host__ __device__ __forceinline__ uint32_t level_nodes(const LodPlan& P, int k
   return 4u * P.p3[k];
 }
 
+// An active node: its prefix matrix p, q, r, s (re, im) as double-floats
+// (hi + lo float pairs, about 48 bits: the FP64 pipe, the scarce one on this
+// GPU, is left out of the tree levels) and its slot.
 struct __align__(16) Active {
-  double m[8];  // prefix matrix p, q, r, s (re, im)
+  float hi[8], lo[8];
   uint32_t slot;
   uint32_t pad[3];
 };
 
-__device__ __forceinline__ M2 to_m2(const double* m) {
-  return {{m[0], m[1]}, {m[2], m[3]}, {m[4], m[5]}, {m[6], m[7]}};
+__device__ __forceinline__ M1 m1_load(const Active& a) {
+  M1 P;
+  D1* e = &P.p.re;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) e[i] = {a.hi[i], a.lo[i]};
+  return P;
 }
-__device__ __forceinline__ void from_m2(const M2& a, double* m) {
-  m[0] = a.p.re; m[1] = a.p.im; m[2] = a.q.re; m[3] = a.q.im;
-  m[4] = a.r.re; m[5] = a.r.im; m[6] = a.s.re; m[7] = a.s.im;
+__device__ __forceinline__ void m1_store(const M1& P, Active& a) {
+  const D1* e = &P.p.re;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    a.hi[i] = e[i].hi;
+    a.lo[i] = e[i].lo;
+  }
 }
 
 // Prefix matrix of node `slot` at level k (nk = 3^(k-1)): letters right to left.
@@ -92,6 +103,20 @@ __device__ void node_features(const M2& P, float* f) {
   const bool neg = lead < 0.0;
   for (int i = 0; i < 8; ++i) {
     const float a = neg ? -(float)v[i] : (float)v[i];
+    f[i] = copysignf(log1pf(fabsf(a)), a);
+  }
+}
+
+// The same features from a double-float node matrix: the high parts are the
+// FP32 roundings of the entries (what node_features converts), and the sign
+// of the trace is taken from its double-float sum.
+__device__ void node_features_df(const M1& P, float* f) {
+  const D1* e = &P.p.re;
+  float lead = d1_add(P.p.re, P.s.re).hi;
+  for (int i = 0; i < 8 && lead == 0.0f; ++i) lead = e[i].hi;
+  const bool neg = lead < 0.0f;
+  for (int i = 0; i < 8; ++i) {
+    const float a = neg ? -e[i].hi : e[i].hi;
     f[i] = copysignf(log1pf(fabsf(a)), a);
   }
 }
@@ -238,15 +263,38 @@ constexpr int kNearEdge = -2;
 // Pixel id of pixel coordinates (u, v) if the point lies at least `edge`
 // inside that pixel; -1 if it lies at least `edge` outside the window (or is
 // not finite); kNearEdge otherwise.
-__device__ __forceinline__ int guarded_pixel(double u, double v, const View& V, double edge) {
-  if (!(fabs(u) < 4.0e9 && fabs(v) < 4.0e9)) return -1;
-  const double W = (double)V.W, H = (double)V.H;
-  if (u < -edge || v < -edge || u >= W + edge || v >= H + edge) return -1;
-  if (u < 0.0 || v < 0.0 || u >= W || v >= H) return kNearEdge;
-  const double fu = floor(u), fv = floor(v);
-  if (u - fu < edge || fu + 1.0 - u <= edge || v - fv < edge || fv + 1.0 - v <= edge)
-    return kNearEdge;
-  return (int)fv * (int)V.W + (int)fu;
+// Coordinates u, v are double-floats; u = cu + ru with cu an integer (exact
+// as a float near the window) and ru in [0, 1) from the exact fraction of
+// u.hi plus u.lo.
+__device__ __forceinline__ void split_unit(D1 u, float& c, float& r) {
+  c = floorf(u.hi);
+  r = __fadd_rn(__fsub_rn(u.hi, c), u.lo);
+  if (r < 0.0f) {
+    r = __fadd_rn(r, 1.0f);
+    c -= 1.0f;
+  } else if (r >= 1.0f) {
+    r = __fsub_rn(r, 1.0f);
+    c += 1.0f;
+  }
+}
+__device__ __forceinline__ int guarded_pixel_df(D1 u, D1 v, const View& V, float edge) {
+  const float W = (float)V.W, H = (float)V.H;
+  // far outside (or not finite): no finer test needed
+  if (!(u.hi > -2.0f - edge && u.hi < W + 2.0f + edge && v.hi > -2.0f - edge &&
+        v.hi < H + 2.0f + edge))
+    return -1;
+  float cu, ru, cv, rv;
+  split_unit(u, cu, ru);
+  split_unit(v, cv, rv);
+  // at least `edge` outside the window
+  const bool out_u = cu <= -2.0f || (cu == -1.0f && ru < 1.0f - edge) || cu >= W + 1.0f ||
+                     (cu == W && ru >= edge);
+  const bool out_v = cv <= -2.0f || (cv == -1.0f && rv < 1.0f - edge) || cv >= H + 1.0f ||
+                     (cv == H && rv >= edge);
+  if (out_u || out_v) return -1;
+  if (cu < 0.0f || cv < 0.0f || cu >= W || cv >= H) return kNearEdge;
+  if (ru < edge || 1.0f - ru <= edge || rv < edge || 1.0f - rv <= edge) return kNearEdge;
+  return (int)cv * (int)V.W + (int)cu;
 }
 
 __global__ void vstar_kernel(Group G, int D, int lo, int hi, double2* vstar) {
@@ -269,7 +317,7 @@ __global__ void init_active_kernel(Group G, int k, uint32_t nk, Active* out, uin
   const uint32_t n = 4u * nk;
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
     Active a;
-    from_m2(node_matrix(G, k, s, nk), a.m);
+    m1_store(m1_of(node_matrix(G, k, s, nk)), a);
     a.slot = s;
     a.pad[0] = a.pad[1] = a.pad[2] = 0;
     out[s] = a;
@@ -291,8 +339,25 @@ __global__ void __launch_bounds__(kLodThreads) expand_kernel(
   __shared__ MlpSmem S;
   __shared__ float xs[kLodThreads / 32][32][8];
   __shared__ float ys[kLodThreads / 32][32];
+  // the generators, this level's representative suffix points and the view
+  // as double-floats (split once per block)
+  __shared__ M1 gen[4];
+  __shared__ C1 reps[kReps * 4];
+  __shared__ D1 vx0, vy1, vsx, vsy;
   if (mlp) load_mlp(S, mlp);
+  if (threadIdx.x < 4) gen[threadIdx.x] = m1_of(load_gen(G, (int)threadIdx.x));
+  if (threadIdx.x < kReps * 4) {
+    const double2 v = vstar[threadIdx.x * (hi + 1) + k];
+    reps[threadIdx.x] = {d1_of(v.x), d1_of(v.y)};
+  }
+  if (threadIdx.x == 0) {
+    vx0 = d1_neg(d1_of(V.x0));
+    vy1 = d1_of(V.y1);
+    vsx = d1_of(V.sx);
+    vsy = d1_of(V.sy);
+  }
   __syncthreads();
+  const float edge_f = (float)edge;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
   const uint32_t n = *in_count;
   unsigned long long words_sub = 1;
@@ -308,7 +373,7 @@ __global__ void __launch_bounds__(kLodThreads) expand_kernel(
     float y;
     if (mlp) {
       float f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      if (valid) node_features(to_m2(a.m), f);
+      if (valid) node_features_df(m1_load(a), f);
       for (int j = 0; j < 8; ++j) xs[warp][lane][j] = f[j];
       __syncwarp();
       for (int half = 0; half < 2; ++half) {
@@ -331,22 +396,19 @@ __global__ void __launch_bounds__(kLodThreads) expand_kernel(
     int action = 0;  // 1: expand to the three children, 2: defer to the exact render
     if (valid) {
       ++visited;
-      const M2 P = to_m2(a.m);
+      const M1 P = m1_load(a);
       const int x = (int)(a.slot / nk);
       // prune when the score says resolved and the subtree's first, middle and
-      // last words agree on one pixel (or all miss the window)
+      // last words agree on one pixel (or all miss the window); the words'
+      // values in double-float arithmetic
       bool prune = y + margin < 0.5f;
       int pix = -1;
       if (prune) {
         for (int e = 0; e < kReps; ++e) {
-          const double2 v = vstar[(e * 4 + x) * (hi + 1) + k];
-          // P(v) with a refined reciprocal instead of a division
-          const dc num = cadd(cmul(P.p, {v.x, v.y}), P.q);
-          const dc den = cadd(cmul(P.r, {v.x, v.y}), P.s);
-          const double rc = rcp64(den.re * den.re + den.im * den.im);
-          const dc z = {(num.re * den.re + num.im * den.im) * rc,
-                        (num.im * den.re - num.re * den.im) * rc};
-          const int pe = guarded_pixel((z.re - V.x0) * V.sx, (V.y1 - z.im) * V.sy, V, edge);
+          const C1 z = m1_apply(P, reps[e * 4 + x]);
+          const D1 u = d1_mul(d1_add(z.re, vx0), vsx);
+          const D1 v = d1_mul(d1_add(vy1, d1_neg(z.im)), vsy);
+          const int pe = guarded_pixel_df(u, v, V, edge_f);
           if (e == 0) pix = pe;
           if (pe == kNearEdge || pe != pix) prune = false;
         }
@@ -379,7 +441,7 @@ __global__ void __launch_bounds__(kLodThreads) expand_kernel(
     base_d = __shfl_sync(0xFFFFFFFFu, base_d, 0);
     const unsigned lt = (1u << lane) - 1u;
     if (action == 1) {
-      const M2 P = to_m2(a.m);
+      const M1 P = m1_load(a);
       const int x = (int)(a.slot / nk);
       const uint32_t base = base_e + 3u * (uint32_t)__popc(be & lt);
       const uint32_t r = a.slot % nk;
@@ -387,7 +449,7 @@ __global__ void __launch_bounds__(kLodThreads) expand_kernel(
         const int yl = allowed_letter(q, (x + 2) & 3);
         const int rk = x - (x > ((yl + 2) & 3) ? 1 : 0);
         Active b;
-        from_m2(mmul(P, load_gen(G, yl)), b.m);
+        m1_store(m1_mul(P, gen[yl]), b);
         b.slot = (uint32_t)yl * 3u * nk + (uint32_t)rk * nk + r;
         b.pad[0] = b.pad[1] = b.pad[2] = 0;
         out[base + q] = b;

@@ -161,33 +161,40 @@ PRUNE_EDGES = (0.0, 1 / 512, 1 / 128)
 
 
 def tune_prune(params: Sequence[kb.Params], mlp, lo: int, hi: int, target: float = 0.9995,
-               margins=PRUNE_MARGINS, edges=PRUNE_EDGES) -> Dict:
-    """The fastest (margin, edge) setting whose pruned renders of `params`
-    all reach occupancy IoU >= target against their exact renders (the
-    setting with the best worst-case IoU if none does).  `params` are
-    validation groups, apart from both the training and the held-out groups.
-    Returns {"margin", "edge", "tried": [(margin, edge, worst IoU, ms)]}."""
-    exact, lods = [], []
+               margins=PRUNE_MARGINS, edges=PRUNE_EDGES, his=None) -> Dict:
+    """The fastest (margin, edge, hi) setting whose pruned renders of
+    `params` all reach occupancy IoU >= target against their exact renders
+    (the setting with the best worst-case IoU if none does).  hi is the last
+    level the render expands (the network is trained on levels lo..hi; a
+    smaller hi hands the remaining nodes to the exact render sooner); by
+    default hi - 2 .. hi.  `params` are validation groups, apart from both the
+    training and the held-out groups.  Returns {"margin", "edge", "hi",
+    "tried": [(margin, edge, hi, worst IoU, ms)]}."""
+    if his is None:
+        his = [h for h in (hi - 2, hi - 1, hi) if h >= lo]
+    exact = []
     for p in params:
         r = kb.Renderer(p)
         r()
         exact.append(r.image != 0)
-        lods.append(kb.LodRenderer(p, lo, hi))
         del r
     tried = []
-    for margin in margins:
-        for edge in edges:
-            worst, ms = 1.0, 0.0
-            for occ, L in zip(exact, lods):
-                ms += time_ms(lambda: L(mlp, margin, edge), 1)
-                img, _, _ = L(mlp, margin, edge)
-                b = img != 0
-                union = int((occ | b).sum())
-                worst = min(worst, int((occ & b).sum()) / union if union else 1.0)
-            tried.append((margin, edge, worst, ms))
-    ok = [t for t in tried if t[2] >= target]
-    best = min(ok, key=lambda t: t[3]) if ok else max(tried, key=lambda t: t[2])
-    return {"margin": best[0], "edge": best[1], "tried": tried}
+    for h in his:
+        lods = [kb.LodRenderer(p, lo, h) for p in params]
+        for margin in margins:
+            for edge in edges:
+                worst, ms = 1.0, 0.0
+                for occ, L in zip(exact, lods):
+                    ms += time_ms(lambda: L(mlp, margin, edge), 1)
+                    img, _, _ = L(mlp, margin, edge)
+                    b = img != 0
+                    union = int((occ | b).sum())
+                    worst = min(worst, int((occ & b).sum()) / union if union else 1.0)
+                tried.append((margin, edge, h, worst, ms))
+        del lods
+    ok = [t for t in tried if t[3] >= target]
+    best = min(ok, key=lambda t: t[4]) if ok else max(tried, key=lambda t: t[3])
+    return {"margin": best[0], "edge": best[1], "hi": best[2], "tried": tried}
 
 
 def summarize(evals: List[Eval]) -> Dict:

@@ -242,7 +242,7 @@ def test_trained_network_gain(kl):
         # leave its pixel, up to the rounding of the mixed words
         floor = lod.evaluate_labels(p, lo, hi, extent)
         assert floor.words == kl.word_count(d) and floor.iou >= 0.9999, floor
-        e = lod.evaluate(p, mlp, lo, hi, tuned["margin"], tuned["edge"], repeats=2)
+        e = lod.evaluate(p, mlp, lo, tuned["hi"], tuned["margin"], tuned["edge"], repeats=2)
         assert e.words == kl.word_count(d)
         assert e.iou >= 0.999, (e, tuned)
         # the gain over the method without the network: the per-word render
