@@ -655,9 +655,10 @@ def lod_config(kl, n_train: int = 64, n_test: int = 16, n_valid: int = 8):
                    "iou_min_vs_exact": cul_iou, "pixels_differing_from_exact": cul_diff,
                    "pruned_speedup_over_culled": cul_ms / s["pruned_ms"],
                    "network_beats_culled": s["pruned_ms"] < cul_ms,
-                   "reading": "the exact culled render certifies the sub-pixel subtrees "
-                              "the network learns to prune, without its losses; the "
-                              "network's gain is over the per-word render only"}
+                   "reading": "the exact culled render certifies sub-pixel subtrees "
+                              "without the network's losses; the network prunes whole "
+                              "subtrees before any of their words or disks are computed "
+                              "and hands the rest to the same culling engine"}
     s.update({"workload": f"{n_test} held-out groups (seed 1711), depth 22 "
                           f"({kl.word_count(d)} words each), 8192^2 over [-2,2]^2; network "
                           f"trained on {n_train} groups (seed 1710); pruning setting chosen "

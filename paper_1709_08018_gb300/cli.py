@@ -50,6 +50,10 @@ def main(argv=None):
     ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--per-level", type=int, default=20_000)
     ap.add_argument("--held-out", type=int, default=1)
+    ap.add_argument("--margin", type=float, default=-1.4, help="pruning margin (--lod)")
+    ap.add_argument("--edge", type=float, default=1.0 / 128, help="edge guard in px (--lod)")
+    ap.add_argument("--last-level", type=int, default=0,
+                    help="last expanded level of the pruned render (--lod; default hi - 2)")
     ap.add_argument("--scan", action="store_true")
     ap.add_argument("--mlp", type=int, default=0, help="rows of a training-step timing")
     ap.add_argument("--tiling", action="store_true")
@@ -152,9 +156,11 @@ def run_mlp(a, kl, torch):
 def run_lod(a, kl, klsynth, torch):
     """Train the pruning network on --train-groups groups (--per-level nodes
     per level, --train-steps steps; bench.py's setting is 64, 60000, 10000)
-    and run the pruned render (margin -0.8, edge 1/512 px) of the first
-    --held-out held-out groups, --repeat times each, at depth --depth (22) and
-    --size (8192) pixels."""
+    and run the pruned render (--margin, --edge px, levels lo..--last-level)
+    of the first --held-out held-out groups, --repeat times each, at depth
+    --depth (22) and --size (8192) pixels.  The defaults are the setting
+    bench.py's validation groups select (margin -1.4, edge 1/128 px, last
+    level hi - 2)."""
     from paper_1709_08018_gb300 import lod
     # bench.py's setting by default; --depth and --size give a smaller case
     # (levels lo..hi follow the depth: hi = d - 7, lo = hi - 7)
@@ -166,16 +172,17 @@ def run_lod(a, kl, klsynth, torch):
     tr = [mk(g) for g, _ in klsynth.draw_groups(klsynth.LOD_TRAIN_SEED, a.train_groups)]
     x, t = lod.make_dataset(tr, lo, hi, per_level=a.per_level, seed=3, extent=extent)
     mlp, losses = lod.train(x, t, steps=a.train_steps, batch=16384, lr=2e-3, seed=5, under=32.0)
+    last = a.last_level or max(lo, hi - 2)
     for g, _ in klsynth.draw_groups(klsynth.LOD_HELDOUT_SEED, a.held_out):
-        L = kl.LodRenderer(mk(g), lo, hi)
+        L = kl.LodRenderer(mk(g), lo, last)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         for _ in range(a.repeat):
             e0.record()
-            img, cnt, st = L(mlp, -0.8, 1.0 / 512)
+            img, cnt, st = L(mlp, a.margin, a.edge)
             e1.record()
         torch.cuda.synchronize()
         st, cnt = st.cpu().tolist(), cnt.cpu().tolist()
-        print(f"lod d={d} {size}^2 levels {lo}..{hi}: loss {losses[0]:.3g} -> {losses[-1]:.3g}, "
+        print(f"lod d={d} {size}^2 levels {lo}..{last}: loss {losses[0]:.3g} -> {losses[-1]:.3g}, "
               f"nodes {st[0]}, pruned {st[1]}, deferred {st[2]}, words {cnt[0] + cnt[1]}, "
               f"{e0.elapsed_time(e1):.3f} ms")
         del L
