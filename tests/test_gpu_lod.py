@@ -6,11 +6,11 @@
   - the labels obey their recursion, and level-hi labels agree with the
     oracle's own test "the subtree's image is under `extent` pixels, or
     misses the window";
-  - a network trained on a few groups, with its pruning setting chosen on
-    separate validation groups, renders held-out groups faster than the exact
-    render (the method without it, which evaluates every word) at occupancy
-    IoU >= 0.999; pruning by the true labels with the edge guard at the label
-    extent keeps IoU >= 0.9999.
+  - a network trained on 64 groups, with its pruning setting chosen on
+    separate validation groups, renders 16 held-out groups faster than both
+    exact methods without it (the per-word render, which evaluates every
+    word, and the culled render) at occupancy IoU >= 0.999; pruning by the
+    true labels with the edge guard at the label extent keeps IoU >= 0.9999.
 """
 import numpy as np
 import pytest
@@ -225,36 +225,47 @@ def test_features_against_oracle(kl):
 
 
 def test_trained_network_gain(kl):
+    """The benchmark's setting: a network trained on 64 groups, its pruning
+    setting (margin, edge, last level) chosen on 8 validation groups, judged
+    on the 16 held-out groups at depth 22, 8192^2.  Against the method
+    without it, both ways: the per-word render (every word evaluated) and the
+    exact culled render (kl_params.cull), which certifies sub-pixel blocks
+    without the network's losses."""
     from paper_1709_08018_gb300 import lod
     d, lo, hi, size, extent = 22, 8, 15, 8192, 1.0 / 32
-    train_groups = [g for g, _ in klsynth.draw_groups(klsynth.LOD_TRAIN_SEED, 16)]
-    valid_groups = [g for g, _ in klsynth.draw_groups(klsynth.LOD_VALID_SEED, 4)]
-    test_groups = [g for g, _ in klsynth.draw_groups(klsynth.LOD_HELDOUT_SEED, 2)]
+    train_groups = [g for g, _ in klsynth.draw_groups(klsynth.LOD_TRAIN_SEED, 64)]
+    valid_groups = [g for g, _ in klsynth.draw_groups(klsynth.LOD_VALID_SEED, 8)]
+    test_groups = [g for g, _ in klsynth.draw_groups(klsynth.LOD_HELDOUT_SEED, 16)]
     ptrain = [group_params(kl, g, d, size) for g in train_groups]
     x, t = lod.make_dataset(ptrain, lo, hi, per_level=60_000, seed=3, extent=extent)
     mlp, losses = lod.train(x, t, steps=10000, batch=16384, lr=2e-3, seed=5, under=32.0)
-    assert losses[-1] < 0.1 * losses[0]
+    assert losses[-1] < 0.01 * losses[0]
     tuned = lod.tune_prune([group_params(kl, g, d, size) for g in valid_groups], mlp, lo, hi,
                            target=0.9995)
-    for g in test_groups:
+    pruned_ms = exact_ms = culled_ms = 0.0
+    iou_min = 1.0
+    for n, g in enumerate(test_groups):
         p = group_params(kl, g, d, size)
-        # true labels with the edge guard at the label extent: no word may
-        # leave its pixel, up to the rounding of the mixed words
-        floor = lod.evaluate_labels(p, lo, hi, extent)
-        assert floor.words == kl.word_count(d) and floor.iou >= 0.9999, floor
+        if n < 2:
+            # true labels with the edge guard at the label extent: no word may
+            # leave its pixel, up to the rounding of the mixed words
+            floor = lod.evaluate_labels(p, lo, hi, extent)
+            assert floor.words == kl.word_count(d) and floor.iou >= 0.9999, floor
         e = lod.evaluate(p, mlp, lo, tuned["hi"], tuned["margin"], tuned["edge"], repeats=2)
         assert e.words == kl.word_count(d)
-        assert e.iou >= 0.999, (e, tuned)
-        # the gain over the method without the network: the per-word render
-        assert e.pruned_ms < 0.8 * e.exact_ms, (e, tuned)
-        # and the comparison with the exact culled render (kl_params.cull),
-        # which certifies sub-pixel subtrees exactly: measured and printed,
-        # not asserted (this test's network is trained on 16 groups only; the
-        # benchmark's on 64 reports lod.culled)
+        iou_min = min(iou_min, e.iou)
+        pruned_ms += e.pruned_ms
+        exact_ms += e.exact_ms
         q = kl.Params.from_buffer_copy(p)
         q.cull = 1
         rc = kl.Renderer(q)
-        culled_ms = lod.time_ms(lambda: rc(), 2)
-        print(f"\nheld-out group: per-word {e.exact_ms:.2f} ms, pruned {e.pruned_ms:.2f} ms "
-              f"(IoU {e.iou:.5f}), culled exact {culled_ms:.2f} ms")
-        assert culled_ms < e.exact_ms
+        culled_ms += lod.time_ms(lambda: rc(), 2)
+        del rc
+    print(f"\n16 held-out groups: per-word {exact_ms:.2f} ms, pruned {pruned_ms:.2f} ms "
+          f"(IoU min {iou_min:.5f}; margin {tuned['margin']}, edge {tuned['edge']}, "
+          f"levels {lo}..{tuned['hi']}), culled exact {culled_ms:.2f} ms")
+    assert iou_min >= 0.999, tuned
+    # the gain over the per-word render
+    assert pruned_ms < 0.2 * exact_ms
+    # and over the exact culled render
+    assert pruned_ms < culled_ms
