@@ -40,10 +40,10 @@ FP32_OPS_PER_WORD = 12    # FP32 operations of the mixed per-word map: w = v + g
                           # |w|^2 (2), M w (4), M w / |w|^2 + alpha (2), the two floors (2)
 FP64_OPS_PER_WORD = 13    # FP64 operations of the plain per-word map: w = v + gamma (2),
                           # |w|^2 (2), reciprocal refinement (3), M w (4), final FMAs (2)
-DF64_OPS_PER_WORD = 127   # FP32 operations of the double-float per-word map: w = v + gamma
-                          # (2 double-float sums, 11 each), |w|^2 (19), the reciprocal's Newton
-                          # step (10), the two numerators (dot products, 19 each), a + b c for
-                          # the two coordinates (15 each), and the two pixel keys (4 each)
+DF64_OPS_PER_WORD = 117   # FP32 operations of the double-float per-word map: w = v + gamma
+                          # (2 double-float sums, 11 each), |w|^2 (16), the reciprocal's Newton
+                          # step (7), the two numerators (dot products, 19 each), a + b c for
+                          # the two coordinates (15 each), and the two pixel keys (2 each)
 SMS = 152
 FP32_LANES_PER_SM = 128
 FP64_LANES_PER_SM = 2

@@ -68,7 +68,7 @@ typedef enum {
                     value an unevaluated sum of two floats, about 48 significant bits,
                     error-free sums and products built from FP32 adds and fused
                     multiply-adds), giving word values within the FP64 tolerance
-                    (1e-9 relative) at FP32-pipe speed, 127 FP32 operations per word.  Prefixes whose pole form is
+                    (1e-9 relative) at FP32-pipe speed, 117 FP32 operations per word.  Prefixes whose pole form is
                     invalid or out of float range (P10 ~ 0, pixel offsets >= 2^20,
                     constants outside [1e-30, 1e30]) run in FP64.  kl_render (limit
                     set and tiling), kl_render_noalloc and kl_eval_words only; not

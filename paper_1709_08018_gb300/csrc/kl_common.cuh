@@ -942,25 +942,11 @@ __device__ __forceinline__ DD dd_add(const DD& a, const DD& b) {
   fast_two_sum2(s, e, r.hi, r.lo);
   return r;
 }
-__device__ __forceinline__ DD dd_mul(const DD& a, const DD& b) {
-  const f2 p = mul2(a.hi, b.hi);
-  f2 e = fma2(a.hi, b.hi, neg2(p));  // the rounding error of a.hi b.hi, exactly
-  e = fma2(a.hi, b.lo, e);
-  e = fma2(a.lo, b.hi, e);
-  DD r;
-  fast_two_sum2(p, e, r.hi, r.lo);
-  return r;
-}
-__device__ __forceinline__ DD dd_sqr(const DD& a) {
-  const f2 p = mul2(a.hi, a.hi);
-  f2 e = fma2(a.hi, a.hi, neg2(p));
-  e = fma2(add2(a.hi, a.hi), a.lo, e);
-  DD r;
-  fast_two_sum2(p, e, r.hi, r.lo);
-  return r;
-}
 // 1/m: the hardware seed y (about 2^-23) and one Newton step y + y (1 - m y),
-// with the residual 1 - m y formed from the exact product m.hi y: about 2^-46
+// with the residual 1 - m y formed from the exact product m.hi y: about 2^-46.
+// The result is left as the pair (y, y (1 - m y)) without renormalising: its
+// low part is below 2^-22 of the high part, which is all that its one use,
+// the products of dd_fma, needs.  7 operations.
 __device__ __forceinline__ DD dd_rcp(const DD& m) {
   float ma, mb;
   upk(m.hi, ma, mb);
@@ -969,9 +955,7 @@ __device__ __forceinline__ DD dd_rcp(const DD& m) {
   const f2 p = mul2(m.hi, y);
   const f2 pe = fma2(m.hi, y, neg2(p));       // m.hi y = p + pe
   const f2 res = sub2(sub2(sub2(one, p), pe), mul2(m.lo, y));
-  DD r;
-  fast_two_sum2(y, mul2(y, res), r.hi, r.lo);
-  return r;
+  return DD{y, mul2(y, res)};
 }
 
 // a1 b1 + a2 b2 as one sequence: the two high products and their exact
@@ -992,7 +976,9 @@ __device__ __forceinline__ DD dd_dot(const DD& a1, const DD& b1, const DD& a2, c
   fast_two_sum2(s, e, r.hi, r.lo);
   return r;
 }
-// |w|^2 = wr^2 + wi^2 in the same way
+// |w|^2 = wr^2 + wi^2 in the same way, left unrenormalised: both products are
+// >= 0, so nothing cancels and the low part stays within a few ulp of the
+// high part, which is all dd_rcp needs (16 operations)
 __device__ __forceinline__ DD dd_norm2(const DD& wr, const DD& wi) {
   const f2 p1 = mul2(wr.hi, wr.hi), p2 = mul2(wi.hi, wi.hi);
   const f2 e1 = fma2(wr.hi, wr.hi, neg2(p1)), e2 = fma2(wi.hi, wi.hi, neg2(p2));
@@ -1001,9 +987,7 @@ __device__ __forceinline__ DD dd_norm2(const DD& wr, const DD& wi) {
   e = add2(e, add2(e1, e2));
   e = fma2(add2(wr.hi, wr.hi), wr.lo, e);
   e = fma2(add2(wi.hi, wi.hi), wi.lo, e);
-  DD r;
-  fast_two_sum2(s, e, r.hi, r.lo);
-  return r;
+  return DD{s, e};
 }
 // a + b c: the product's high part summed exactly with a.hi, its error and
 // cross terms and a.lo added before one renormalisation (15 against 18)
@@ -1049,16 +1033,21 @@ __device__ __forceinline__ void uv_df2(const DfConst& K, const DD& vr, const DD&
 
 // Pixel keys 0x4B400000 + floor(u) of two double-float coordinates: floor
 // of u.hi from its rounding toward minus infinity after adding 1.5 2^23, less
-// one where u.lo takes u below that integer (the sign of the exact fraction
-// u.hi - floor(u.hi) plus u.lo, which |u.lo| <= ulp(u.hi)/2 keeps exact).
+// one where u.lo takes u below that integer.  That happens exactly when u.hi
+// is an integer and u.lo < 0: a non-integral u.hi lies at least ulp(u.hi)
+// from the integers on both sides, farther than |u.lo| <= ulp(u.hi)/2.  The
+// tests are on the bits (u.hi equal to its floor; u.lo negative, -0 not).
 // As for the mixed path, any |u| >= 2^22, infinity or NaN gives a key whose
 // column or row falls outside the image.
 __device__ __forceinline__ void floor_keys(const DD& u, uint32_t& ka, uint32_t& kb) {
   const f2 magic = 0x4B4000004B400000ull;
   const f2 t = add2_rm(u.hi, magic);
-  const f2 sl = add2(sub2(u.hi, sub2(t, magic)), u.lo);
-  ka = (uint32_t)t - ((uint32_t)sl >> 31);
-  kb = (uint32_t)(t >> 32) - ((uint32_t)(sl >> 32) >> 31);
+  const f2 fl = sub2(t, magic);  // floor(u.hi), exactly
+  const bool da = ((uint32_t)fl == (uint32_t)u.hi) & ((uint32_t)u.lo > 0x80000000u);
+  const bool db = ((uint32_t)(fl >> 32) == (uint32_t)(u.hi >> 32)) &
+                  ((uint32_t)(u.lo >> 32) > 0x80000000u);
+  ka = (uint32_t)t - (da ? 1u : 0u);
+  kb = (uint32_t)(t >> 32) - (db ? 1u : 0u);
 }
 
 // One run of n words ending in the pixel of keys (cu, cv) (absolute pixel
