@@ -927,7 +927,7 @@ def run_ours(args):
 
     line = {"metric": METRIC, "value": value, "unit": "words/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
-            "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "f64",
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config, "clocks": clocks,
             "roofline": dict(roofline64(N if world == 1 else N / world,
                                         statistics.mean(kern_ms), cfg.name),
