@@ -112,10 +112,14 @@ __global__ void __launch_bounds__(BT, 1280 / BT) render_mixed_kernel(
 // Double-float (KL_DF64): the queue holds first the FP64 fallback items (the
 // direct-form, far and out-of-float-range prefixes), then the double-float
 // items (32 prefixes x one chunk of suffix pairs), drawn per warp like the
-// mixed render's.  The per-word map is about 150 FP32 operations, so the FMA
-// pipe, not issue, bounds the loop.
+// mixed render's.  The per-word map is 117 FP32 operations in dependent
+// double-float chains, so the FMA pipe and the chains' latency, not issue,
+// bound the loop.  72 registers (7 blocks of 128 threads per SM): 2% faster
+// than at 82 registers (5 blocks) and than at 64 (8 blocks, spilling in the
+// loop); at 72 a few values are spilled per work item, not per word (local
+// loads are 0.01% of the instructions).
 template <int BT>
-__global__ void __launch_bounds__(BT, 512 / BT) render_df64_kernel(
+__global__ void __launch_bounds__(BT, 896 / BT) render_df64_kernel(
     Tables T, Plan L, View V, Work Wk, uint32_t* __restrict__ img,
     unsigned long long* counters) {
   pdl_wait();
