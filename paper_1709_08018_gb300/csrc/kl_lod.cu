@@ -29,7 +29,7 @@
 // The others expand to their children; nodes still active at level hi are
 // rendered exactly (all their words) by the mixed kernel.  Every word is
 // counted once.
-#include "kl_mlp_dev.cuh"
+#include "kl_mlp_tc.cuh"
 
 namespace {
 
@@ -325,10 +325,14 @@ __global__ void init_active_kernel(Group G, int k, uint32_t nk, Active* out, uin
   if (blockIdx.x == 0 && threadIdx.x == 0) *count = n;
 }
 
-// One level: each warp takes 32 active nodes, evaluates the network on them
-// with the tensor cores (two 16-row tiles), then prunes, expands or defers
-// each node.  stats: [0] nodes visited, [1] pruned, [2] deferred to the exact
-// render.
+// One level: each CTA takes tiles of 128 active nodes (thread t: node t of
+// the tile), scores them with the network on the tensor cores (the tcgen05
+// forward pass of kl_mlp_tc.cuh) or takes their true labels, then prunes,
+// expands or defers each node.  stats: [0] nodes visited, [1] pruned, [2]
+// deferred to the exact render.  If a tensor-core wait runs out, the CTA's
+// later scores are NaN, which prunes nothing: those nodes are still drawn
+// exactly.
+static_assert(kLodThreads == kTile, "one tile row per thread");
 __global__ void __launch_bounds__(kLodThreads) expand_kernel(
     const float* __restrict__ mlp, const uint8_t* __restrict__ labels, Group G, View V, int D,
     int k, int hi, uint32_t nk,
@@ -336,15 +340,14 @@ __global__ void __launch_bounds__(kLodThreads) expand_kernel(
     const uint32_t* __restrict__ in_count, Active* __restrict__ out, uint32_t* out_count,
     uint32_t* __restrict__ deferred, uint32_t* deferred_count, uint32_t* __restrict__ img,
     unsigned long long* counters, unsigned long long* stats) {
-  __shared__ MlpSmem S;
-  __shared__ float xs[kLodThreads / 32][32][8];
-  __shared__ float ys[kLodThreads / 32][32];
+  extern __shared__ __align__(1024) unsigned char sm[];  // kFwdSmem bytes when mlp
   // the generators, this level's representative suffix points and the view
   // as double-floats (split once per block)
   __shared__ M1 gen[4];
   __shared__ C1 reps[kReps * 4];
   __shared__ D1 vx0, vy1, vsx, vsy;
-  if (mlp) load_mlp(S, mlp);
+  Fwd F{};
+  if (mlp) F = fwd_begin(sm, mlp);  // uniform: mlp is the same for every thread
   if (threadIdx.x < 4) gen[threadIdx.x] = m1_of(load_gen(G, (int)threadIdx.x));
   if (threadIdx.x < kReps * 4) {
     const double2 v = vstar[threadIdx.x * (hi + 1) + k];
@@ -358,15 +361,14 @@ __global__ void __launch_bounds__(kLodThreads) expand_kernel(
   }
   __syncthreads();
   const float edge_f = (float)edge;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+  const int lane = threadIdx.x & 31;
   const uint32_t n = *in_count;
   unsigned long long words_sub = 1;
   for (int j = k; j < D; ++j) words_sub *= 3ull;
-  const uint64_t nwarps = (uint64_t)gridDim.x * (kLodThreads / 32);
   unsigned long long visited = 0, pruned = 0, defer = 0, inw = 0, drop = 0;
-  for (uint64_t tile = blockIdx.x * (uint64_t)(kLodThreads / 32) + warp; tile * 32 < n;
-       tile += nwarps) {
-    const uint64_t e = tile * 32 + lane;
+  // the tile loop is uniform over the CTA (the forward pass synchronises it)
+  for (uint64_t tile = blockIdx.x; tile * kLodThreads < n; tile += gridDim.x) {
+    const uint64_t e = tile * kLodThreads + threadIdx.x;
     const bool valid = e < n;
     Active a;
     if (valid) a = in[e];
@@ -374,22 +376,7 @@ __global__ void __launch_bounds__(kLodThreads) expand_kernel(
     if (mlp) {
       float f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
       if (valid) node_features_df(m1_load(a), f);
-      for (int j = 0; j < 8; ++j) xs[warp][lane][j] = f[j];
-      __syncwarp();
-      for (int half = 0; half < 2; ++half) {
-        const int ra = 16 * half + g, rb = ra + 8;
-        const uint32_t xa0 = pack_bf16(xs[warp][ra][2 * c], xs[warp][ra][2 * c + 1]);
-        const uint32_t xa1 = pack_bf16(xs[warp][rb][2 * c], xs[warp][rb][2 * c + 1]);
-        Tile T;
-        forward_tile(S, xa0, xa1, T);
-        if (c == 0) {
-          ys[warp][ra] = T.y0;
-          ys[warp][rb] = T.y1;
-        }
-      }
-      __syncwarp();
-      y = ys[warp][lane];
-      __syncwarp();
+      y = fwd_tile(F, f);
     } else {
       y = valid ? (float)labels[a.slot] : 0.0f;  // the level's true labels
     }
@@ -429,7 +416,7 @@ __global__ void __launch_bounds__(kLodThreads) expand_kernel(
       }
     }
     // output slots, one atomic per warp and list (all lanes take part: the
-    // tile loop is uniform over the warp)
+    // tile loop is uniform over the CTA)
     const unsigned be = __ballot_sync(0xFFFFFFFFu, action == 1);
     const unsigned bd = __ballot_sync(0xFFFFFFFFu, action == 2);
     uint32_t base_e = 0, base_d = 0;
@@ -473,6 +460,7 @@ __global__ void __launch_bounds__(kLodThreads) expand_kernel(
     if (inw) atomicAdd(counters + KL_CNT_IN_WINDOW, inw);
     if (drop) atomicAdd(counters + KL_CNT_DROPPED, drop);
   }
+  if (mlp) fwd_end(F);
 }
 
 // Culled exact render of the deferred level-hi nodes (the culling of
@@ -807,9 +795,13 @@ int render_lod_impl(const kl_params* p, uint32_t lo, uint32_t hi, const float* d
   init_active_kernel<<<grid_for(4ull * P.p3[lo], 128, 8), 128, 0, s>>>(G, (int)lo, P.p3[lo],
                                                                         act[0], counts + lo);
   if (check_launch() != KL_OK) return KL_ECUDA;
+  if (d_mlp && cudaFuncSetAttribute(expand_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kFwdSmem) != cudaSuccess)
+    return KL_ECUDA;
   for (int k = (int)lo; k <= (int)hi; ++k) {
     const int cur = (k - (int)lo) & 1;
-    expand_kernel<<<grid_for(4ull * P.p3[k], kLodThreads, 4), kLodThreads, 0, s>>>(
+    expand_kernel<<<grid_for(4ull * P.p3[k], kLodThreads, 3), kLodThreads,
+                    d_mlp ? kFwdSmem : 0u, s>>>(
         d_mlp, d_labels ? d_labels + P.base[k] : nullptr, G, V, P.D, k, (int)hi, P.p3[k],
         d_mlp ? margin : 0.0f, (double)edge, vstar, act[cur], counts + k, act[cur ^ 1],
         counts + k + 1, deferred, counts + 32, d_image, cnt, stats);

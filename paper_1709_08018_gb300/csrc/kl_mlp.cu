@@ -22,22 +22,18 @@
 //                                0..63, column 8) and db2 (rows 64..127,
 //                                column 8).
 // The transposed operands are stored MN-major, so that a row-owning thread
-// writes 8 of its values with one 16-byte store.
-#include "kl_mlp_dev.cuh"
-#include "kl_tc.cuh"
+// writes 8 of its values with one 16-byte store.  The forward pass (its
+// shared-memory layout and per-tile steps) is in kl_mlp_tc.cuh, shared with
+// the pruned render's scoring.
+#include "kl_mlp_tc.cuh"
 
 namespace {
 
-constexpr int kTile = 128;                        // rows per tile = TMEM lanes = threads
-constexpr long long kWaitCycles = 2000000000ll;   // bound on an MMA wait (about a second)
-
-// Shared memory (bytes from a 1024-aligned base).  BF16 tiles (kl_tc.cuh):
-// K-major where the threads own the rows of the tile (the layer inputs) or
-// where the tile is staged once (the weights), MN-major where a thread owns
-// one K index (the row of the batch) of the gradient products' operands.
-// LBO = 16 x (rows, or MN extent) in both cases.
-constexpr uint32_t kLboW = 64 * 16;           // weight tiles, 64 rows
-constexpr uint32_t kLboRow = kTile * 16;      // X, H1, dH2: 128 rows, row-wise
+// Training kernel's shared memory (bytes from a 1024-aligned base).  BF16
+// tiles (kl_tc.cuh): K-major where the threads own the rows of the tile (the
+// layer inputs) or where the tile is staged once (the weights), MN-major
+// where a thread owns one K index (the row of the batch) of the gradient
+// products' operands.  LBO = 16 x (rows, or MN extent) in both cases.
 constexpr uint32_t kLboA = kTile * 16;        // [H1^T; H2^T], [dH1^T; dH2^T]: M = 128, MN-major
 constexpr uint32_t kLboB1 = 80 * 16;          // [dH2 | dy | 0]: N = 80, MN-major
 constexpr uint32_t kLboB2 = 16 * 16;          // [X | 1 | 0]: N = 16, MN-major
@@ -58,28 +54,11 @@ constexpr uint32_t SM_RED = SM_PAR + 3 * kHid * 4; // per-warp loss and db3
 constexpr uint32_t SM_BAR = SM_RED + 32;           // mbarrier, TMEM address
 constexpr uint32_t kGradSmem = SM_BAR + 16;
 
-// forward kernel
-constexpr uint32_t FW_W1 = 0;
-constexpr uint32_t FW_W2 = FW_W1 + 2 * kLboW;
-constexpr uint32_t FW_X = FW_W2 + 8 * kLboW;
-constexpr uint32_t FW_H1 = FW_X + 2 * kLboRow;
-constexpr uint32_t FW_PAR = FW_H1 + 8 * kLboRow;   // b1, b2, w3
-constexpr uint32_t FW_BAR = FW_PAR + 3 * kHid * 4;
-// 64 KB per CTA keeps at most 3 CTAs (3 x 128 TMEM columns) on an SM, so a
-// TMEM allocation never waits for another CTA
-constexpr uint32_t kFwdSmem = 64 * 1024;
-static_assert(FW_BAR + 16 <= kFwdSmem, "forward shared memory");
 static_assert(kGradSmem <= 227 * 1024, "training shared memory");
 
-// TMEM columns: layer outputs and dH1 (64 each), the two gradient accumulators.
-constexpr uint32_t TD1 = 0, TD2 = 64, TWA = 128, TWB = 224;
-
-
-// Eight values as one 16-byte chunk of BF16.
-__device__ __forceinline__ uint4 pack8(const float* v) {
-  return make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
-                    pack_bf16(v[6], v[7]));
-}
+// TMEM columns beyond the layer outputs TD1, TD2 (dH1 reuses TD1): the two
+// gradient accumulators.
+constexpr uint32_t TWA = 128, TWB = 224;
 
 // MN elements m .. m+7 (m a multiple of 8) of K index t of an MN-major tile.
 __device__ __forceinline__ void st_mn8(unsigned char* base, uint32_t lbo, int m, int t,
@@ -87,103 +66,16 @@ __device__ __forceinline__ void st_mn8(unsigned char* base, uint32_t lbo, int m,
   *reinterpret_cast<uint4*>(base + tc_off_mn(m, t, lbo)) = pack8(v);
 }
 
-// Weights as BF16 B operands (K-major, 16-byte chunks of 8 K elements: one
-// store per chunk), biases and w3 in FP32.
-__device__ void stage_weights(unsigned char* sm, uint32_t w1, uint32_t w2, int w2t,
-                              uint32_t par, const float* __restrict__ P) {
-  // W1 as B of layer 1: (n = h, k = f), f = 0..15 with zeros from 8 on
-  for (int i = threadIdx.x; i < kHid * 2; i += blockDim.x) {
-    const int h = i % kHid, kc = i / kHid;
-    float v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = kc == 0 ? P[OFF_W1 + j * kHid + h] : 0.0f;
-    *reinterpret_cast<uint4*>(sm + w1 + tc_off(h, 8 * kc, kLboW)) = pack8(v);
-  }
-  // W2 as B of layer 2: (n = out, k = in), 8 inputs per chunk (a column of W2,
-  // read with consecutive threads on consecutive outputs)
-  for (int i = threadIdx.x; i < kHid * 8; i += blockDim.x) {
-    const int out = i % kHid, kc = i / kHid;
-    float v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = P[OFF_W2 + (8 * kc + j) * kHid + out];
-    *reinterpret_cast<uint4*>(sm + w2 + tc_off(out, 8 * kc, kLboW)) = pack8(v);
-  }
-  // W2 as B of dH1 = dH2 W2^T: (n = in, k = out), 8 outputs per chunk (part of a row)
-  if (w2t >= 0)
-    for (int i = threadIdx.x; i < kHid * 8; i += blockDim.x) {
-      const int in = i / 8, kc = i % 8;
-      float v[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = P[OFF_W2 + in * kHid + 8 * kc + j];
-      *reinterpret_cast<uint4*>(sm + (uint32_t)w2t + tc_off(in, 8 * kc, kLboW)) = pack8(v);
-    }
-  float* q = reinterpret_cast<float*>(sm + par);
-  for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
-    q[i] = P[OFF_B1 + i];
-    q[kHid + i] = P[OFF_B2 + i];
-    q[2 * kHid + i] = P[OFF_W3 + i];
-  }
-}
-
-// Hand the tiles just written to the tensor cores and order the TMEM reads
-// before the next MMA: every thread fences, then the block synchronises.
-__device__ __forceinline__ void sync_for_mma() {
-  fence_smem_async();
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-}
-
-// Row t of a row-wise tile: 16 values (columns c .. c+15) as two 16-byte chunks.
-__device__ __forceinline__ void st_row16(unsigned char* base, int t, int c, const float* v) {
-  uint4 a, b;
-  a.x = pack_bf16(v[0], v[1]); a.y = pack_bf16(v[2], v[3]);
-  a.z = pack_bf16(v[4], v[5]); a.w = pack_bf16(v[6], v[7]);
-  b.x = pack_bf16(v[8], v[9]); b.y = pack_bf16(v[10], v[11]);
-  b.z = pack_bf16(v[12], v[13]); b.w = pack_bf16(v[14], v[15]);
-  *reinterpret_cast<uint4*>(base + tc_off(t, c, kLboRow)) = a;
-  *reinterpret_cast<uint4*>(base + tc_off(t, c + 8, kLboRow)) = b;
-}
-
-// Wait for the MMAs committed last (block-uniform result); on a timeout the
-// caller stops issuing work.
-__device__ __forceinline__ bool mma_done(uint64_t* bar, uint32_t& phase) {
-  const bool ok = mbar_wait(bar, phase, kWaitCycles);
-  phase ^= 1u;
-  return __syncthreads_and(ok) != 0;
-}
-
+// y = network(x) for n rows of 8 features, one 128-row tile per CTA at a time.
 __global__ void __launch_bounds__(kTile, 1) mlp_forward_kernel(const float* __restrict__ P,
                                                                const float* __restrict__ x,
                                                                uint64_t n,
                                                                float* __restrict__ y) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  const int t = threadIdx.x, warp = t >> 5;
-  const float* b1 = reinterpret_cast<const float*>(sm + FW_PAR);
-  const float* b2 = b1 + kHid;
-  const float* w3 = b2 + kHid;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + FW_BAR);
-  uint32_t* slot = reinterpret_cast<uint32_t*>(sm + FW_BAR + 8);
-  stage_weights(sm, FW_W1, FW_W2, -1, FW_PAR, P);
-  const float b3 = P[OFF_B3];
-  *reinterpret_cast<uint4*>(sm + FW_X + tc_off(t, 8, kLboRow)) = make_uint4(0u, 0u, 0u, 0u);
-  if (t == 0) mbar_init(bar, 1);
-  if (warp == 0) tc_alloc(slot, 128);
-  sync_for_mma();
-  const uint32_t tm = *slot;
-  const uint32_t la = tm + ((uint32_t)(warp * 32) << 16);
-  const uint32_t id64 = tc_idesc_bf16(128, 64);
-  const uint32_t aX = smem_u32(sm + FW_X), aH1 = smem_u32(sm + FW_H1);
-  const uint32_t aW1 = smem_u32(sm + FW_W1), aW2 = smem_u32(sm + FW_W2);
-  uint32_t phase = 0;
-  bool ok = true;
+  Fwd F = fwd_begin(sm, P);
   const uint64_t tiles = (n + kTile - 1) / kTile;
   for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const uint64_t row = tile * kTile + t;
-    if (!ok) {   // an MMA did not finish: mark this CTA's outputs
-      if (row < n) y[row] = __int_as_float(0x7FC00000);
-      continue;
-    }
+    const uint64_t row = tile * kTile + threadIdx.x;
     float xv[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     if (row < n) {
       const float4 u = *reinterpret_cast<const float4*>(x + row * kIn);
@@ -191,58 +83,11 @@ __global__ void __launch_bounds__(kTile, 1) mlp_forward_kernel(const float* __re
       xv[0] = u.x; xv[1] = u.y; xv[2] = u.z; xv[3] = u.w;
       xv[4] = w.x; xv[5] = w.y; xv[6] = w.z; xv[7] = w.w;
     }
-    *reinterpret_cast<uint4*>(sm + FW_X + tc_off(t, 0, kLboRow)) =
-        make_uint4(pack_bf16(xv[0], xv[1]), pack_bf16(xv[2], xv[3]), pack_bf16(xv[4], xv[5]),
-                   pack_bf16(xv[6], xv[7]));
-    sync_for_mma();
-    if (t == 0) {
-      tc_mma(tm + TD1, tc_desc(aX, kLboRow), tc_desc(aW1, kLboW), id64, 0u);
-      tc_commit(bar);
-    }
-    ok = mma_done(bar, phase);
-    if (!ok) {
-      if (row < n) y[row] = __int_as_float(0x7FC00000);
-      continue;
-    }
-    tc_fence_after();
-#pragma unroll
-    for (int c = 0; c < kHid; c += 16) {
-      float v[16];
-      tc_ld16(la + TD1 + c, v);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j] + b1[c + j], 0.0f);
-      st_row16(sm + FW_H1, t, c, v);
-    }
-    sync_for_mma();
-    if (t == 0) {
-#pragma unroll
-      for (int ks = 0; ks < 4; ++ks)
-        tc_mma(tm + TD2, tc_desc(aH1 + 2 * ks * kLboRow, kLboRow),
-               tc_desc(aW2 + 2 * ks * kLboW, kLboW), id64, ks > 0 ? 1u : 0u);
-      tc_commit(bar);
-    }
-    ok = mma_done(bar, phase);
-    if (!ok) {
-      if (row < n) y[row] = __int_as_float(0x7FC00000);
-      continue;
-    }
-    tc_fence_after();
-    float acc = 0.0f;
-#pragma unroll
-    for (int c = 0; c < kHid; c += 16) {
-      float v[16];
-      tc_ld16(la + TD2 + c, v);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) acc += fmaxf(v[j] + b2[c + j], 0.0f) * w3[c + j];
-    }
-    if (row < n) y[row] = acc + b3;
-    tc_fence_before();
+    // NaN for the whole CTA's rows once an MMA has not finished
+    const float v = fwd_tile(F, xv);
+    if (row < n) y[row] = v;
   }
-  if (!ok) mbar_wait(bar, phase ^ 1u, kWaitCycles);   // let a late MMA finish first
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (warp == 0) tc_dealloc(tm, 128);
+  fwd_end(F);
 }
 
 // Gradients are summed in a fixed order, so that a training run repeats
