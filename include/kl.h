@@ -403,7 +403,10 @@ KL_API size_t kl_lod_render_bytes(const kl_params* p, uint32_t lo, uint32_t hi);
  * for (kl_lod_labels), a right prediction keeps every word in its own pixel.
  * Every word is counted once (in d_counters, as kl_render).  d_stats (4
  * uint64): nodes scored, nodes pruned, level-hi nodes rendered exactly, 0.
- * KL_EINVAL unless 0 <= edge < 1/2. */
+ * The scores come from the same tensor-core forward pass as kl_mlp_forward,
+ * 128 nodes per tile; if a tensor-core wait runs out (bounded at about a
+ * second), the affected scores are NaN, which prunes nothing, so those nodes
+ * are still drawn exactly.  KL_EINVAL unless 0 <= edge < 1/2. */
 KL_API int kl_render_lod(const kl_params* p, uint32_t lo, uint32_t hi, const float* d_mlp,
                          float margin, float edge, uint32_t* d_image, uint64_t* d_counters,
                          uint64_t* d_stats, void* d_workspace, size_t workspace_bytes,
