@@ -732,6 +732,33 @@ def events(stream, n):
     return ev
 
 
+def l2_atomic_peak(dev, n_adds: int = 1 << 26, image_words: int = 64 << 20, reps: int = 5):
+    """Measured ceiling for the image adds: 32-bit atomic adds per second at
+    uniformly random addresses of a 256 MiB image (torch's index_add_, one
+    atomic add per index), the median of `reps` timed calls after 3 warm-ups.
+    The render's adds come in runs and hit far fewer lines, so this is the
+    pessimistic (scattered) ceiling the atomic fraction is quoted against."""
+    import torch
+    img = torch.zeros(image_words, dtype=torch.int32, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(1709)
+    idx = torch.randint(0, image_words, (n_adds,), device=dev, generator=g)
+    ones = torch.ones(n_adds, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        img.index_add_(0, idx, ones)
+    ev = events(stream, 2 * reps)
+    for k in range(reps):
+        ev[2 * k].record(stream)
+        img.index_add_(0, idx, ones)
+        ev[2 * k + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    ms = statistics.median(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps))
+    assert int(img.sum(dtype=torch.int64)) == (3 + reps) * n_adds
+    del img, idx, ones
+    return n_adds / (ms / 1000.0)
+
+
 def timed_render(kl, r, flush, stream, K, dev, image_sum=None):
     """K renders, each after an L2 flush, timed with CUDA events on `stream`
     (step = the kl_render call, plus the image sum when given) and with the
@@ -991,6 +1018,18 @@ def run_ours(args):
         line["df64_nearcusp_d20"] = df3
         line["mixed_nearcusp_d20"] = mixed3
         line["mixed_gasket_d18"] = mixed2
+        # the image adds against a measured ceiling (scattered 32-bit atomic adds)
+        peak = l2_atomic_peak(dev)
+        line["l2_atomics"] = {
+            "peak_per_s": peak,
+            "peak_kind": "measured: torch index_add_ of 2^26 int32 adds at uniformly random "
+                         "addresses of a 256 MiB buffer (one atomic add each)",
+            "fp64_nearcusp_d20_frac": line["atomics_per_s"] / peak,
+            "mixed_nearcusp_d20_frac": mixed3["atomics_per_s"] / peak,
+            "mixed_gasket_d18_frac": mixed2["atomics_per_s"] / peak,
+            "reading": "the ceiling is for scattered adds; the renders' adds come in runs "
+                       "and bursts on nearby lines, and their kernels are bound by the FP64 "
+                       "pipe (FP64) or by issue (mixed), not by the L2"}
         line["fp64_gasket_d18"] = fp64_2
         line["fp64_gasket_d10"] = fp64_1
         if not args.no_tiling:
