@@ -160,6 +160,8 @@ class ClockSampler:
 
 
 RENDER_SOURCES = ("paper_1709_08018_gb300/csrc/kl_common.cuh",
+                  "paper_1709_08018_gb300/csrc/kl_df.cuh", "paper_1709_08018_gb300/csrc/kl_cull.cuh",
+                  "paper_1709_08018_gb300/csrc/kl_plan.cuh",
                   "paper_1709_08018_gb300/csrc/kl_render.cu", "include/kl.h")
 
 

@@ -70,7 +70,7 @@ def _apply(p: kb.Params, knobs: Dict[str, int]) -> kb.Params:
 
 
 def default_prefix_len(depth: int, batched: bool) -> int:
-    """The library's own split (kl_common.cuh make_plan) for a depth."""
+    """The library's own split (kl_plan.cuh make_plan) for a depth."""
     if depth <= 1:
         return 1
     if batched:

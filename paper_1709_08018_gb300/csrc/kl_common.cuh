@@ -900,999 +900,9 @@ __device__ __forceinline__ void mixed_item(uint32_t item, const Work& Wk, const 
   mixed_slot_words<BBOX>(slot, u, k0, k1, L, V, T, t, words, img, B);
 }
 
-
-// ---------------------------------------------------------------------------
-// double-float per-word map (KL_DF64), two words per packed f32x2 instruction
-//
-// A value is an unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2
-// (Dekker 1971; the "double-double" arithmetic of Hida, Li and Bailey 2001,
-// here on floats): about 48 significant bits.  Sums use Knuth's two-sum and
-// Dekker's fast two-sum; products use the fused multiply-add for the exact
-// rounding error of hi * hi.  Every operation below is an FP32 add, multiply
-// or fused multiply-add, so the map runs on the FP32 pipe.
-
-__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
-  f2 d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-// both halves negated (their sign bits flipped; an integer operation)
-__device__ __forceinline__ f2 neg2(f2 a) { return a ^ 0x8000000080000000ull; }
-
-struct DD {
-  f2 hi, lo;
-};
-
-// s + e = a + b exactly (two-sum)
-__device__ __forceinline__ void two_sum2(f2 a, f2 b, f2& s, f2& e) {
-  s = add2(a, b);
-  const f2 bb = sub2(s, a);
-  e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
-}
-// s + e = a + b exactly when |a| >= |b| (fast two-sum)
-__device__ __forceinline__ void fast_two_sum2(f2 a, f2 b, f2& s, f2& e) {
-  s = add2(a, b);
-  e = sub2(b, sub2(s, a));
-}
-__device__ __forceinline__ DD dd_add(const DD& a, const DD& b) {
-  f2 s, e;
-  two_sum2(a.hi, b.hi, s, e);
-  e = add2(e, add2(a.lo, b.lo));
-  DD r;
-  fast_two_sum2(s, e, r.hi, r.lo);
-  return r;
-}
-// 1/m: the hardware seed y (about 2^-23) and one Newton step y + y (1 - m y),
-// with the residual 1 - m y formed from the exact product m.hi y: about 2^-46.
-// The result is left as the pair (y, y (1 - m y)) without renormalising: its
-// low part is below 2^-22 of the high part, which is all that its one use,
-// the products of dd_fma, needs.  7 operations.
-__device__ __forceinline__ DD dd_rcp(const DD& m) {
-  float ma, mb;
-  upk(m.hi, ma, mb);
-  const f2 y = pk(rcp32(ma), rcp32(mb));
-  const f2 one = 0x3F8000003F800000ull;
-  const f2 p = mul2(m.hi, y);
-  const f2 pe = fma2(m.hi, y, neg2(p));       // m.hi y = p + pe
-  const f2 res = sub2(sub2(sub2(one, p), pe), mul2(m.lo, y));
-  return DD{y, mul2(y, res)};
-}
-
-// a1 b1 + a2 b2 as one sequence: the two high products and their exact
-// errors, an exact sum of the products, then the cross terms added to the
-// error before one renormalisation (19 operations against 25 for two
-// products and a sum; the same error order, about 2^-48 of |a1 b1| + |a2 b2|)
-__device__ __forceinline__ DD dd_dot(const DD& a1, const DD& b1, const DD& a2, const DD& b2) {
-  const f2 p1 = mul2(a1.hi, b1.hi), p2 = mul2(a2.hi, b2.hi);
-  const f2 e1 = fma2(a1.hi, b1.hi, neg2(p1)), e2 = fma2(a2.hi, b2.hi, neg2(p2));
-  f2 s, e;
-  two_sum2(p1, p2, s, e);
-  e = add2(e, add2(e1, e2));
-  e = fma2(a1.hi, b1.lo, e);
-  e = fma2(a1.lo, b1.hi, e);
-  e = fma2(a2.hi, b2.lo, e);
-  e = fma2(a2.lo, b2.hi, e);
-  DD r;
-  fast_two_sum2(s, e, r.hi, r.lo);
-  return r;
-}
-// |w|^2 = wr^2 + wi^2 in the same way, left unrenormalised: both products are
-// >= 0, so nothing cancels and the low part stays within a few ulp of the
-// high part, which is all dd_rcp needs (16 operations)
-__device__ __forceinline__ DD dd_norm2(const DD& wr, const DD& wi) {
-  const f2 p1 = mul2(wr.hi, wr.hi), p2 = mul2(wi.hi, wi.hi);
-  const f2 e1 = fma2(wr.hi, wr.hi, neg2(p1)), e2 = fma2(wi.hi, wi.hi, neg2(p2));
-  f2 s, e;
-  two_sum2(p1, p2, s, e);
-  e = add2(e, add2(e1, e2));
-  e = fma2(add2(wr.hi, wr.hi), wr.lo, e);
-  e = fma2(add2(wi.hi, wi.hi), wi.lo, e);
-  return DD{s, e};
-}
-// a + b c: the product's high part summed exactly with a.hi, its error and
-// cross terms and a.lo added before one renormalisation (15 against 18)
-__device__ __forceinline__ DD dd_fma(const DD& a, const DD& b, const DD& c) {
-  const f2 p = mul2(b.hi, c.hi);
-  f2 e = fma2(b.hi, c.hi, neg2(p));
-  e = fma2(b.hi, c.lo, e);
-  e = fma2(b.lo, c.hi, e);
-  f2 s, f;
-  two_sum2(a.hi, p, s, f);
-  f = add2(f, add2(e, a.lo));
-  DD r;
-  fast_two_sum2(s, f, r.hi, r.lo);
-  return r;
-}
-
-// Pole-form constants of a prefix as double-floats, each in both halves.
-struct DfConst {
-  DD k[8];  // gr, gi, ax, ay, c1, c2, c3, c4
-};
-__device__ __forceinline__ DfConst df_const(const PreDF& c) {
-  DfConst K;
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    K.k[q].hi = pk(c.h[q], c.h[q]);
-    K.k[q].lo = pk(c.l[q], c.l[q]);
-  }
-  return K;
-}
-
-// Pixel coordinates (u, v) of two words with suffix points (vr, vi):
-// u = ax + (c1 wr + c2 wi) / |w|^2, v = ay + (c3 wr + c4 wi) / |w|^2, w = v + gamma.
-__device__ __forceinline__ void uv_df2(const DfConst& K, const DD& vr, const DD& vi, DD& u,
-                                       DD& v) {
-  const DD wr = dd_add(vr, K.k[0]);
-  const DD wi = dd_add(vi, K.k[1]);
-  const DD r = dd_rcp(dd_norm2(wr, wi));
-  const DD tx = dd_dot(K.k[4], wr, K.k[5], wi);
-  const DD ty = dd_dot(K.k[6], wr, K.k[7], wi);
-  u = dd_fma(K.k[2], tx, r);
-  v = dd_fma(K.k[3], ty, r);
-}
-
-// Pixel keys 0x4B400000 + floor(u) of two double-float coordinates: floor
-// of u.hi from its rounding toward minus infinity after adding 1.5 2^23, less
-// one where u.lo takes u below that integer.  That happens exactly when u.hi
-// is an integer and u.lo < 0: a non-integral u.hi lies at least ulp(u.hi)
-// from the integers on both sides, farther than |u.lo| <= ulp(u.hi)/2.  The
-// tests are on the bits (u.hi equal to its floor; u.lo negative, -0 not).
-// As for the mixed path, any |u| >= 2^22, infinity or NaN gives a key whose
-// column or row falls outside the image.
-__device__ __forceinline__ void floor_keys(const DD& u, uint32_t& ka, uint32_t& kb) {
-  const f2 magic = 0x4B4000004B400000ull;
-  const f2 t = add2_rm(u.hi, magic);
-  const f2 fl = sub2(t, magic);  // floor(u.hi), exactly
-  const bool da = ((uint32_t)fl == (uint32_t)u.hi) & ((uint32_t)u.lo > 0x80000000u);
-  const bool db = ((uint32_t)(fl >> 32) == (uint32_t)(u.hi >> 32)) &
-                  ((uint32_t)(u.lo >> 32) > 0x80000000u);
-  ka = (uint32_t)t - (da ? 1u : 0u);
-  kb = (uint32_t)(t >> 32) - (db ? 1u : 0u);
-}
-
-// One run of n words ending in the pixel of keys (cu, cv) (absolute pixel
-// keys: col = cu - 0x4B400000).
-__device__ __forceinline__ void flush_key(uint32_t cu, uint32_t cv, uint32_t n, const View& V,
-                                          Tally& t, uint32_t* __restrict__ img) {
-  const uint32_t col = cu - 0x4B400000u, row = cv - 0x4B400000u;
-  if (n && col < V.W && row < V.H) {
-    atomicAdd(img + row * V.W + col, n);
-    ++t.atomics;
-    t.in_window += n;
-  }
-}
-
-// Double-float words of prefix slot `slot` on suffix point pairs [k0, k1) of
-// first letter u, with the run-length splat of mixed_slot_words on pixel keys.
-__device__ __forceinline__ void df64_slot_words(uint32_t slot, int u, uint32_t k0, uint32_t k1,
-                                                const Plan& L, const View& V, const Tables& T,
-                                                Tally& t, uint32_t& words,
-                                                uint32_t* __restrict__ img) {
-  const DfConst K = df_const(T.predf[slot]);
-  const float4* src = T.sufdf + 2ull * (size_t)u * L.npairs;
-  t.flush(img);
-  t.cur = -1;
-  uint32_t cu = 0, cv = 0, run = 0;  // keys (0, 0): no in-window pixel
-  uint32_t e_run = k0;
-  for (uint32_t e = k0; e < k1; ++e) {
-    const float4 a = __ldg(src + 2 * e), b = __ldg(src + 2 * e + 1);
-    const DD vr = {pk(a.x, a.y), pk(a.z, a.w)}, vi = {pk(b.x, b.y), pk(b.z, b.w)};
-    DD U, Vv;
-    uv_df2(K, vr, vi, U, Vv);
-    uint32_t ua, ub, va, vb;
-    floor_keys(U, ua, ub);
-    floor_keys(Vv, va, vb);
-    if (!((ua == cu) & (ub == cu) & (va == cv) & (vb == cv))) {
-      const bool a_in = (ua == cu) & (va == cv);
-      const bool ab = (ua == ub) & (va == vb);
-      run += 2u * (e - e_run) + (a_in ? 1u : 0u);
-      e_run = e + 1;
-      flush_key(cu, cv, run, V, t, img);
-      if (!a_in && !ab) flush_key(ua, va, 1u, V, t, img);  // word a on its own
-      run = (!a_in && ab) ? 2u : 1u;
-      cu = ub;
-      cv = vb;
-    }
-  }
-  run += 2u * (k1 - e_run);
-  flush_key(cu, cv, run, V, t, img);
-  words += min(2u * k1, L.ns) - 2u * k0;
-}
-
-// One double-float item: this thread's prefix on one chunk of suffix pairs.
-template <int BT>
-__device__ __forceinline__ void df64_item(uint32_t item, const Work& Wk, const Plan& L,
-                                          const View& V, const Tables& T, Tally& t,
-                                          uint32_t& words, uint32_t* __restrict__ img) {
-  int x, u;
-  uint32_t pb, c;
-  item_of(item, Wk, x, u, pb, c);
-  const uint32_t k = pb * BT + (threadIdx.x % BT);
-  if (k >= L.nr) return;
-  const uint32_t slot = (uint32_t)x * L.np + L.r0 + k;
-  if (T.flags[slot] & kFallback) return;
-  const uint32_t k0 = c * Wk.chunk, k1 = min(L.npairs, k0 + Wk.chunk);
-  df64_slot_words(slot, u, k0, k1, L, V, T, t, words, img);
-}
-
-// ---------------------------------------------------------------------------
-// scalar double-floats: one value per thread (the level-of-detail expansion,
-// where each lane holds its own node matrix).  The same arithmetic as the
-// packed pairs above.
-
-struct D1 {
-  float hi, lo;
-};
-
-__device__ __forceinline__ D1 d1_of(double d) {
-  D1 r;
-  split_df(d, r.hi, r.lo);
-  return r;
-}
-__device__ __forceinline__ D1 d1_neg(D1 a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ void two_sum1(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-__device__ __forceinline__ D1 fast_two_sum1(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ D1 d1_add(D1 a, D1 b) {
-  float s, e;
-  two_sum1(a.hi, b.hi, s, e);
-  return fast_two_sum1(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
-}
-__device__ __forceinline__ D1 d1_mul(D1 a, D1 b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = __fmaf_rn(a.hi, b.hi, -p);
-  e = __fmaf_rn(a.hi, b.lo, e);
-  e = __fmaf_rn(a.lo, b.hi, e);
-  return fast_two_sum1(p, e);
-}
-// sum of N products a_i b_i: high products and their exact errors, an exact
-// running sum of the products, the cross terms, one renormalisation
-template <int N>
-__device__ __forceinline__ D1 d1_dot(const D1 (&a)[N], const D1 (&b)[N]) {
-  float s = __fmul_rn(a[0].hi, b[0].hi);
-  float e = __fmaf_rn(a[0].hi, b[0].hi, -s);
-#pragma unroll
-  for (int i = 1; i < N; ++i) {
-    const float p = __fmul_rn(a[i].hi, b[i].hi);
-    e = __fadd_rn(e, __fmaf_rn(a[i].hi, b[i].hi, -p));
-    float t;
-    two_sum1(s, p, s, t);
-    e = __fadd_rn(e, t);
-  }
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    e = __fmaf_rn(a[i].hi, b[i].lo, e);
-    e = __fmaf_rn(a[i].lo, b[i].hi, e);
-  }
-  return fast_two_sum1(s, e);
-}
-// 1/m: hardware seed and one Newton step with the residual from m.hi y exactly
-__device__ __forceinline__ D1 d1_rcp(D1 m) {
-  const float y = rcp32(m.hi);
-  const float p = __fmul_rn(m.hi, y);
-  const float pe = __fmaf_rn(m.hi, y, -p);
-  const float res = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, p), pe), __fmul_rn(m.lo, y));
-  return fast_two_sum1(y, __fmul_rn(y, res));
-}
-
-struct C1 {
-  D1 re, im;
-};
-struct M1 {
-  C1 p, q, r, s;
-};
-
-__device__ __forceinline__ M1 m1_of(const M2& a) {
-  return {{d1_of(a.p.re), d1_of(a.p.im)}, {d1_of(a.q.re), d1_of(a.q.im)},
-          {d1_of(a.r.re), d1_of(a.r.im)}, {d1_of(a.s.re), d1_of(a.s.im)}};
-}
-// a b + c d (complex), each part one 4-term dot product
-__device__ __forceinline__ C1 c1_mul_add(C1 a, C1 b, C1 c, C1 d) {
-  const D1 xr[4] = {a.re, d1_neg(a.im), c.re, d1_neg(c.im)};
-  const D1 yr[4] = {b.re, b.im, d.re, d.im};
-  const D1 xi[4] = {a.re, a.im, c.re, c.im};
-  const D1 yi[4] = {b.im, b.re, d.im, d.re};
-  return {d1_dot<4>(xr, yr), d1_dot<4>(xi, yi)};
-}
-__device__ __forceinline__ M1 m1_mul(const M1& a, const M1& b) {
-  return {c1_mul_add(a.p, b.p, a.q, b.r), c1_mul_add(a.p, b.q, a.q, b.s),
-          c1_mul_add(a.r, b.p, a.s, b.r), c1_mul_add(a.r, b.q, a.s, b.s)};
-}
-// a v + b (complex)
-__device__ __forceinline__ C1 c1_affine(C1 a, C1 v, C1 b) {
-  const D1 one = {1.0f, 0.0f};
-  const D1 xr[3] = {a.re, d1_neg(a.im), b.re};
-  const D1 yr[3] = {v.re, v.im, one};
-  const D1 xi[3] = {a.re, a.im, b.im};
-  const D1 yi[3] = {v.im, v.re, one};
-  return {d1_dot<3>(xr, yr), d1_dot<3>(xi, yi)};
-}
-// P(v) = (p v + q) / (r v + s) as n conj(m) / |m|^2
-__device__ __forceinline__ C1 m1_apply(const M1& P, C1 v) {
-  const C1 n = c1_affine(P.p, v, P.q), m = c1_affine(P.r, v, P.s);
-  const D1 mm[2] = {m.re, m.im};
-  const D1 k = d1_rcp(d1_dot<2>(mm, mm));
-  const D1 ar[2] = {n.re, n.im}, br[2] = {m.re, m.im};
-  const D1 ai[2] = {n.im, d1_neg(n.re)}, bi[2] = {m.re, m.im};
-  return {d1_mul(d1_dot<2>(ar, br), k), d1_mul(d1_dot<2>(ai, bi), k)};
-}
-
-// ---------------------------------------------------------------------------
-// culled renders (kl_params.cull), shared by the single and batched renders
-//
-// The suffix points of one first letter come in aligned blocks of 3^j
-// consecutive points: the points of one subtree, which share all but their
-// last j letters and so lie close together.  Blocks of 9 .. 729 points form a
-// tree (a block's children are the three blocks of a third its size inside
-// it), and the disk pass (cull_disk_unit) bounds every block by a disk.  A
-// prefix in pole form, (u, v) = M (w_re, w_im) / |w|^2 + (ax, ay) with
-// w = v + gamma, sends a disk D(c, rho) with |c + gamma| > rho onto a set
-// inside the disk of center M (c + gamma) / q + (ax, ay) and radius
-// |M| rho / q, q = |c + gamma|^2 - rho^2
-// (inversion maps a disk clear of the pole onto a disk; M is linear with
-// operator norm |M|).  When that disk, widened by a margin larger than the
-// rounding error of the per-word map, lies inside one pixel or wholly outside
-// the window, every word of the block lands there and the block is tallied
-// with one add; otherwise its three children are tested, and a failing block
-// of the smallest size is evaluated word by word.  Tests run 32 to a warp, one
-// per lane, from a per-warp stack of (prefix, level, block) entries in shared
-// memory; word-by-word blocks wait in a second per-warp queue until 32 are
-// there.
-
-constexpr int kCullStack = 384;  // per-warp test stack (entries)
-constexpr int kLeafQueue = 64;   // per-warp queue of blocks left to the per-word path
-
-// Operator norm of the 2x2 real matrix [[c1, c2], [c3, c4]] (its largest
-// singular value), slightly rounded up.
-__device__ __forceinline__ float opnorm32(float c1, float c2, float c3, float c4) {
-  const float a = sqrtf(fmaf(c1 + c4, c1 + c4, (c2 - c3) * (c2 - c3)));
-  const float b = sqrtf(fmaf(c1 - c4, c1 - c4, (c2 + c3) * (c2 + c3)));
-  return 0.5f * (a + b) * (1.0f + 0x1p-16f);
-}
-__device__ __forceinline__ double opnorm64(double c1, double c2, double c3, double c4) {
-  const double a = sqrt(fma(c1 + c4, c1 + c4, (c2 - c3) * (c2 - c3)));
-  const double b = sqrt(fma(c1 - c4, c1 - c4, (c2 + c3) * (c2 + c3)));
-  return 0.5 * (a + b) * (1.0 + 0x1p-40);
-}
-
-constexpr int kUncertified = -2;
-
-// Certified pixel of a whole block under an FP32 prefix (local frame, as the
-// mixed per-word map): the pixel id, -1 (every word outside the window), or
-// kUncertified.  The margin, 2^-11 px + 2^-20 of the offsets from alpha's
-// pixel, is far above the per-word map's rounding error; the interval ends are
-// rounded outwards before flooring, so a certified block never straddles a
-// pixel edge.
-__device__ __forceinline__ int block_pixel32(const Pre32& k, float nrm, float4 D, const View& V) {
-  const float c0r = D.x + k.gr, c0i = D.y + k.gi;
-  const float n2 = fmaf(c0r, c0r, c0i * c0i), rho2 = D.z * D.z;
-  if (!(4.0f * rho2 < n2)) return kUncertified;  // near the pole, or not finite
-  const float rq = rcp32(n2 - rho2);
-  const float X = fmaf(fmaf(k.c1, c0r, k.c2 * c0i), rq, k.axf);
-  const float Y = fmaf(fmaf(k.c3, c0r, k.c4 * c0i), rq, k.ayf);
-  const float R = nrm * D.z * rq;
-  const float m = R + fmaf(fabsf(X) + fabsf(Y) + R, 0x1p-20f, 0x1p-11f);
-  if (m < 0.5f && fabsf(X) < 0x1p21f && fabsf(Y) < 0x1p21f) {
-    const float magic = 12582912.0f;  // 1.5 * 2^23: t bits - 0x4B400000 = floor
-    const int xl = __float_as_int(__fadd_rd(__fsub_rd(X, m), magic));
-    const int xh = __float_as_int(__fadd_rd(__fadd_ru(X, m), magic));
-    const int yl = __float_as_int(__fadd_rd(__fsub_rd(Y, m), magic));
-    const int yh = __float_as_int(__fadd_rd(__fadd_ru(Y, m), magic));
-    if (xl == xh && yl == yh) {
-      const int col = xl - k.kx, row = yl - k.ky;
-      return ((uint32_t)col < V.W && (uint32_t)row < V.H) ? row * (int)V.W + col : -1;
-    }
-  }
-  // wholly outside the window (one pixel of slack covers the rounding of the
-  // absolute coordinates)
-  const float Xa = X + (float)k.axi, Ya = Y + (float)k.ayi;
-  if (Xa + m < -1.0f || Xa - m > (float)V.W + 1.0f || Ya + m < -1.0f ||
-      Ya - m > (float)V.H + 1.0f)
-    return -1;
-  return kUncertified;
-}
-
-// The same in FP64 (pole-form prefixes; absolute pixel coordinates).  Margin
-// 2^-30 px + 2^-44 of the offsets from alpha.
-__device__ __forceinline__ int block_pixel64(const Pre64& k, double nrm, const Disk64& D,
-                                             const View& V) {
-  const double c0r = D.cr + k.gr, c0i = D.ci + k.gi;
-  const double n2 = fma(c0r, c0r, c0i * c0i), rho2 = D.rho * D.rho;
-  if (!(4.0 * rho2 < n2)) return kUncertified;
-  const double rq = rcp64(n2 - rho2);
-  const double ox = fma(k.c1, c0r, k.c2 * c0i) * rq, oy = fma(k.c3, c0r, k.c4 * c0i) * rq;
-  const double R = nrm * D.rho * rq;
-  const double m = R + fma(fabs(ox) + fabs(oy) + R, 0x1p-44, 0x1p-30);
-  const double X = ox + k.ax, Y = oy + k.ay;
-  if (m < 0.5 && fabs(X) < 0x1p40 && fabs(Y) < 0x1p40) {
-    const double xl = floor(__dsub_rd(X, m)), xh = floor(__dadd_ru(X, m));
-    const double yl = floor(__dsub_rd(Y, m)), yh = floor(__dadd_ru(Y, m));
-    if (xl == xh && yl == yh)
-      return (xl >= 0.0 && xl < (double)V.W && yl >= 0.0 && yl < (double)V.H)
-                 ? (int)yl * (int)V.W + (int)xl
-                 : -1;
-  }
-  if (X + m < -1.0 || X - m > (double)V.W + 1.0 || Y + m < -1.0 || Y - m > (double)V.H + 1.0)
-    return -1;
-  return kUncertified;
-}
-
-// One FP32 word of prefix constants k: suffix point j of the letter's pair
-// table (the operations of the packed per-word loop, on one half).
-__device__ __forceinline__ void mixed_single_word(const Pre32& k, const float4* src, uint32_t j,
-                                                  const View& V, Tally& t,
-                                                  uint32_t* __restrict__ img) {
-  const float4 s = __ldg(src + j / 2u);
-  const bool odd = j & 1u;
-  float uf, vf;
-  uv_pole32(k, odd ? s.y : s.x, odd ? s.w : s.z, uf, vf);
-  const int col = __float_as_int(__fadd_rd(uf, 12582912.0f)) - k.kx;
-  const int row = __float_as_int(__fadd_rd(vf, 12582912.0f)) - k.ky;
-  t.add(((uint32_t)col < V.W && (uint32_t)row < V.H) ? row * (int)V.W + col : -1, img);
-}
-
-// Words of FP32 prefix slot `slot` on suffix points [j0, j0 + n) of letter u:
-// the odd ends one at a time, the rest as packed pairs.
-__device__ __forceinline__ void mixed_block_words(uint32_t slot, int u, uint32_t j0, uint32_t n,
-                                                  const Plan& L, const View& V, const Tables& T,
-                                                  Tally& t, uint32_t& words,
-                                                  uint32_t* __restrict__ img) {
-  const float4* src = T.suf32p + (size_t)u * L.npairs;
-  uint32_t j1 = j0 + n;
-  if (j0 & 1u) {
-    mixed_single_word(T.pre32[slot], src, j0, V, t, img);
-    ++j0;
-    ++words;
-  }
-  if (j1 > j0 && (j1 & 1u)) {
-    --j1;
-    mixed_single_word(T.pre32[slot], src, j1, V, t, img);
-    ++words;
-  }
-  if (j1 > j0) mixed_slot_words(slot, u, j0 / 2u, j1 / 2u, L, V, T, t, words, img);
-}
-
-// Disk of culling block `disk` of plan L (all lanes of a warp take part),
-// from the FP32 points that the mixed per-word path reads: center = middle of
-// their bounding box, radius = largest distance from it, with a relative
-// allowance for the FP32 rounding of that distance.  The FP64 disk has the
-// same center and a radius larger by 2^-23 of the largest coordinate, which
-// covers the distance from an FP64 point to its FP32 rounding.  A block with a
-// non-finite point gets an infinite radius, which no test certifies.
-__device__ __forceinline__ void cull_disk(const Plan& L, const Tables& T, uint32_t disk,
-                                          uint32_t lane) {
-  uint32_t l = 0;
-  while (l + 1 < L.clev && L.cdisk[l + 1] <= disk) ++l;
-  const uint32_t rem = disk - L.cdisk[l];
-  const uint32_t u = rem / L.cnb[l], j0 = (rem % L.cnb[l]) * L.csz[l], j1 = j0 + L.csz[l];
-  const float* s32 = reinterpret_cast<const float*>(T.suf32p + (size_t)u * L.npairs);
-  const float inf = __int_as_float(0x7F800000);
-  float x0 = inf, y0 = inf, x1 = -inf, y1 = -inf, amax = 0.0f;
-  bool finite = true;
-  for (uint32_t j = j0 + lane; j < j1; j += 32) {
-    const float x = s32[4 * (j / 2) + (j & 1)], y = s32[4 * (j / 2) + 2 + (j & 1)];
-    finite = finite && isfinite(x) && isfinite(y);
-    x0 = fminf(x0, x);
-    x1 = fmaxf(x1, x);
-    y0 = fminf(y0, y);
-    y1 = fmaxf(y1, y);
-    amax = fmaxf(amax, fmaxf(fabsf(x), fabsf(y)));
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    x0 = fminf(x0, __shfl_xor_sync(0xFFFFFFFFu, x0, o));
-    x1 = fmaxf(x1, __shfl_xor_sync(0xFFFFFFFFu, x1, o));
-    y0 = fminf(y0, __shfl_xor_sync(0xFFFFFFFFu, y0, o));
-    y1 = fmaxf(y1, __shfl_xor_sync(0xFFFFFFFFu, y1, o));
-    amax = fmaxf(amax, __shfl_xor_sync(0xFFFFFFFFu, amax, o));
-  }
-  finite = __all_sync(0xFFFFFFFFu, finite);
-  const float cx = 0.5f * x0 + 0.5f * x1, cy = 0.5f * y0 + 0.5f * y1;  // any center serves
-  float d2 = 0.0f;
-  for (uint32_t j = j0 + lane; j < j1; j += 32) {
-    const float dx = s32[4 * (j / 2) + (j & 1)] - cx, dy = s32[4 * (j / 2) + 2 + (j & 1)] - cy;
-    d2 = fmaxf(d2, fmaf(dx, dx, dy * dy));
-  }
-  for (int o = 16; o > 0; o >>= 1) d2 = fmaxf(d2, __shfl_xor_sync(0xFFFFFFFFu, d2, o));
-  if (lane == 0) {
-    // six roundings at most, each within 2^-24 relative; 1e-30 covers underflow
-    const float r32 = finite ? __fmaf_ru(sqrtf(d2), 1.0f + 0x1p-20f, 1e-30f) : inf;
-    T.disk32[disk] = make_float4(cx, cy, r32, 0.0f);
-    Disk64 D;
-    D.cr = cx;
-    D.ci = cy;
-    D.rho = finite ? ((double)r32 + (double)amax * 0x1p-23) * (1.0 + 0x1p-40)
-                   : __longlong_as_double(0x7FF0000000000000ll);
-    D.pad = 0.0;
-    T.disk64[disk] = D;
-  }
-}
-
-// Operator norms of prefix slot `slot`'s pole-form matrix (the FP64 norm from
-// the FP32 one where that is finite and nonzero, since the FP32 entries are
-// the FP64 ones rounded).
-__device__ __forceinline__ void cull_norm(const Tables& T, uint32_t slot) {
-  const Pre32 k = T.pre32[slot];
-  const float n32 = opnorm32(k.c1, k.c2, k.c3, k.c4);
-  T.nrm32[slot] = n32;
-  if (isfinite(n32) && n32 > 0.0f) {
-    T.nrm64[slot] = (double)n32 * (1.0 + 0x1p-20);
-  } else {
-    const Pre64 c = T.pre64[slot];
-    T.nrm64[slot] = opnorm64(c.c1, c.c2, c.c3, c.c4);
-  }
-}
-
-// The same for a small block, by one thread.
-__device__ __forceinline__ void cull_disk_thread(const Plan& L, const Tables& T, uint32_t disk) {
-  uint32_t l = 0;
-  while (l + 1 < L.clev && L.cdisk[l + 1] <= disk) ++l;
-  const uint32_t rem = disk - L.cdisk[l];
-  const uint32_t u = rem / L.cnb[l], j0 = (rem % L.cnb[l]) * L.csz[l], j1 = j0 + L.csz[l];
-  const float* s32 = reinterpret_cast<const float*>(T.suf32p + (size_t)u * L.npairs);
-  const float inf = __int_as_float(0x7F800000);
-  float x0 = inf, y0 = inf, x1 = -inf, y1 = -inf, amax = 0.0f;
-  bool finite = true;
-  for (uint32_t j = j0; j < j1; ++j) {
-    const float x = s32[4 * (j / 2) + (j & 1)], y = s32[4 * (j / 2) + 2 + (j & 1)];
-    finite = finite && isfinite(x) && isfinite(y);
-    x0 = fminf(x0, x);
-    x1 = fmaxf(x1, x);
-    y0 = fminf(y0, y);
-    y1 = fmaxf(y1, y);
-    amax = fmaxf(amax, fmaxf(fabsf(x), fabsf(y)));
-  }
-  const float cx = 0.5f * x0 + 0.5f * x1, cy = 0.5f * y0 + 0.5f * y1;
-  float d2 = 0.0f;
-  for (uint32_t j = j0; j < j1; ++j) {
-    const float dx = s32[4 * (j / 2) + (j & 1)] - cx, dy = s32[4 * (j / 2) + 2 + (j & 1)] - cy;
-    d2 = fmaxf(d2, fmaf(dx, dx, dy * dy));
-  }
-  const float r32 = finite ? __fmaf_ru(sqrtf(d2), 1.0f + 0x1p-20f, 1e-30f) : inf;
-  T.disk32[disk] = make_float4(cx, cy, r32, 0.0f);
-  Disk64 D;
-  D.cr = cx;
-  D.ci = cy;
-  D.rho = finite ? ((double)r32 + (double)amax * 0x1p-23) * (1.0 + 0x1p-40)
-                 : __longlong_as_double(0x7FF0000000000000ll);
-  D.pad = 0.0;
-  T.disk64[disk] = D;
-}
-
-// Work units of a plan's disk-and-norm pass, in warps: the disks of blocks of
-// up to kThreadDiskPoints points one per thread (the smallest levels come
-// first in the disk table), then one warp per larger disk, then one thread
-// per prefix norm.
-constexpr uint32_t kThreadDiskPoints = 81;
-
-__device__ __host__ __forceinline__ uint32_t cull_small_disks(const Plan& L) {
-  uint32_t l = 0;
-  while (l < L.clev && L.csz[l] <= kThreadDiskPoints) ++l;
-  return l < L.clev ? L.cdisk[l] : L.ndisks;
-}
-__device__ __host__ __forceinline__ uint32_t cull_disk_units(const Plan& L) {
-  const uint32_t small = cull_small_disks(L);
-  return (small + 31) / 32 + (L.ndisks - small) + (4u * L.np + 31) / 32;
-}
-// One warp's share (all lanes call): unit w of cull_disk_units(L).
-__device__ __forceinline__ void cull_disk_unit(const Plan& L, const Tables& T, uint32_t w,
-                                               uint32_t lane) {
-  const uint32_t small = cull_small_disks(L), ws = (small + 31) / 32;
-  if (w < ws) {
-    const uint32_t disk = w * 32 + lane;
-    if (disk < small) cull_disk_thread(L, T, disk);
-  } else if (w < ws + (L.ndisks - small)) {
-    cull_disk(L, T, small + (w - ws), lane);
-  } else {
-    const uint32_t slot = (w - ws - (L.ndisks - small)) * 32 + lane;
-    if (slot < 4u * L.np) cull_norm(T, slot);
-  }
-}
-
-// Culling levels of one plan in shared memory (the kernels index them by a
-// run-time level).
-struct CullLevels {
-  uint32_t sz[kMaxCullLevels], nb[kMaxCullLevels], disk[kMaxCullLevels];
-};
-
-// Stack entry: prefix slot (bits 0-31), suffix letter (32-33), level (34-36),
-// FP64 flag (37: a mixed render's fallback prefix), block (38-63).
-__device__ __forceinline__ unsigned long long cull_entry(uint32_t slot, uint32_t u, uint32_t l,
-                                                         bool f64, uint32_t b) {
-  return (unsigned long long)slot | ((unsigned long long)u << 32) |
-         ((unsigned long long)l << 34) | ((unsigned long long)f64 << 37) |
-         ((unsigned long long)b << 38);
-}
-
-// The culling of one warp, over one group at a time: the warp's test stack
-// and leaf queue (shared memory), its tally and counts.  Every lane of the
-// warp calls every method; the group's plan, view, tables and image are
-// passed in.  In a mixed render the fallback prefixes (near-parabolic,
-// direct-form and far) take FP64 tests and FP64 words, as in the per-word
-// render.
-template <bool MIXED>
-struct CullWarp {
-  unsigned long long* stack;
-  unsigned long long* leafq;
-  const CullLevels* C;
-  uint32_t len = 0, lq = 0, lane;
-  unsigned lt;
-  Tally t;
-  uint32_t words = 0, fp64_words = 0;
-
-  __device__ __forceinline__ CullWarp(unsigned long long* s, unsigned long long* q,
-                                      const CullLevels* c)
-      : stack(s), leafq(q), C(c), lane(threadIdx.x & 31), lt((1u << (threadIdx.x & 31)) - 1u) {}
-
-  // all words of block b (level l) of letter u under slot, one by one
-  __device__ __forceinline__ void block_words(const Plan& L, const View& V, const Tables& T,
-                                              uint32_t* __restrict__ img, uint32_t slot,
-                                              uint32_t u, uint32_t l, bool f64, uint32_t b) {
-    const uint32_t j0 = b * C->sz[l];
-    if (MIXED && !f64) {
-      mixed_block_words(slot, (int)u, j0, C->sz[l], L, V, T, t, words, img);
-    } else {
-      words64(T.pre64[slot], T.flags[slot] & kDirect, T.suf64 + (size_t)u * L.ns, j0,
-              j0 + C->sz[l], V, t, img);
-      words += C->sz[l];
-      if (MIXED) fp64_words += C->sz[l];
-    }
-  }
-  // leaf queue entries [0, n), one per lane
-  __device__ __forceinline__ void drain_leaves(const Plan& L, const View& V, const Tables& T,
-                                               uint32_t* __restrict__ img, uint32_t n) {
-    if (lane < n) {
-      const unsigned long long e = leafq[lane];
-      block_words(L, V, T, img, (uint32_t)e, (uint32_t)(e >> 32) & 3u, 0u, (e >> 37) & 1ull,
-                  (uint32_t)(e >> 38));
-    }
-    __syncwarp();
-  }
-  // certified pixel of (slot, u, l, b), or kUncertified
-  __device__ __forceinline__ int test(const View& V, const Tables& T, uint32_t slot, uint32_t u,
-                                      uint32_t l, bool f64, uint32_t b) {
-    const uint32_t di = C->disk[l] + u * C->nb[l] + b;
-    if (MIXED && !f64) return block_pixel32(T.pre32[slot], T.nrm32[slot], T.disk32[di], V);
-    if (T.flags[slot] & kDirect) return kUncertified;
-    return block_pixel64(T.pre64[slot], T.nrm64[slot], T.disk64[di], V);
-  }
-  // the outcome of one test per lane (act: this lane tested an entry)
-  __device__ __forceinline__ void settle(const Plan& L, const View& V, const Tables& T,
-                                         uint32_t* __restrict__ img, bool act, uint32_t slot,
-                                         uint32_t u, uint32_t l, bool f64, uint32_t b, int pix) {
-    if (act && pix != kUncertified) {
-      t.add_n(pix, C->sz[l], img);
-      words += C->sz[l];
-      if (MIXED && f64) fp64_words += C->sz[l];
-    }
-    const bool miss = act && pix == kUncertified;
-    const bool direct = miss && f64 && (T.flags[slot] & kDirect);
-    const bool kids = miss && l > 0 && !direct;
-    const bool leaf = miss && l == 0 && !direct;
-    // children onto the stack while there is room; a block that finds none
-    // (never with the stack's size) and a direct-form prefix (no pole form to
-    // test) are evaluated word by word at once
-    const unsigned bk = __ballot_sync(0xFFFFFFFFu, kids);
-    const uint32_t room = (uint32_t)(kCullStack - len) / 3u, rank = __popc(bk & lt);
-    const bool pushed = kids && rank < room;
-    if (pushed)
-      for (uint32_t i = 0; i < 3; ++i)
-        stack[len + 3 * rank + i] = cull_entry(slot, u, l - 1, f64, 3 * b + 2 - i);
-    len += 3u * min((uint32_t)__popc(bk), room);
-    if ((kids && !pushed) || direct) block_words(L, V, T, img, slot, u, l, f64, b);
-    const unsigned bl = __ballot_sync(0xFFFFFFFFu, leaf);
-    if (leaf) leafq[lq + __popc(bl & lt)] = cull_entry(slot, u, 0, f64, b);
-    lq += __popc(bl);
-    __syncwarp();
-    if (lq >= 32) {
-      drain_leaves(L, V, T, img, 32);
-      lq -= 32;
-      if (lane < lq) leafq[lane] = leafq[32 + lane];
-      __syncwarp();
-    }
-  }
-  // one round: the top n (<= 32) stack entries, one per lane
-  __device__ __forceinline__ void round(const Plan& L, const View& V, const Tables& T,
-                                        uint32_t* __restrict__ img, uint32_t n) {
-    unsigned long long e = 0;
-    if (lane < n) e = stack[len - n + lane];
-    __syncwarp();
-    len -= n;
-    const bool act = lane < n;
-    const uint32_t slot = (uint32_t)e, u = (uint32_t)(e >> 32) & 3u;
-    const uint32_t l = (uint32_t)(e >> 34) & 7u, b = (uint32_t)(e >> 38);
-    const bool f64 = (e >> 37) & 1ull;
-    settle(L, V, T, img, act, slot, u, l, f64, b, act ? test(V, T, slot, u, l, f64, b)
-                                                      : kUncertified);
-  }
-  // top-level blocks [b0, b1) of letter u under this lane's prefix slot
-  // (live: the lane has one), with the rounds their children call for
-  __device__ __forceinline__ void item(const Plan& L, const View& V, const Tables& T,
-                                       uint32_t* __restrict__ img, bool live, uint32_t slot,
-                                       uint32_t u, bool f64, uint32_t b0, uint32_t b1) {
-    const uint32_t top = L.clev - 1;
-    for (uint32_t b = b0; b < b1; ++b) {
-      settle(L, V, T, img, live, slot, u, top, f64, b,
-             live ? test(V, T, slot, u, top, f64, b) : kUncertified);
-      while (len >= 32) round(L, V, T, img, 32);
-    }
-  }
-  // everything still on the stack or in the leaf queue
-  __device__ __forceinline__ void finish(const Plan& L, const View& V, const Tables& T,
-                                         uint32_t* __restrict__ img) {
-    while (len > 0) round(L, V, T, img, min(len, 32u));
-    drain_leaves(L, V, T, img, lq);
-    lq = 0;
-  }
-};
-
-// The lanes of one culling item: prefix slot of this lane and whether it is
-// live, and (mixed) whether it takes the FP64 path.  Items are 32 prefixes x
-// a chunk of top-level blocks of one suffix letter.
-template <bool MIXED>
-__device__ __forceinline__ void cull_item(CullWarp<MIXED>& w, uint32_t item, const Work& Wk,
-                                          const Plan& L, const View& V, const Tables& T,
-                                          uint32_t* __restrict__ img, uint32_t top_blocks) {
-  int x, u;
-  uint32_t pb, c;
-  item_of(item, Wk, x, u, pb, c);
-  const uint32_t k = pb * 32 + w.lane;
-  const uint32_t slot = (uint32_t)x * L.np + L.r0 + k;
-  const bool live = k < L.nr;
-  const bool f64 = !MIXED || (live && (T.flags[slot] & kFallback));
-  const uint32_t b0 = c * Wk.chunk, b1 = min(top_blocks, b0 + Wk.chunk);
-  w.item(L, V, T, img, live, slot, (uint32_t)u, f64, b0, b1);
-}
-
-// ---------------------------------------------------------------------------
-// host helpers
-
-// Launch `k` as a programmatic dependent of the previous kernel in stream s
-// (it must call pdl_wait before reading that kernel's output).
-template <typename... Params, typename... Args>
-int launch_dependent(void (*k)(Params...), dim3 grid, dim3 block, cudaStream_t s,
-                     Args&&... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  if (cudaLaunchKernelEx(&cfg, k, static_cast<Args&&>(args)...) != cudaSuccess) return KL_ECUDA;
-  return KL_OK;
-}
-
-inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-inline uint32_t pow3u(int e) {
-  uint32_t v = 1;
-  while (e-- > 0) v *= 3u;
-  return v;
-}
-
-inline bool valid_view(const kl_params* p) {
-  if (p->width < 1 || p->height < 1 || p->width > KL_MAX_IMAGE_SIDE ||
-      p->height > KL_MAX_IMAGE_SIDE)
-    return false;
-  if ((uint64_t)p->width * p->height > (1ull << 31) - 1) return false;
-  if (!(p->x0 < p->x1) || !(p->y0 < p->y1)) return false;
-  const double v[4] = {p->x0, p->x1, p->y0, p->y1};
-  for (double t : v)
-    if (!isfinite(t)) return false;
-  for (int k = 0; k < 32; ++k)
-    if (!isfinite(p->gens[k])) return false;
-  for (int k = 0; k < 8; ++k)
-    if (!isfinite(p->seeds[k])) return false;
-  if (p->block_threads != 0 && p->block_threads != 64 && p->block_threads != 128 &&
-      p->block_threads != 256)
-    return false;
-  return true;
-}
-
-// Prefix/suffix split.  Single renders: up to 9 prefix letters while the
-// words are few (enough threads), then suffixes of up to 8 letters (9 beyond
-// depth 20), the rest prefix.  Batched renders draw their parallelism from
-// many groups and use suffixes of up to 8 letters with at least 7 prefix
-// letters (729 prefix slots per letter fill whole thread blocks).
-inline int make_plan(const kl_params* p, Plan* L, bool batched) {
-  const int d = (int)p->depth;
-  if (d < 1 || d > kMaxRenderDepth) return KL_ERANGE;
-  int pl, sl;
-  if (d == 1) {
-    pl = 1;
-    sl = 0;
-  } else if (p->prefix_len) {
-    pl = (int)p->prefix_len;
-    sl = d - pl;
-    if (pl < 1 || sl < 1 || pl > kMaxPrefix || sl > kMaxSuffix) return KL_EINVAL;
-  } else if (p->cull) {
-    // culled renders: long suffix tables (large blocks, and a prefix table
-    // whose FP64 products are the bulk of the table cost kept small): all but
-    // one letter up to 9, then about half the word plus one, at most 12
-    if (d - 1 <= kMaxPlainSuffix) {
-      sl = d - 1;
-    } else {
-      sl = d / 2 + 1;
-      if (sl < kMaxPlainSuffix) sl = kMaxPlainSuffix;
-      if (sl > kMaxSuffix) sl = kMaxSuffix;
-    }
-    pl = d - sl;
-    if (pl > kMaxPrefix) return KL_ERANGE;
-  } else if (batched) {
-    sl = d - 7;
-    if (sl > 8) sl = 8;
-    if (sl < 1) sl = 1;
-    pl = d - sl;
-    if (pl > kMaxPrefix) return KL_ERANGE;
-  } else if (d <= 10) {
-    pl = d - 1;
-    sl = 1;
-  } else {
-    sl = d - 9;
-    const int smax = d > 20 ? 9 : 8;
-    if (sl > smax) sl = smax;
-    pl = d - sl;
-    if (pl > kMaxPrefix) return KL_ERANGE;
-  }
-  L->d = d;
-  L->p = pl;
-  L->s = sl;
-  L->np = pow3u(pl - 1);
-  L->ns = sl > 0 ? pow3u(sl - 1) : 0;
-  L->npairs = (L->ns + 1) / 2;
-  // shard k of n: prefix slots [floor(k np / n), floor((k+1) np / n)) per letter
-  if (p->shard_count > 1) {
-    if (batched || p->shard_index >= p->shard_count) return KL_EINVAL;
-    const uint64_t n = p->shard_count, k = p->shard_index;
-    L->r0 = (uint32_t)(k * L->np / n);
-    L->nr = (uint32_t)((k + 1) * L->np / n) - L->r0;
-  } else {
-    L->r0 = 0;
-    L->nr = L->np;
-  }
-  L->q = (pl + 1) / 2;
-  L->so = sl / 2;
-  L->si = sl - L->so;
-  L->p3_q1 = pow3u(L->q - 1);
-  L->p3_pq = pow3u(pl - L->q);
-  L->p3_so1 = L->so > 0 ? pow3u(L->so - 1) : 1;
-  L->p3_si = pow3u(L->si);
-  L->p3_si1 = L->si > 0 ? pow3u(L->si - 1) : 1;
-  // culling levels: blocks of 9 .. 729 points (fewer levels for short suffixes)
-  {
-    const int top = sl > 0 ? (sl - 1 < 6 ? sl - 1 : 6) : 0;
-    const int j0 = top < 2 ? top : 2;
-    L->cj0 = (uint32_t)j0;
-    L->clev = sl > 0 ? (uint32_t)(top - j0 + 1) : 0;
-    L->ndisks = 0;
-    for (uint32_t l = 0; l < (uint32_t)kMaxCullLevels; ++l) {
-      const bool on = l < L->clev;
-      L->csz[l] = on ? pow3u(j0 + (int)l) : 0;
-      L->cnb[l] = on ? L->ns / L->csz[l] : 0;
-      L->cdisk[l] = L->ndisks;
-      L->ndisks += 4u * L->cnb[l];
-    }
-  }
-  const size_t nP = 4ull * L->np, nS = 4ull * L->ns;
-  size_t off = 0;
-  L->off_pre64 = off; off = align256(off + nP * sizeof(Pre64));
-  L->off_pre32 = off; off = align256(off + nP * sizeof(Pre32));
-  L->off_flags = off; off = align256(off + nP * sizeof(uint32_t));
-  L->off_suf64 = off; off = align256(off + nS * sizeof(double2));
-  L->off_suf32 = off; off = align256(off + 4ull * L->npairs * sizeof(float4));
-  L->off_fb = off; off = align256(off + nP * sizeof(unsigned long long));
-  L->off_fbcount = off; off = align256(off + 2 * sizeof(uint32_t));  // fallback count, queue
-  L->off_L = off; off = align256(off + 4ull * L->p3_q1 * sizeof(PartM));
-  L->off_H = off; off = align256(off + 4ull * L->p3_pq * sizeof(M2));
-  L->off_So = off; off = align256(off + 4ull * L->p3_so1 * sizeof(PartM));
-  L->off_Si = off; off = align256(off + 4ull * L->p3_si1 * sizeof(double2));
-  // disks and prefix norms exist in culled plans only
-  const size_t nD = p->cull ? L->ndisks : 0, nN = p->cull ? nP : 0;
-  L->off_disk32 = off; off = align256(off + nD * sizeof(float4));
-  L->off_disk64 = off; off = align256(off + nD * sizeof(Disk64));
-  L->off_nrm32 = off; off = align256(off + nN * sizeof(float));
-  L->off_nrm64 = off; off = align256(off + nN * sizeof(double));
-  // double-float constants and suffix pairs exist in KL_DF64 plans only
-  const bool df = p->precision == KL_DF64;
-  L->off_predf = off; off = align256(off + (df ? nP : 0) * sizeof(PreDF));
-  L->off_sufdf = off; off = align256(off + (df ? 8ull * L->npairs : 0) * sizeof(float4));
-  L->total = off;
-  return KL_OK;
-}
-
-inline View make_view(const kl_params* p) {
-  View V;
-  V.x0 = p->x0;
-  V.y1 = p->y1;
-  V.sx = (double)p->width / (p->x1 - p->x0);
-  V.sy = (double)p->height / (p->y1 - p->y0);
-  V.W = p->width;
-  V.H = p->height;
-  const double w = (double)p->width, h = (double)p->height;
-  uint64_t bw, bh;
-  memcpy(&bw, &w, sizeof bw);
-  memcpy(&bh, &h, sizeof bh);
-  V.hiW = (uint32_t)(bw >> 32);
-  V.hiH = (uint32_t)(bh >> 32);
-  return V;
-}
-
-inline Group make_group(const kl_params* p) {
-  Group G;
-  for (int k = 0; k < 32; ++k) G.g[k] = p->gens[k];
-  for (int k = 0; k < 8; ++k) G.seed[k] = p->seeds[k];
-  return G;
-}
-
-inline Tables carve(const Plan& L, void* ws) {
-  char* b = (char*)ws;
-  return {(Pre64*)(b + L.off_pre64),          (Pre32*)(b + L.off_pre32),
-          (uint32_t*)(b + L.off_flags),        (double2*)(b + L.off_suf64),
-          (float4*)(b + L.off_suf32),          (unsigned long long*)(b + L.off_fb),
-          (uint32_t*)(b + L.off_fbcount),      (PartM*)(b + L.off_L),
-          (M2*)(b + L.off_H),                  (PartM*)(b + L.off_So),
-          (double2*)(b + L.off_Si),            (float4*)(b + L.off_disk32),
-          (Disk64*)(b + L.off_disk64),         (float*)(b + L.off_nrm32),
-          (double*)(b + L.off_nrm64),          (PreDF*)(b + L.off_predf),
-          (float4*)(b + L.off_sufdf)};
-}
-
-inline int sm_count() {
-  int dev = 0, n = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  return n;
-}
-
-inline int check_launch() { return cudaGetLastError() == cudaSuccess ? KL_OK : KL_ECUDA; }
-
-// SM count and resident blocks per SM of a kernel with BT threads.
-inline int device_slots(const void* kernel, int bt, int* sms, int* occ) {
-  *sms = sm_count();
-  if (*sms <= 0) return KL_ECUDA;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kernel, bt, 0) != cudaSuccess ||
-      *occ < 1)
-    return KL_ECUDA;
-  return KL_OK;
-}
-
-// Items of about equal cost.  chunk_units = 0: about 12 items per resident
-// block, so that the queue drains within a small fraction of one item, but no
-// chunk below 16 units; else chunks of that many units (suffix points or
-// point pairs).
-inline Work make_work(const Plan& L, int bt, uint32_t units, int slots, uint32_t chunk_units) {
-  Work W;
-  W.n_pb = (L.nr + bt - 1) / bt;
-  if (W.n_pb == 0) {  // an empty shard
-    W.n_chunks = 1;
-    W.chunk = units > 0 ? units : 1;
-    W.n_items = 0;
-    return W;
-  }
-  const uint64_t base = 12ull * W.n_pb;
-  if (chunk_units == 0) {
-    const uint64_t target = 12ull * (uint64_t)slots;
-    uint64_t n_chunks = (target + base - 1) / base;
-    const uint64_t most = units / 16 > 0 ? units / 16 : 1;
-    if (n_chunks > most) n_chunks = most;
-    if (n_chunks < 1) n_chunks = 1;
-    W.chunk = (uint32_t)((units + n_chunks - 1) / n_chunks);
-  } else {
-    W.chunk = chunk_units < units ? chunk_units : units;
-  }
-  if (W.chunk < 1) W.chunk = 1;
-  W.n_chunks = (units + W.chunk - 1) / W.chunk;
-  W.n_items = (uint32_t)(base * W.n_chunks);
-  return W;
-}
-
 }  // namespace
+
+// The double-float arithmetic, the culled renders and the host helpers.
+#include "kl_df.cuh"
+#include "kl_cull.cuh"
+#include "kl_plan.cuh"

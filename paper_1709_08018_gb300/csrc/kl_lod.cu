@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(kLodThreads) expand_kernel(
 }
 
 // Culled exact render of the deferred level-hi nodes (the culling of
-// kl_params.cull, kl_common.cuh): the same image as the per-word render of
+// kl_params.cull, kl_cull.cuh): the same image as the per-word render of
 // those nodes on this split, with whole blocks of a node's words placed at
 // once where certified.
 // lod_disk_kernel first bounds the suffix blocks (warps [0, ndisks)) and

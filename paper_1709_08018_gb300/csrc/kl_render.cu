@@ -1,5 +1,6 @@
 // Single render, decode and evaluation entry points of the C ABI (sm_103a).
-// The arithmetic, tables and per-item bodies are in kl_common.cuh.
+// The arithmetic, tables and per-item bodies are in kl_common.cuh and the
+// headers it includes (kl_df.cuh, kl_cull.cuh, kl_plan.cuh).
 #include <mutex>
 
 #include "kl_common.cuh"
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(BT, 896 / BT) render_df64_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// culled renders (kl_params.cull; the culling itself is in kl_common.cuh)
+// culled renders (kl_params.cull; the culling itself is in kl_cull.cuh)
 
 // Disks of all culling blocks, then the prefix norms (cull_disk_unit).
 __global__ void __launch_bounds__(128) disk_kernel(Plan L, Tables T) {
