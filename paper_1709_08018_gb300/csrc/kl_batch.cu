@@ -84,6 +84,9 @@ __global__ void __launch_bounds__(BT, 1280 / BT) batch_render_kernel(
   Tally t;
   uint32_t words = 0;
   int gcur = -1;
+  // the current group's items are [glo, ghi): consecutive items of a block
+  // usually stay in one group, which then needs no search
+  uint32_t glo = 0u, ghi = 0u;  // empty: the first item searches
   for (;;) {
     const uint32_t item = next_item(queue);
     if (item >= total) break;
@@ -107,21 +110,24 @@ __global__ void __launch_bounds__(BT, 1280 / BT) batch_render_kernel(
       continue;
     }
     const uint32_t local = item - n64;
-    const int g = (int)find_group(item_bases, n, local);
-    if (g != gcur) {
+    if (local - glo >= ghi - glo) {  // outside [glo, ghi): another group
+      const int g = (int)find_group(item_bases, n, local);
       if (gcur >= 0) publish_counts(t.in_window, words, 0, t.atomics, D[gcur].cnt);
       t = Tally();
       words = 0;
       gcur = g;
+      glo = item_bases[g];
+      ghi = item_bases[g + 1];
     }
+    const int g = gcur;
     const Plan L = D[g].L;
     const View V = D[g].V;
     const Tables T = D[g].T;
     const Work Wk = D[g].Wk;
     if (MIXED)
-      mixed_item<BT>(local - item_bases[g], Wk, L, V, T, t, words, D[g].img);
+      mixed_item<BT>(local - glo, Wk, L, V, T, t, words, D[g].img);
     else
-      fp64_item<BT>(local - item_bases[g], Wk, L, V, T, t, words, D[g].img);
+      fp64_item<BT>(local - glo, Wk, L, V, T, t, words, D[g].img);
   }
   if (gcur >= 0) publish_counts(t.in_window, words, 0, t.atomics, D[gcur].cnt);
 }
