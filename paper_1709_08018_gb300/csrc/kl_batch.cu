@@ -67,9 +67,10 @@ __global__ void batch_combine_kernel(const GroupDesc* __restrict__ D,
 }
 
 // One persistent launch for the whole batch.  Queue order: all groups' FP64
-// fallback units (BT per item; mixed mode only), then every group's items in
-// group order.  Counters are published per group whenever a block moves to
-// another group (the item, hence the group, is uniform over the block).
+// fallback units (32 per item; mixed mode only), then every group's items in
+// group order.  Counters are published per group whenever a warp moves to
+// another group (the item, hence the group, is uniform over the warp, and
+// over the block for FP64 items).
 // Registers are capped at 48 (10 blocks of 128 threads per SM): the group
 // lookup and descriptor spill at the single render's 40, and the batch ran
 // 3% faster at 48.
@@ -78,20 +79,23 @@ __global__ void __launch_bounds__(BT, 1280 / BT) batch_render_kernel(
     const GroupDesc* __restrict__ D, const uint32_t* __restrict__ item_bases, uint32_t n,
     uint32_t n_items, const unsigned long long* __restrict__ fb,
     const uint32_t* __restrict__ fb_count, uint32_t cmax, uint32_t* queue) {
+  // mixed items are drawn per warp (32 prefixes each, no block barrier), FP64
+  // items per block (BT prefixes)
+  constexpr uint32_t IT = MIXED ? 32u : (uint32_t)BT;
   const uint32_t fb_units = MIXED ? 3u * cmax * (*fb_count) : 0u;
-  const uint32_t n64 = (fb_units + BT - 1) / BT;
+  const uint32_t n64 = (fb_units + IT - 1) / IT;
   const uint32_t total = n64 + n_items;
   Tally t;
   uint32_t words = 0;
   int gcur = -1;
-  // the current group's items are [glo, ghi): consecutive items of a block
-  // usually stay in one group, which then needs no search
+  // the current group's items are [glo, ghi): consecutive items of a warp
+  // (or block) usually stay in one group, which then needs no search
   uint32_t glo = 0u, ghi = 0u;  // empty: the first item searches
   for (;;) {
-    const uint32_t item = next_item(queue);
+    const uint32_t item = MIXED ? next_item_warp(queue) : next_item(queue);
     if (item >= total) break;
     if (MIXED && item < n64) {
-      const uint32_t unit = item * BT + threadIdx.x;
+      const uint32_t unit = item * IT + (threadIdx.x & 31u);
       if (unit < fb_units) {
         const unsigned long long ent = fb[unit / (3u * cmax)];
         const uint32_t rem = unit % (3u * cmax);
@@ -125,7 +129,7 @@ __global__ void __launch_bounds__(BT, 1280 / BT) batch_render_kernel(
     const Tables T = D[g].T;
     const Work Wk = D[g].Wk;
     if (MIXED)
-      mixed_item<BT>(local - glo, Wk, L, V, T, t, words, D[g].img);
+      mixed_item<32>(local - glo, Wk, L, V, T, t, words, D[g].img);
     else
       fp64_item<BT>(local - glo, Wk, L, V, T, t, words, D[g].img);
   }
@@ -395,7 +399,7 @@ extern "C" int kl_batch_create(const kl_params* params, uint32_t n_groups, kl_ba
     }
     // culled: warp items of 32 prefixes x one top-level block
     b->works[g] = b->cull    ? make_work(L, 32, L.cnb[L.clev - 1], 1, 1u)
-                  : b->mixed ? make_work(L, b->bt, L.npairs, 1, chunk)
+                  : b->mixed ? make_work(L, 32, L.npairs, 1, chunk)
                              : make_work(L, b->bt, L.ns, 1, 2u * chunk);
     b->bases[g] = (uint32_t)parts;
     b->bases[(n_groups + 1) + g] = (uint32_t)comb;
