@@ -224,6 +224,27 @@ def test_features_against_oracle(kl):
     assert base == feats.shape[0]
 
 
+@pytest.mark.parametrize("prec,tol", [("MIXED", 2e-5), ("FP64", 1e-9), ("DF64", 1e-9)])
+def test_depth22_word_values(kl, prec, tol):
+    """The exact depth-22 render the pruned render is judged against (8192^2
+    over [-2,2]^2, held-out groups): its word values on a seeded sample of
+    1e5 indices against the oracle's per-word definition."""
+    d, size, window = 22, 8192, (-2.0, 2.0, -2.0, 2.0)
+    for g, _ in klsynth.draw_groups(klsynth.LOD_HELDOUT_SEED, 2):
+        p = kl.params_init(g.ta, g.tb, d, size, size, window, getattr(kl, prec))
+        idx = klsynth.index_sample(klsynth.SAMPLE_SEED, 100_000, d)
+        uv = kl.eval_words(p, dev_index(idx)).cpu().numpy()
+        go, so = oracle.group(g.ta, g.tb)
+        z = oracle.evaluate(go, so, d, idx)
+        sx = size / (window[1] - window[0])
+        zg = (window[0] + uv[:, 0] / sx) + 1j * (window[3] - uv[:, 1] / sx)
+        fin = np.isfinite(z) & (np.abs(z) < 1e12)
+        assert np.isfinite(uv[fin]).all()
+        err = np.abs(zg[fin] - z[fin]) / np.maximum(1.0, np.abs(z[fin]))
+        print(f"\n{prec} d=22 group {g.ta:.4f}: max rel |dz| {err.max():.3e}")
+        assert err.max() <= tol
+
+
 def test_trained_network_gain(kl):
     """The benchmark's setting: a network trained on 64 groups, its pruning
     setting (margin, edge, last level) chosen on 8 validation groups, judged
