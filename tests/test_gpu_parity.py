@@ -198,6 +198,26 @@ def test_render_degenerate_sizes(kl):
     assert int(cnt[0]) == 0 and int(cnt[1]) == oracle.word_count(7)
 
 
+@pytest.mark.parametrize("prec,tol", [("MIXED", 2e-5), ("DF64", 1e-9)])
+def test_render_at_the_maximum_depth(kl, prec, tol):
+    """The deepest render a plan allows (length 24: 4 3^23 = 1.1e11 words,
+    above 2^32): every word counted once in the 64-bit counters, the image
+    holding every in-window word, and word values on a seeded sample against
+    the oracle."""
+    g, d, W, window = GROUPS["nearcusp"], 24, 1024, (-2.0, 2.0, -2.0, 2.0)
+    p = kl.params_init(g.ta, g.tb, d, W, W, window, getattr(kl, prec))
+    img, cnt = kl.render(p)
+    c = cnt.cpu().numpy()
+    n = oracle.word_count(d)
+    assert n > 2 ** 32 and int(c[0]) + int(c[1]) == n
+    assert int(as_u32(img).astype(np.uint64).sum()) == int(c[0])
+    idx = klsynth.index_sample(klsynth.SAMPLE_SEED, 100_000, d)
+    compare_values(kl, g, d, idx, window, W, W, getattr(kl, prec), tol)
+    p.depth = d + 1
+    with pytest.raises(kl.KlError):
+        kl.render(p)
+
+
 def test_render_accumulate_and_errors(kl):
     import torch
     g = GROUPS["gasket"]
