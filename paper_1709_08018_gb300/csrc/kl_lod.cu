@@ -17,7 +17,8 @@
 // enumeration").
 //
 // Pruned render.  From level lo down, the network predicts each active
-// node's label from the 8 features of its det-normalised prefix matrix.  A
+// node's label from the 8 features of its prefix matrix (a product of det-1
+// generators), on the tensor cores in tiles of 128 nodes.  A
 // node predicted resolved (y + margin < 1/2) is pruned when its first, middle
 // and last words in index order (the two ends and the middle of its piece of
 // the limit set) fall into one pixel, each at least `edge` pixels away from
@@ -27,7 +28,8 @@
 // a right prediction never moves a word across a pixel edge; a node too near
 // an edge is expanded instead, and its smaller children are tried in turn.
 // The others expand to their children; nodes still active at level hi are
-// rendered exactly (all their words) by the mixed kernel.  Every word is
+// rendered exactly (all their words) by the culling engine of kl_cull.cuh,
+// with the image of the per-word mixed render of those nodes.  Every word is
 // counted once.
 #include "kl_mlp_tc.cuh"
 
