@@ -1,6 +1,7 @@
 // Host-side part of the C ABI: status strings, word counts, generators from
-// traces (Grandma's recipe), seeds and parameter defaults.  No GPU is needed
-// for anything in this file.
+// traces (Grandma's recipe), seeds, Maskit's slice group, the cusp seed list
+// of multi-seed feeding and parameter defaults.  No GPU is needed for
+// anything in this file.
 #include <cmath>
 #include <complex>
 #include <cstring>
