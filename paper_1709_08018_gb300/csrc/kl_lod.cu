@@ -802,7 +802,7 @@ int render_lod_impl(const kl_params* p, uint32_t lo, uint32_t hi, const float* d
     return KL_ECUDA;
   for (int k = (int)lo; k <= (int)hi; ++k) {
     const int cur = (k - (int)lo) & 1;
-    expand_kernel<<<grid_for(4ull * P.p3[k], kLodThreads, 3), kLodThreads,
+    expand_kernel<<<grid_for(4ull * P.p3[k], kLodThreads, 4), kLodThreads,
                     d_mlp ? kFwdSmem : 0u, s>>>(
         d_mlp, d_labels ? d_labels + P.base[k] : nullptr, G, V, P.D, k, (int)hi, P.p3[k],
         d_mlp ? margin : 0.0f, (double)edge, vstar, act[cur], counts + k, act[cur ^ 1],

@@ -396,7 +396,7 @@ extern "C" int kl_mlp_forward(const float* d_params, const float* d_x, uint64_t 
                            (int)kFwdSmem) != cudaSuccess)
     return KL_ECUDA;
   const uint64_t tiles = (n + kTile - 1) / kTile;
-  const unsigned grid = (unsigned)(tiles < (uint64_t)sms * 3 ? tiles : (uint64_t)sms * 3);
+  const unsigned grid = (unsigned)(tiles < (uint64_t)sms * 4 ? tiles : (uint64_t)sms * 4);
   mlp_forward_kernel<<<grid, kTile, kFwdSmem, (cudaStream_t)stream>>>(d_params, d_x, n, d_y);
   return check_launch();
 }
