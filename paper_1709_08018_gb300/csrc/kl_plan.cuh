@@ -140,31 +140,44 @@ inline int make_plan(const kl_params* p, Plan* L, bool batched) {
       L->ndisks += 4u * L->cnb[l];
     }
   }
+  // The prefix side first: its offsets depend only on the prefix (its length,
+  // the shard, the precision and culling), so two plans with the same prefix
+  // find each other's prefix tables in the same place (prefix_tables_shared).
   const size_t nP = 4ull * L->np, nS = 4ull * L->ns;
+  const bool df = p->precision == KL_DF64;
+  // disks and prefix norms exist in culled plans only
+  const size_t nD = p->cull ? L->ndisks : 0, nN = p->cull ? nP : 0;
   size_t off = 0;
   L->off_pre64 = off; off = align256(off + nP * sizeof(Pre64));
   L->off_pre32 = off; off = align256(off + nP * sizeof(Pre32));
   L->off_flags = off; off = align256(off + nP * sizeof(uint32_t));
-  L->off_suf64 = off; off = align256(off + nS * sizeof(double2));
-  L->off_suf32 = off; off = align256(off + 4ull * L->npairs * sizeof(float4));
   L->off_fb = off; off = align256(off + nP * sizeof(unsigned long long));
   L->off_fbcount = off; off = align256(off + 2 * sizeof(uint32_t));  // fallback count, queue
   L->off_L = off; off = align256(off + 4ull * L->p3_q1 * sizeof(PartM));
   L->off_H = off; off = align256(off + 4ull * L->p3_pq * sizeof(M2));
-  L->off_So = off; off = align256(off + 4ull * L->p3_so1 * sizeof(PartM));
-  L->off_Si = off; off = align256(off + 4ull * L->p3_si1 * sizeof(double2));
-  // disks and prefix norms exist in culled plans only
-  const size_t nD = p->cull ? L->ndisks : 0, nN = p->cull ? nP : 0;
-  L->off_disk32 = off; off = align256(off + nD * sizeof(float4));
-  L->off_disk64 = off; off = align256(off + nD * sizeof(Disk64));
   L->off_nrm32 = off; off = align256(off + nN * sizeof(float));
   L->off_nrm64 = off; off = align256(off + nN * sizeof(double));
   // double-float constants and suffix pairs exist in KL_DF64 plans only
-  const bool df = p->precision == KL_DF64;
   L->off_predf = off; off = align256(off + (df ? nP : 0) * sizeof(PreDF));
+  // the suffix side
+  L->off_suf64 = off; off = align256(off + nS * sizeof(double2));
+  L->off_suf32 = off; off = align256(off + 4ull * L->npairs * sizeof(float4));
+  L->off_So = off; off = align256(off + 4ull * L->p3_so1 * sizeof(PartM));
+  L->off_Si = off; off = align256(off + 4ull * L->p3_si1 * sizeof(double2));
+  L->off_disk32 = off; off = align256(off + nD * sizeof(float4));
+  L->off_disk64 = off; off = align256(off + nD * sizeof(Disk64));
   L->off_sufdf = off; off = align256(off + (df ? 8ull * L->npairs : 0) * sizeof(float4));
   L->total = off;
   return KL_OK;
+}
+
+// Whether a plan B built after plan A (same parameters apart from the word
+// length) can use A's prefix tables as they are: the same prefix length and
+// shard, and neither culled (culled plans also hold per-prefix norms computed
+// with their own suffix blocks).
+inline bool prefix_tables_shared(const Plan& A, const Plan& B, const kl_params* p) {
+  return !p->cull && A.p == B.p && A.q == B.q && A.np == B.np && A.r0 == B.r0 &&
+         A.nr == B.nr && B.off_suf64 == A.off_suf64;
 }
 
 inline View make_view(const kl_params* p) {

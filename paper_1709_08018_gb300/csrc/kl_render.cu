@@ -17,12 +17,16 @@ constexpr uint32_t kPartLanes = 8;
 // counters); the blocks after them clear the image.  The parts work is a few
 // thousand short FP64 chains, far from filling the GPU, so the clearing runs
 // beside it and a render needs no separate memset.
+// Entries [first, parts_count) of the parts tables; first > 0 (the prefix
+// parts skipped) when the prefix tables are already in place, whose fallback
+// count is then kept.
 __global__ void parts_kernel(Group G, Plan L, int renorm, Tables T, Clear C,
-                             uint32_t part_blocks) {
+                             uint32_t part_blocks, uint32_t first) {
   pdl_trigger();
   if (blockIdx.x < part_blocks) {
     if (blockIdx.x == 0) {
-      if (threadIdx.x < 2) T.fbcount[threadIdx.x] = 0u;
+      if (threadIdx.x == 0 && first == 0) T.fbcount[0] = 0u;  // fallback prefixes
+      if (threadIdx.x == 1) T.fbcount[1] = 0u;                // the work queue
       if (C.counters && threadIdx.x < KL_N_COUNTERS) C.counters[threadIdx.x] = 0ull;
     }
     // kPartLanes entries per block: each entry is one long chain of dependent
@@ -30,7 +34,7 @@ __global__ void parts_kernel(Group G, Plan L, int renorm, Tables T, Clear C,
     // launch more than filling warps does
     const uint32_t total = parts_count(L);
     if (threadIdx.x < kPartLanes)
-      for (uint32_t idx = blockIdx.x * kPartLanes + threadIdx.x; idx < total;
+      for (uint32_t idx = first + blockIdx.x * kPartLanes + threadIdx.x; idx < total;
            idx += part_blocks * kPartLanes)
         part_entry(G, L, renorm, idx, T);
     return;
@@ -39,11 +43,13 @@ __global__ void parts_kernel(Group G, Plan L, int renorm, Tables T, Clear C,
               (size_t)(gridDim.x - part_blocks) * blockDim.x);
 }
 
-__global__ void combine_kernel(View V, Plan L, double ptol, int prec, Tables T) {
+// Entries [first, combine_count): first = 4 nr (the prefixes skipped) when
+// the prefix tables are already in place.
+__global__ void combine_kernel(View V, Plan L, double ptol, int prec, Tables T, uint32_t first) {
   pdl_trigger();
   pdl_wait();
   const uint32_t total = combine_count(L);
-  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+  for (uint32_t idx = first + blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += gridDim.x * blockDim.x)
     combine_entry(V, L, ptol, prec, idx, T, 0u, T.fb, T.fbcount);
 }
@@ -346,11 +352,16 @@ int prof_mark(cudaEvent_t e, cudaStream_t s) {
 
 // Tables of a render: parts (with the image clearing of C riding along),
 // then combine, launched as a programmatic dependent of parts.
+// The tables of plan L; with prefix_ready the prefix tables (and the list of
+// fallback prefixes) are taken as they are and only the suffix side is built.
 int build_tables(const kl_params* p, const Plan& L, const View& V, const Group& G,
-                 const Tables& T, cudaStream_t st, const Clear& C = Clear{}) {
+                 const Tables& T, cudaStream_t st, const Clear& C = Clear{},
+                 bool prefix_ready = false) {
   const int prec = (int)p->precision;
-  const uint32_t nParts = parts_count(L);
-  const uint32_t part_blocks = (nParts + kPartLanes - 1) / kPartLanes;
+  const uint32_t first_part = prefix_ready ? 4u * L.p3_q1 + (L.p > L.q ? 4u * L.p3_pq : 0u) : 0u;
+  const uint32_t first_comb = prefix_ready ? 4u * L.nr : 0u;
+  const uint32_t nParts = parts_count(L) - first_part;
+  const uint32_t part_blocks = nParts > 0 ? (nParts + kPartLanes - 1) / kPartLanes : 1u;
   uint32_t clear_blocks = 0;
   if (C.words) {
     const int sms = sm_count();
@@ -359,11 +370,11 @@ int build_tables(const kl_params* p, const Plan& L, const View& V, const Group& 
     clear_blocks = (uint32_t)(need < (size_t)sms * 8 ? (need > 0 ? need : 1) : (size_t)sms * 8);
   }
   parts_kernel<<<part_blocks + clear_blocks, 32, 0, st>>>(G, L, (int)p->renorm_every, T, C,
-                                                          part_blocks);
+                                                          part_blocks, first_part);
   if (check_launch() != KL_OK) return KL_ECUDA;
-  const uint32_t n = combine_count(L);
-  return launch_dependent(combine_kernel, dim3((n + 127) / 128), dim3(128), st, V, L,
-                          p->parabolic_tol, prec, T);
+  const uint32_t n = combine_count(L) - first_comb;
+  return launch_dependent(combine_kernel, dim3(n > 0 ? (n + 127) / 128 : 1u), dim3(128), st, V,
+                          L, p->parabolic_tol, prec, T, first_comb);
 }
 
 // Length k of a tiling render of *p: a limit-set render of the words of
@@ -526,12 +537,17 @@ extern "C" int kl_eval_words(const kl_params* p_in, const uint64_t* d_index, uin
 
 namespace {
 
-// One limit-set render of *p (already validated).
+// One limit-set render of *p (already validated).  prev (if not null) is the
+// plan of the render that last built tables in d_workspace, whose prefix
+// tables are reused when they serve this plan too (the lengths of a tiling
+// render).  *used: this render's plan.
 int render_length(const kl_params* p, uint32_t* d_image, unsigned long long* cnt,
-                  void* d_workspace, cudaStream_t s, bool profile) {
+                  void* d_workspace, cudaStream_t s, bool profile, const Plan* prev = nullptr,
+                  Plan* used = nullptr) {
   Plan L;
   int st = make_plan(p, &L, false);
   if (st != KL_OK) return st;
+  if (used) *used = L;
   const View V = make_view(p);
   const Group G = make_group(p);
   if (L.d == 1) {
@@ -549,7 +565,7 @@ int render_length(const kl_params* p, uint32_t* d_image, unsigned long long* cnt
   const Tables T = carve(L, d_workspace);
   Clear C{};
   if (!p->accumulate) C = {d_image, (size_t)p->width * p->height, cnt};
-  st = build_tables(p, L, V, G, T, s, C);
+  st = build_tables(p, L, V, G, T, s, C, prev && prefix_tables_shared(*prev, L, p));
   if (st != KL_OK) return st;
   switch (p->block_threads) {
     case 64: return launch_render<64>(p, L, V, T, d_image, cnt, s, profile);
@@ -571,13 +587,20 @@ extern "C" int kl_render(const kl_params* p, uint32_t* d_image, uint64_t* d_coun
   if (p->mode == KL_TILING) {
     // the lengths above kShortTiling as renders of their own, the longest
     // first (it clears the image unless accumulating), each next one added
-    // in; then all the short lengths in one launch
+    // in; then all the short lengths in one launch.  Consecutive lengths with
+    // the same prefix length share its prefix tables, built once.
     const uint32_t k0 = p->depth < kShortTiling ? p->depth : kShortTiling;
+    Plan prev;
+    bool have_prev = false;
     for (uint32_t k = p->depth; k > k0; --k) {
       kl_params q = length_params(p, k);
       q.accumulate = k == p->depth ? p->accumulate : 1u;
-      st = render_length(&q, d_image, cnt, d_workspace, s, k == p->depth);
+      Plan used;
+      st = render_length(&q, d_image, cnt, d_workspace, s, k == p->depth,
+                         have_prev ? &prev : nullptr, &used);
       if (st != KL_OK) return st;
+      prev = used;
+      have_prev = used.d > 1;
     }
     if (p->depth <= k0 && !p->accumulate) {
       if (cudaMemsetAsync(d_image, 0, (size_t)p->width * p->height * sizeof(uint32_t), s) !=
