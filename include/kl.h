@@ -256,6 +256,21 @@ KL_API int kl_eval_words(const kl_params* p, const uint64_t* d_index, uint64_t n
 KL_API int kl_render(const kl_params* p, uint32_t* d_image, uint64_t* d_counters, void* d_workspace,
               size_t workspace_bytes, void* stream);
 
+/* Multi-seed feeding (Sec. "Implementation": the drawing loop runs over a list
+ * of fixed points): every word of *p drawn once per point, i.e. the render of
+ * *p with all four seeds set to points[2i] + i points[2i+1], for i = 0 ..
+ * n_points - 1, into one image and one set of counters (zeroed first unless
+ * p->accumulate; the counters add up to n_points N_d).  The points' renders
+ * differ only in their suffix tables, so the prefix tables are built once
+ * (limit-set mode; a KL_TILING render shares them per point across its
+ * lengths).  kl_cusp_seeds gives the paper's list; its last four points are
+ * the repetend points of the cusps.  points: host array of 2 n_points
+ * doubles.  KL_EINVAL if n_points is 0 or a point is not finite; otherwise
+ * the arguments and errors of kl_render. */
+KL_API int kl_render_multiseed(const kl_params* p, const double* points, uint32_t n_points,
+                               uint32_t* d_image, uint64_t* d_counters, void* d_workspace,
+                               size_t workspace_bytes, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Batched render: a sweep over many groups in one persistent launch.
  *

@@ -17,6 +17,7 @@ API = ("kl_status_string", "kl_word_count", "kl_grandma", "kl_seeds", "kl_maskit
        "kl_cusp_seeds",
        "kl_params_init",
        "kl_decode_words", "kl_workspace_bytes", "kl_eval_words", "kl_render",
+       "kl_render_multiseed",
        "kl_batch_create", "kl_batch_workspace_bytes", "kl_batch_render", "kl_batch_capture",
        "kl_batch_replay", "kl_batch_destroy", "kl_mlp_forward", "kl_mlp_scratch_bytes",
        "kl_mlp_grad", "kl_mlp_adam", "kl_mlp_train_step", "kl_lod_node_count", "kl_lod_label_bytes", "kl_lod_labels",
@@ -163,6 +164,8 @@ def lib():
         L.kl_eval_words.restype = I
         L.kl_render.argtypes = [ctypes.POINTER(Params), P, P, P, SZ, P]
         L.kl_render.restype = I
+        L.kl_render_multiseed.argtypes = [ctypes.POINTER(Params), P, U32, P, P, P, SZ, P]
+        L.kl_render_multiseed.restype = I
         L.kl_batch_create.argtypes = [ctypes.POINTER(Params), U32, ctypes.POINTER(P)]
         L.kl_batch_create.restype = I
         L.kl_batch_workspace_bytes.argtypes = [P]
@@ -266,20 +269,21 @@ def cusp_seeds(gens) -> np.ndarray:
 
 def render_multiseed(p: "Params", points, image=None, counters=None, workspace=None,
                      stream=None, device="cuda"):
-    """Multi-seed feeding: every word of p drawn once per seed point, i.e.
-    one kl_render per point with all four seeds set to it, accumulated into
-    one image and one set of counters.  points: complex seed points."""
-    q = Params.from_buffer_copy(p)
-    workspace = _workspace(q, device if image is None else image.device, workspace)
-    out = None
-    for n, z in enumerate(points):
-        for x in range(4):
-            q.seeds[2 * x] = complex(z).real
-            q.seeds[2 * x + 1] = complex(z).imag
-        q.accumulate = p.accumulate if n == 0 else 1
-        out = render(q, image, counters, workspace, stream, device)
-        image, counters = out
-    return out
+    """kl_render_multiseed: every word of p drawn once per seed point (all four
+    seeds set to it), into one image and one set of counters.  points:
+    complex seed points."""
+    torch = _torch()
+    pts = np.array([[complex(z).real, complex(z).imag] for z in points], dtype=np.float64)
+    if image is None:
+        image = torch.empty((p.height, p.width), dtype=torch.int32, device=device)
+    if counters is None:
+        counters = torch.zeros(KL_N_COUNTERS, dtype=torch.int64, device=image.device)
+    workspace = _workspace(p, image.device, workspace)
+    _check(lib().kl_render_multiseed(ctypes.byref(p), pts.ctypes.data, len(pts),
+                                     image.data_ptr(), counters.data_ptr(),
+                                     workspace.data_ptr(), workspace.numel(),
+                                     _stream_handle(stream)), "kl_render_multiseed")
+    return image, counters
 
 
 def render_repetends(p: "Params", image=None, counters=None, workspace=None, stream=None,

@@ -1,6 +1,7 @@
 // Single render, decode and evaluation entry points of the C ABI (sm_103a).
 // The arithmetic, tables and per-item bodies are in kl_common.cuh and the
 // headers it includes (kl_df.cuh, kl_cull.cuh, kl_plan.cuh).
+#include <cmath>
 #include <mutex>
 
 #include "kl_common.cuh"
@@ -576,6 +577,44 @@ int render_length(const kl_params* p, uint32_t* d_image, unsigned long long* cnt
 
 }  // namespace
 
+namespace {
+
+// A tiling render of *p (already validated): the lengths above kShortTiling
+// as renders of their own, the longest first (it clears the image unless
+// accumulating), each next one added in; then all the short lengths in one
+// launch.  Consecutive lengths with the same prefix length share its prefix
+// tables, built once.
+int render_tiling(const kl_params* p, uint32_t* d_image, unsigned long long* cnt,
+                  void* d_workspace, cudaStream_t s) {
+  const uint32_t k0 = p->depth < kShortTiling ? p->depth : kShortTiling;
+  Plan prev;
+  bool have_prev = false;
+  for (uint32_t k = p->depth; k > k0; --k) {
+    kl_params q = length_params(p, k);
+    q.accumulate = k == p->depth ? p->accumulate : 1u;
+    Plan used;
+    const int st = render_length(&q, d_image, cnt, d_workspace, s, k == p->depth,
+                                 have_prev ? &prev : nullptr, &used);
+    if (st != KL_OK) return st;
+    prev = used;
+    have_prev = used.d > 1;
+  }
+  if (p->depth <= k0 && !p->accumulate) {
+    if (cudaMemsetAsync(d_image, 0, (size_t)p->width * p->height * sizeof(uint32_t), s) !=
+        cudaSuccess)
+      return KL_ECUDA;
+    if (cnt && cudaMemsetAsync(cnt, 0, KL_N_COUNTERS * sizeof(uint64_t), s) != cudaSuccess)
+      return KL_ECUDA;
+  }
+  const int sms = sm_count();
+  if (sms <= 0) return KL_ECUDA;
+  tiling_short_kernel<<<sms * 4, 256, 0, s>>>(make_group(p), make_view(p), k0,
+                                              p->precision != KL_FP64, d_image, cnt);
+  return check_launch();
+}
+
+}  // namespace
+
 extern "C" int kl_render(const kl_params* p, uint32_t* d_image, uint64_t* d_counters,
                          void* d_workspace, size_t workspace_bytes, void* stream) {
   Plan L;
@@ -584,38 +623,43 @@ extern "C" int kl_render(const kl_params* p, uint32_t* d_image, uint64_t* d_coun
   if (!d_image) return KL_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned long long* cnt = (unsigned long long*)d_counters;
-  if (p->mode == KL_TILING) {
-    // the lengths above kShortTiling as renders of their own, the longest
-    // first (it clears the image unless accumulating), each next one added
-    // in; then all the short lengths in one launch.  Consecutive lengths with
-    // the same prefix length share its prefix tables, built once.
-    const uint32_t k0 = p->depth < kShortTiling ? p->depth : kShortTiling;
-    Plan prev;
-    bool have_prev = false;
-    for (uint32_t k = p->depth; k > k0; --k) {
-      kl_params q = length_params(p, k);
-      q.accumulate = k == p->depth ? p->accumulate : 1u;
+  if (p->mode == KL_TILING) return render_tiling(p, d_image, cnt, d_workspace, s);
+  return render_length(p, d_image, cnt, d_workspace, s, true);
+}
+
+extern "C" int kl_render_multiseed(const kl_params* p, const double* points, uint32_t n_points,
+                                   uint32_t* d_image, uint64_t* d_counters, void* d_workspace,
+                                   size_t workspace_bytes, void* stream) {
+  Plan L;
+  int st = validate(p, workspace_bytes, d_workspace, &L);
+  if (st != KL_OK) return st;
+  if (!d_image || !points || n_points == 0) return KL_EINVAL;
+  for (uint32_t i = 0; i < 2 * n_points; ++i)
+    if (!std::isfinite(points[i])) return KL_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long* cnt = (unsigned long long*)d_counters;
+  Plan prev;
+  bool have_prev = false;
+  for (uint32_t i = 0; i < n_points; ++i) {
+    kl_params q = *p;
+    for (int x = 0; x < 4; ++x) {
+      q.seeds[2 * x] = points[2 * i];
+      q.seeds[2 * x + 1] = points[2 * i + 1];
+    }
+    q.accumulate = i == 0 ? p->accumulate : 1u;
+    if (p->mode == KL_TILING) {
+      st = render_tiling(&q, d_image, cnt, d_workspace, s);
+    } else {
+      // the points' renders differ only in their suffix tables
       Plan used;
-      st = render_length(&q, d_image, cnt, d_workspace, s, k == p->depth,
-                         have_prev ? &prev : nullptr, &used);
-      if (st != KL_OK) return st;
+      st = render_length(&q, d_image, cnt, d_workspace, s, i == 0, have_prev ? &prev : nullptr,
+                         &used);
       prev = used;
       have_prev = used.d > 1;
     }
-    if (p->depth <= k0 && !p->accumulate) {
-      if (cudaMemsetAsync(d_image, 0, (size_t)p->width * p->height * sizeof(uint32_t), s) !=
-          cudaSuccess)
-        return KL_ECUDA;
-      if (cnt && cudaMemsetAsync(cnt, 0, KL_N_COUNTERS * sizeof(uint64_t), s) != cudaSuccess)
-        return KL_ECUDA;
-    }
-    const int sms = sm_count();
-    if (sms <= 0) return KL_ECUDA;
-    tiling_short_kernel<<<sms * 4, 256, 0, s>>>(make_group(p), make_view(p), k0,
-                                                p->precision != KL_FP64, d_image, cnt);
-    return check_launch();
+    if (st != KL_OK) return st;
   }
-  return render_length(p, d_image, cnt, d_workspace, s, true);
+  return KL_OK;
 }
 
 extern "C" int kl_set_profile_events(void* ev_start, void* ev_stop) {

@@ -100,3 +100,38 @@ def test_repetends_catch_cusp_detail(kl):
           f"{recall_both:.4f}; added pixels {int(added.sum())}, on it {on_deep:.4f}")
     assert recall_both > recall_base + 0.01
     assert on_deep > 0.9
+
+
+@pytest.mark.parametrize("prec", ["FP64", "MIXED", "DF64"])
+@pytest.mark.parametrize("mode", ["LIMIT_SET", "TILING"])
+def test_multiseed_equals_single_seed_renders(kl, prec, mode):
+    """kl_render_multiseed builds the prefix tables once for all points: its
+    image and counters are those of one kl_render per point (all four seeds
+    set to the point), summed, bit for bit."""
+    import torch
+    g = klsynth.NEAR_CUSP
+    p = kl.params_init(g.ta, g.tb, 13, 512, 384, (-2.0, 2.0, -1.5, 1.5), getattr(kl, prec),
+                       mode=getattr(kl, mode))
+    s16 = kl.cusp_seeds(list(p.gens))
+    points = [complex(s16[2 * i], s16[2 * i + 1]) for i in range(8)]
+    img, cnt = kl.render_multiseed(p, points)
+    acc = torch.zeros_like(img)
+    acc_c = torch.zeros_like(cnt)
+    q = kl.Params.from_buffer_copy(p)
+    for z in points:
+        for x in range(4):
+            q.seeds[2 * x], q.seeds[2 * x + 1] = z.real, z.imag
+        one, c1 = kl.render(q)
+        acc += one
+        acc_c += c1
+    assert torch.equal(img, acc)
+    assert torch.equal(cnt[:3], acc_c[:3])
+
+
+def test_multiseed_refuses_bad_points(kl):
+    g = klsynth.GASKET
+    p = kl.params_init(g.ta, g.tb, 8, 64, 64, (-1.5, 1.5, -1.5, 1.5), kl.MIXED)
+    for pts in ([], [complex(float("nan"), 0.0)], [0.1 + 0.2j, complex(0.0, float("inf"))]):
+        with pytest.raises(kl.KlError) as e:
+            kl.render_multiseed(p, pts)
+        assert e.value.status == 1
