@@ -240,3 +240,24 @@ def test_cusp_seeds_agree_with_the_oracle(kl, ta, tb):
     g = kl.grandma(ta, tb)
     assert np.allclose(kl.cusp_seeds(g), oracle.cusp_seeds(oracle.grandma(ta, tb)),
                        rtol=1e-9, atol=1e-12)
+
+
+def test_multiseed_argument_checks_need_no_gpu(kl):
+    """kl_render_multiseed refuses a missing, empty or non-finite point list
+    before any device call (the pointers below are never dereferenced)."""
+    import ctypes
+    p = kl.params_init(2 + 0j, 2 + 0j, 10, 256, 256, (-1.5, 1.5, -1.5, 1.5), kl.MIXED)
+    ws_bytes = kl.workspace_bytes(p)
+    fake_img, fake_ws = ctypes.c_void_p(1 << 20), ctypes.c_void_p(1 << 24)
+    L = kl.lib()
+    ok_pts = np.array([0.1, 0.2, 0.3, 0.4])
+    bad_pts = np.array([0.1, float("nan"), 0.3, 0.4])
+    cases = [(None, 2), (ok_pts.ctypes.data, 0), (bad_pts.ctypes.data, 2)]
+    for pts, n in cases:
+        st = L.kl_render_multiseed(ctypes.byref(p), pts, n, fake_img, None, fake_ws, ws_bytes,
+                                   None)
+        assert st == 1, (pts, n, st)
+    # and the render's own checks come first: a workspace that is too small
+    st = L.kl_render_multiseed(ctypes.byref(p), ok_pts.ctypes.data, 2, fake_img, None, fake_ws,
+                               ws_bytes - 256, None)
+    assert st == 4
