@@ -58,6 +58,9 @@ def main(argv=None):
     ap.add_argument("--mlp", type=int, default=0, help="rows of a training-step timing")
     ap.add_argument("--tiling", action="store_true")
     ap.add_argument("--cull", action="store_true", help="place certified blocks of words at once")
+    ap.add_argument("--seeds", choices=["one", "cusp", "repetends"], default="one",
+                    help="one seed per first letter (default), the 8-point multi-seed list, or "
+                         "its 4 repetend (commutator) points")
     a = ap.parse_args(argv)
     if a.batch:
         return run_batch(a, kl, klsynth, torch)
@@ -77,14 +80,23 @@ def main(argv=None):
                        prefix_len=a.prefix_len, mode=kl.TILING if a.tiling else kl.LIMIT_SET,
                        cull=int(a.cull))
     r = kl.Renderer(p)
+    points = None
+    if a.seeds != "one":
+        s16 = kl.cusp_seeds(list(p.gens))
+        first = 0 if a.seeds == "cusp" else 4
+        points = [complex(s16[2 * i], s16[2 * i + 1]) for i in range(first, 8)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(a.repeat):
         e0.record()
-        r()
+        if points is None:
+            r()
+        else:
+            kl.render_multiseed(p, points, r.image, r.counters, r.workspace)
         e1.record()
     torch.cuda.synchronize()
     cnt = r.counters.cpu().tolist()
-    print(f"{a.config} {a.precision} d={depth} {W}x{H}: words {kl.word_count(depth)}, "
+    n = 1 if points is None else len(points)
+    print(f"{a.config} {a.precision} d={depth} {W}x{H}: words {n * kl.word_count(depth)}, "
           f"in-window {cnt[0]}, dropped {cnt[1]}, fp64 words {cnt[2]}, atomics {cnt[3]}, "
           f"{e0.elapsed_time(e1):.3f} ms")
     if a.out:
