@@ -611,3 +611,23 @@ class Renderer:
 
     def __call__(self, stream=None):
         return render(self.p, self.image, self.counters, self.workspace, stream)
+
+    def capture(self):
+        """Record one kl_render of p (its three launches: parts, combine and
+        the per-word kernel) in a CUDA graph, after one render outside the
+        capture; replay() then repeats it with one launch from the host."""
+        torch = _torch()
+        dev = self.image.device
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            self()
+        torch.cuda.current_stream(dev).wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self()
+        self.graph = g
+
+    def replay(self):
+        self.graph.replay()
+        return self.image, self.counters

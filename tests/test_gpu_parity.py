@@ -242,3 +242,21 @@ def test_render_accumulate_and_errors(kl):
     with pytest.raises(kl.KlError) as e:
         kl.render(p, img, cnt, big)
     assert e.value.status in (1, 2)
+
+
+@pytest.mark.parametrize("prec,mode", [("FP64", "LIMIT_SET"), ("MIXED", "LIMIT_SET"),
+                                       ("DF64", "LIMIT_SET"), ("MIXED", "TILING")])
+def test_render_replayed_from_a_graph(kl, prec, mode):
+    """A kl_render captured in a CUDA graph and replayed gives the image and
+    counters of the direct call, bit for bit, replay after replay."""
+    import torch
+    g = GROUPS["gasket"]
+    p = kl.params_init(g.ta, g.tb, 12, 1024, 1024, (-1.5, 1.5, -1.5, 1.5), getattr(kl, prec),
+                       mode=getattr(kl, mode))
+    img, cnt = kl.render(p)
+    r = kl.Renderer(p)
+    r.capture()
+    for _ in range(3):
+        gi, gc = r.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(gi, img) and torch.equal(gc[:3], cnt[:3])
