@@ -370,6 +370,16 @@ KL_API int kl_mlp_train_step(float* d_params, float* d_m, float* d_v, const floa
                              float lr, float beta1, float beta2, float eps, float* d_loss,
                              float* d_grad, void* d_scratch, size_t scratch_bytes, void* stream);
 
+/* Self-test of the bounded waits the tensor-core kernels use (their MMA
+ * completions are waited for on an mbarrier, for at most about a second; on
+ * a timeout a kernel marks its results and returns instead of hanging).  One
+ * warp waits on an mbarrier that nothing completes, for at most limit_cycles
+ * clock cycles, then on one it completes itself.  d_result (4 uint32, device):
+ * [0] 1 if the first wait gave up, [1] 1 if the second completed, [2] the
+ * cycles the first wait took, capped at 2^32 - 1, [3] 0.  KL_EINVAL if
+ * limit_cycles is 0 or above 2^31. */
+KL_API int kl_wait_selftest(uint64_t limit_cycles, uint32_t* d_result, void* stream);
+
 /* Level-of-detail labels and pruned render.
  *
  * Tree levels: a node at level k is a reduced prefix w_1 .. w_k (the letters

@@ -20,7 +20,8 @@ API = ("kl_status_string", "kl_word_count", "kl_grandma", "kl_seeds", "kl_maskit
        "kl_render_multiseed",
        "kl_batch_create", "kl_batch_workspace_bytes", "kl_batch_render", "kl_batch_capture",
        "kl_batch_replay", "kl_batch_destroy", "kl_mlp_forward", "kl_mlp_scratch_bytes",
-       "kl_mlp_grad", "kl_mlp_adam", "kl_mlp_train_step", "kl_lod_node_count", "kl_lod_label_bytes", "kl_lod_labels",
+       "kl_mlp_grad", "kl_mlp_adam", "kl_mlp_train_step", "kl_wait_selftest",
+       "kl_lod_node_count", "kl_lod_label_bytes", "kl_lod_labels",
        "kl_lod_render_bytes", "kl_render_lod", "kl_render_lod_labels", "kl_fsa_count",
        "kl_render_fsa", "kl_render_noalloc", "kl_set_profile_events")
 KL_MLP_NPARAMS = 4801
@@ -190,6 +191,8 @@ def lib():
                                         ctypes.c_float, ctypes.c_float, ctypes.c_float, P, P, P,
                                         SZ, P]
         L.kl_mlp_train_step.restype = I
+        L.kl_wait_selftest.argtypes = [U64, P, P]
+        L.kl_wait_selftest.restype = I
         L.kl_lod_node_count.argtypes = [U32, U32]
         L.kl_lod_node_count.restype = U64
         L.kl_lod_label_bytes.argtypes = [ctypes.POINTER(Params), U32, U32]
@@ -473,6 +476,16 @@ def mlp_forward(params, x, stream=None):
     _check(lib().kl_mlp_forward(params.data_ptr(), x.data_ptr(), n, y.data_ptr(),
                                 _stream_handle(stream)), "kl_mlp_forward")
     return y
+
+
+def wait_selftest(limit_cycles: int, stream=None):
+    """kl_wait_selftest: (gave up, completed, cycles the give-up took)."""
+    torch = _torch()
+    out = torch.zeros(4, dtype=torch.int32, device="cuda")
+    _check(lib().kl_wait_selftest(limit_cycles, out.data_ptr(), _stream_handle(stream)),
+           "kl_wait_selftest")
+    r = out.cpu().numpy().view(np.uint32)
+    return bool(r[0]), bool(r[1]), int(r[2])
 
 
 class MlpTrainer:

@@ -455,6 +455,41 @@ extern "C" int kl_mlp_adam(float* d_params, float* d_m, float* d_v, float* d_gra
   return check_launch();
 }
 
+namespace {
+
+// One warp: a wait that nothing completes must give up at its bound, and a
+// wait on a phase this warp completes must succeed.
+__global__ void wait_selftest_kernel(long long limit, uint32_t* out) {
+  __shared__ uint64_t bar[2];
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+  }
+  __syncwarp();
+  const long long t0 = clock64();
+  const bool done = mbar_wait(&bar[0], 0u, limit);  // no arrival: must give up
+  const long long took = clock64() - t0;
+  __syncwarp();
+  if (threadIdx.x == 0)
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar[1])) : "memory");
+  __syncwarp();
+  const bool done2 = mbar_wait(&bar[1], 0u, limit);
+  if (threadIdx.x == 0) {
+    out[0] = done ? 0u : 1u;
+    out[1] = done2 ? 1u : 0u;
+    out[2] = took > 0xFFFFFFFFll ? 0xFFFFFFFFu : (uint32_t)took;
+    out[3] = 0u;
+  }
+}
+
+}  // namespace
+
+extern "C" int kl_wait_selftest(uint64_t limit_cycles, uint32_t* d_result, void* stream) {
+  if (!d_result || limit_cycles == 0 || limit_cycles > (1ull << 31)) return KL_EINVAL;
+  wait_selftest_kernel<<<1, 32, 0, (cudaStream_t)stream>>>((long long)limit_cycles, d_result);
+  return check_launch();
+}
+
 extern "C" int kl_mlp_train_step(float* d_params, float* d_m, float* d_v, const float* d_x,
                                  const float* d_t, uint64_t n, float under_weight, uint32_t step,
                                  float lr, float beta1, float beta2, float eps, float* d_loss,

@@ -128,3 +128,21 @@ def test_train_step_equals_gradient_then_adam(kl):
     assert runs[0][0] == runs[1][0]
     for a, b in zip(runs[0][1:], runs[1][1:]):
         assert np.array_equal(a, b)
+
+
+def test_bounded_wait_gives_up_and_the_device_stays_usable(kl):
+    """The tensor-core kernels wait for their MMAs on an mbarrier with a
+    bound.  A wait that nothing completes gives up after its bound and says
+    so; a completed one succeeds; and the device still works afterwards."""
+    import torch
+    gave_up, completed, cycles = kl.binding.wait_selftest(2_000_000)
+    assert gave_up and completed
+    assert 2_000_000 <= cycles < 200_000_000
+    with pytest.raises(kl.KlError):
+        kl.binding.wait_selftest(0)
+    # a forward pass right after still matches the oracle
+    p, x, _ = setup(300, 300)
+    y = kl.mlp_forward(torch.tensor(p, dtype=torch.float32, device="cuda"),
+                       torch.tensor(x, dtype=torch.float32, device="cuda")).cpu().numpy()
+    ref = mlp.forward(reference_params(p), mlp.bf16_round(x))
+    assert np.linalg.norm(y - ref) <= REL * np.linalg.norm(ref)
